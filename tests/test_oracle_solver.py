@@ -1,0 +1,326 @@
+"""Pins for the oracle's time-march against closed forms and the paper's theorems.
+
+* Closed-form infinite-horizon values of the double integrator, derived from
+  the cost functional of Sec. II-B, Eq. (3)-(4) (tests/closed_forms.py), with
+  first-order convergence under grid refinement.
+* The 1-D advection value min over the path of l, and a stationary case.
+* The variational-inequality invariant V <= l of Eq. (7).
+* The warm-start results of Sec. III and Sec. V / Appendix: Thm. 1 (warm <=
+  standard at every step), Lemma 1 / Thm. 2 (k above the standard solution
+  is squeezed onto it), Props. 1-2 and Sec. V-C (exact cases), Remarks 1-2
+  (monotone improvement), and the Sec. IV scenarios.
+Theorem orderings are checked step by step on the monotone scheme (ENO1 +
+forward Euler at CFL <= 1, global Lax-Friedrichs), for which the discrete
+update is order preserving and the proofs carry over exactly; ENO2 / WENO5
+runs are compared at convergence with a tolerance.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from closed_forms import advection_value, di_paper_strip_value, di_stop_position, di_strip_value
+from conftest import brt_hausdorff
+
+
+def _solve(orc, gd, dyn, l, k=None, scheme="eno2", rk=2, tol=1e-6, **kw):
+    P = orc.problem(gd, dyn)
+    return orc.solve(P, l, k, scheme=scheme, rk=rk, cfl=kw.pop("cfl", 0.5), tol=tol,
+                     max_steps=kw.pop("max_steps", 100000), **kw)
+
+
+# ------------------------------------------------------------ closed forms
+
+def _di_mask(X1, X2, u_eff, margin=0.5):
+    """Nodes whose optimal path stays well inside [-2,2]^2."""
+    stop = di_stop_position(X1, X2, u_eff)
+    return (np.abs(stop) <= 2.0 - margin) & (np.abs(X2) <= 2.0 - margin)
+
+
+@pytest.mark.parametrize("scheme,rk,dmax", [("eno2", 2, 0.0), ("weno5", 3, 0.0),
+                                            ("eno2", 2, 0.2), ("weno5", 3, 0.2)])
+def test_double_integrator_closed_form(orc, scheme, rk, dmax):
+    gd, dyn, l = W.di_config(101, dmax=dmax)
+    V, st = _solve(orc, gd, dyn, l, scheme=scheme, rk=rk)
+    assert st["converged"]
+    X1, X2 = W.mesh(gd)
+    u_eff = 1.0 - dmax
+    Vstar = di_strip_value(X1, X2, u_eff)
+    mask = _di_mask(X1, X2, u_eff)
+    dx = 0.04
+    assert np.abs(V - Vstar)[mask].max() <= 2.0 * dx
+    assert brt_hausdorff(np.where(mask, V, 1.0), np.where(mask, Vstar, 1.0)) <= 1.5
+
+
+def test_first_order_refinement(orc):
+    """Max error on a fixed physical region halves (order >= 0.7) as dx halves."""
+    errs, dxs, haus = [], [], []
+    for n in (51, 101, 201):
+        gd, dyn, l = W.di_config(n)
+        V, st = _solve(orc, gd, dyn, l)
+        X1, X2 = W.mesh(gd)
+        Vstar = di_strip_value(X1, X2, 1.0)
+        mask = _di_mask(X1, X2, 1.0)
+        errs.append(np.abs(V - Vstar)[mask].max())
+        dxs.append(4.0 / (n - 1))
+        haus.append(brt_hausdorff(np.where(mask, V, 1.0), np.where(mask, Vstar, 1.0)) * dxs[-1])
+    order = np.polyfit(np.log(dxs), np.log(errs), 1)[0]
+    assert order >= 0.7, (errs, order)
+    # The zero level set stays within one cell, so its error shrinks with dx.
+    assert all(h <= d + 1e-12 for h, d in zip(haus, dxs)), haus
+
+
+def test_running_example_paper_strip(orc):
+    """Sec. II-B running example: unsafe strip |p| <= 2 (l = |p| - 2).
+    ENO2 settles into a small limit cycle (max|dV| ~ 1e-4 per step) near the
+    valley of l at p = 0, so the march is capped by a horizon instead."""
+    gd = W.grid([121, 91], [-4.0, -3.0], [4.0, 3.0])
+    l = W.target_outside(gd, 0, 2.0)
+    V, st = _solve(orc, gd, W.double_integrator(), l, horizon=8.0)
+    assert st["tau"] >= 8.0 and st["last_delta"] < 1e-3
+    P, Vv = W.mesh(gd)
+    Vstar = di_paper_strip_value(P, Vv, 1.0)
+    stop = di_stop_position(P, Vv, 1.0)
+    mask = (np.abs(stop) <= 3.5) & (np.abs(Vv) <= 2.5) & (np.abs(P) <= 3.5)
+    dx = 8.0 / 120
+    assert np.abs(V - Vstar)[mask].max() <= 2.0 * dx
+    assert brt_hausdorff(np.where(mask, V, 1.0), np.where(mask, Vstar, 1.0)) <= 1.5
+
+
+def test_advection_closed_form(orc):
+    """x' = c, no inputs: V(x, tau) = min over s in [0, tau] of l(x + c s)."""
+    c, tau = 1.0, 1.0
+    l_fn = lambda x: np.abs(x) - 0.5  # noqa: E731
+    errs = []
+    for n in (101, 201, 401):
+        gd = W.grid([n], [-2.0], [2.0])
+        x = W.node_coords(gd)[0]
+        V, st = _solve(orc, gd, {"c": [c], "G": np.zeros((1, 0))}, l_fn(x), horizon=tau,
+                       tol=0.0)
+        assert not st["converged"] and st["tau"] >= tau
+        want = advection_value(x, st["tau"], c, l_fn)
+        errs.append(np.abs(V - want).max())
+        assert errs[-1] <= 2.0 * (4.0 / (n - 1))
+    assert errs[2] < errs[0]
+
+
+@pytest.mark.parametrize("scheme,rk", [("eno1", 1), ("eno2", 2), ("weno5", 3)])
+def test_convex_target_is_stationary(orc, scheme, rk):
+    """x' = u, u in [-1,1]^2: H = |p1| + |p2| >= 0 and a convex l gives
+    non-negative dissipation, so min(V + dt L, l) = l: V* = l."""
+    gd = W.grid([41, 37], [-2.0, -1.5], [2.0, 1.5])
+    X1, X2 = W.mesh(gd)
+    l = X1 ** 2 + 0.5 * X2 ** 2 - 1.0
+    dyn = {"G": np.eye(2), "ulo": [-1, -1], "uhi": [1, 1]}
+    V, st = _solve(orc, gd, dyn, l, scheme=scheme, rk=rk, tol=0.0, max_steps=40)
+    assert np.abs(V - l).max() <= 1e-13
+
+
+def test_vi_invariant_every_step(orc):
+    """Eq. (7): V never exceeds l, from the standard start and from a warm
+    start lying above l (which the init clips to l)."""
+    gd, dyn, l = W.di_config(41, dmax=0.1)
+    P = orc.problem(gd, dyn)
+    alpha, dt = orc.alpha_dt(P, 0.5)
+    for V in (orc.init(P, l), orc.init(P, l, l + 0.5), orc.init(P, l, W.warm_circles(gd, 2))):
+        assert np.all(V <= l)
+        for _ in range(60):
+            V, _ = orc.step(P, "weno5", 3, dt, alpha, l, V)
+            assert np.all(V <= l)
+
+
+def test_warm_start_above_l_equals_standard(orc):
+    """Thm. 1, case b: a warm start k >= l acts as min(k, l) = l, so the march
+    is the standard one, bit for bit."""
+    gd, dyn, l = W.di_config(51)
+    Vs, ss = _solve(orc, gd, dyn, l)
+    Vk, sk = _solve(orc, gd, dyn, l, k=l + np.abs(W.warm_circles(gd, 8)))
+    assert ss["steps"] == sk["steps"] and np.array_equal(Vs, Vk)
+
+
+# ------------------------------------------- theorems on the monotone scheme
+#
+# On a periodic grid (no ghost extrapolation) ENO1 + forward Euler with global
+# Lax-Friedrichs at CFL <= 1 is order preserving: each updated value is a
+# non-decreasing function of the old neighbourhood, and min(., l) keeps that.
+# Linear-extrapolation ghosts break this at the edges, so the step-by-step
+# orderings below are pinned on a torus problem:
+#   x1' = sin(x2) + d, x2' = u,  |u| <= umax, |d| <= 0.2,  l = cos(x1) - c.
+
+TORUS = W.grid([48, 48], [-np.pi, -np.pi], [np.pi, np.pi], periodic=[1, 1])
+
+
+def _torus_dyn(umax=1.0):
+    return {"A": np.zeros((2, 2)), "terms": [(0, 1, "sin", 1.0)], "G": [[0.0], [1.0]],
+            "ulo": [-umax], "uhi": [umax], "E": [[1.0], [0.0]], "dlo": [-0.2], "dhi": [0.2]}
+
+
+def _torus_l(c=0.2):
+    return np.cos(W.mesh(TORUS)[0]) - c
+
+
+def _march(orc, P, l, V0, steps, dt, alpha):
+    out = [V0]
+    V = V0
+    for _ in range(steps):
+        V, _ = orc.step(P, "eno1", 1, dt, alpha, l, V)
+        out.append(V)
+    return out
+
+
+@pytest.fixture(scope="module")
+def mono(orc):
+    l = _torus_l()
+    P = orc.problem(TORUS, _torus_dyn())
+    alpha, dt = orc.alpha_dt(P, 0.9)
+    std = _march(orc, P, l, orc.init(P, l), 1500, dt, alpha)
+    return {"P": P, "l": l, "alpha": alpha, "dt": dt, "std": std}
+
+
+def test_standard_iterates_non_increasing(orc, mono):
+    """From V0 = l the order-preserving update only lowers V."""
+    std = mono["std"]
+    for a, b in zip(std[:-1], std[1:]):
+        assert np.all(b <= a + 1e-14)
+    assert (std[0] - std[-1]).max() > 0.1  # the march does move
+
+
+def test_theorem1_warm_below_standard_every_step(orc, mono):
+    """Thm. 1: for every k, V_k(x, tau) <= V_l(x, tau) at every step."""
+    P, l = mono["P"], mono["l"]
+    X1, X2 = W.mesh(TORUS)
+    ks = [np.zeros_like(l), W.warm_circles(TORUS, 4, radius=(0.3, 1.0)), l + 0.3,
+          np.full_like(l, -2.0), 0.5 * l + 0.25 * np.sin(X2)]
+    for k in ks:
+        run = _march(orc, P, l, orc.init(P, l, k), 300, mono["dt"], mono["alpha"])
+        for n, Vk in enumerate(run):
+            assert np.all(Vk <= mono["std"][n] + 1e-12), n
+
+
+def test_lemma1_theorem2_squeeze(orc, mono):
+    """Lemma 1 / Thm. 2: with k >= (a standard iterate V_l^M), the warm march
+    stays above V_l^{M+n} and below V_l^n, so it is squeezed onto the
+    standard limit.  With k = V_l^M exactly, V_k^n = V_l^{M+n} bit for bit."""
+    P, l, std = mono["P"], mono["l"], mono["std"]
+    M = 1000
+    exact = _march(orc, P, l, orc.init(P, l, std[M]), 200, mono["dt"], mono["alpha"])
+    for n in range(200):
+        assert np.array_equal(exact[n], std[M + n])
+    X1, X2 = W.mesh(TORUS)
+    bump = 0.4 * np.exp(-(X1 ** 2 + X2 ** 2))
+    run = _march(orc, P, l, orc.init(P, l, std[M] + bump), 400, mono["dt"], mono["alpha"])
+    for n in range(400):
+        if M + n < len(std):
+            assert np.all(run[n] >= std[M + n] - 1e-12), n
+        assert np.all(run[n] <= std[n] + 1e-12), n
+    gap0 = np.abs(run[0] - std[0]).max()
+    assert np.abs(run[399] - std[399]).max() < 0.5 * gap0
+
+
+@pytest.mark.parametrize("case", ["control_grows", "target_shrinks"])
+def test_remarks_monotone_improvement(orc, case):
+    """Remarks 1-2: when the control set grows (or the target set shrinks),
+    the warm march from the old solution k improves monotonically and stays
+    below the new standard march.  k is a standard iterate V^M of the old
+    problem; its residual r = max(V^M - V^{M+1}) bounds the per-step decrease
+    exactly (the update commutes with constant shifts and preserves order)."""
+    if case == "control_grows":
+        l_old = l_new = _torus_l()
+        old_dyn, new_dyn = _torus_dyn(umax=0.5), _torus_dyn(umax=1.0)
+    else:
+        l_old, l_new = _torus_l(0.4), _torus_l(0.2)
+        old_dyn = new_dyn = _torus_dyn()
+    # Both problems use one dt and alpha (those of the larger control set).
+    P_new = orc.problem(TORUS, new_dyn)
+    alpha, dt = orc.alpha_dt(P_new, 0.9)
+    P_old = orc.problem(TORUS, old_dyn)
+    old = _march(orc, P_old, l_old, orc.init(P_old, l_old), 1201, dt, alpha)
+    k = old[1200]
+    r = float((old[1200] - old[1201]).max())
+    assert 0.0 <= r < 1e-3
+    std_new = _march(orc, P_new, l_new, orc.init(P_new, l_new), 300, dt, alpha)
+    run = _march(orc, P_new, l_new, orc.init(P_new, l_new, k), 300, dt, alpha)
+    for n in range(300):
+        assert np.all(run[n + 1] >= run[n] - r - 1e-13), n
+        assert np.all(run[n] <= std_new[n] + 1e-12), n
+    assert (run[300] - run[0]).max() > 10 * r  # it does improve
+
+
+# -------------------------------------- exact cases at convergence (ENO2/RK2)
+
+def _exact_case(orc, gd, dyn_old, l_old, dyn_new, l_new, scheme="eno2", rk=2):
+    Vold, _ = _solve(orc, gd, dyn_old, l_old, scheme=scheme, rk=rk)
+    Vstd, sstd = _solve(orc, gd, dyn_new, l_new, scheme=scheme, rk=rk)
+    Vw, sw = _solve(orc, gd, dyn_new, l_new, k=Vold, scheme=scheme, rk=rk)
+    assert sstd["converged"] and sw["converged"]
+    return Vstd, sstd, Vw, sw
+
+
+@pytest.mark.parametrize("case", ["prop1_target_grows", "prop2_control_shrinks",
+                                  "secVC_disturbance_grows"])
+def test_exact_cases_match_standard(orc, case):
+    """Prop. 1, Prop. 2 and Sec. V-C: warm-starting from the old converged
+    value reaches the new standard solution (max-abs <= 1e-4 max|l|, same
+    BRT) and takes no more steps."""
+    gd = W.grid([101, 101], [-2, -2], [2, 2])
+    l = W.target_strip(gd, 0, 1.0)
+    di = W.double_integrator
+    if case == "prop1_target_grows":
+        args = (di(), l, di(), W.target_strip(gd, 0, 0.8))
+    elif case == "prop2_control_shrinks":
+        args = (di(umax=1.2), l, di(umax=1.0), l)
+    else:
+        args = (di(dmax=0.0), l, di(dmax=0.2), l)
+    Vstd, sstd, Vw, sw = _exact_case(orc, gd, *args)
+    scale = np.abs(args[3]).max()
+    assert np.abs(Vw - Vstd).max() <= 1e-4 * scale
+    assert brt_hausdorff(Vw, Vstd) == 0.0
+    assert sw["steps"] <= sstd["steps"]
+
+
+def test_remark2_conservative_at_convergence(orc):
+    """Remark 2 (control grows, Sec. IV-A setting, u in [-.7,.7] -> [-1,1]):
+    the warm result is never above the standard one (conservative)."""
+    gd = W.grid([101, 101], [-2, -2], [2, 2])
+    l = W.target_strip(gd, 0, 1.0)
+    Vstd, _, Vw, _ = _exact_case(orc, gd, W.double_integrator(umax=0.7), l,
+                                 W.double_integrator(umax=1.0), l)
+    assert np.all(Vw <= Vstd + 1e-5)
+    assert np.all((Vw <= 0) | (Vstd > 0))  # warm BRT contains the standard BRT
+
+
+def test_secIV_scenarios(orc):
+    """Sec. IV-B: a flat k below l has zero gradient and stays put.
+    Sec. IV-C: k = 0 gives a conservative BRT (Thm. 1).
+    Sec. IV-D: k from random circles reaches the standard BRT."""
+    gd, dyn, l = W.di_config(101)
+    Vs, _ = _solve(orc, gd, dyn, l)
+    Vc, sc = _solve(orc, gd, dyn, l, k=np.full_like(l, -5.0))
+    assert sc["steps"] == 1 and np.all(Vc == -5.0)
+    Vz, _ = _solve(orc, gd, dyn, l, k=np.zeros_like(l))
+    assert np.all(Vz <= Vs + 1e-5)
+    assert np.all((Vz <= 0) | (Vs > 0))
+    Vr, sr = _solve(orc, gd, dyn, l, k=W.warm_circles(gd, 3))
+    assert sr["converged"] and np.all(Vr <= Vs + 1e-5)
+    assert brt_hausdorff(Vr, Vs) == 0.0
+
+
+@pytest.mark.parametrize("c", [1.0, -1.0])
+@pytest.mark.parametrize("rk,order", [(1, 1.0), (2, 2.0), (3, 3.0)])
+def test_runge_kutta_time_order(orc, rk, order, c):
+    """Periodic transport x' = c from the warm start k = sin(x), with l so large
+    that min(., l) never binds: V(x, tau) = sin(x + c tau).  WENO5's spatial
+    error is far below the time error here, so halving the CFL number must
+    divide the error by 2^rk (Euler, Heun, Shu-Osher).  Also pins the
+    periodic ghost wrap (a wrong wrap gives O(1) errors)."""
+    N = 256
+    gd = W.grid([N], [0.0], [2 * np.pi], periodic=[1])
+    x = W.node_coords(gd)[0]
+    P = orc.problem(gd, {"c": [c], "G": np.zeros((1, 0))})
+    errs = []
+    for cfl in (0.8, 0.4):
+        V, st = orc.solve(P, np.full(N, 10.0), np.sin(x), scheme="weno5", rk=rk, cfl=cfl,
+                          tol=0.0, horizon=1.0)
+        errs.append(np.abs(V - np.sin(x + c * st["tau"])).max())
+    measured = np.log2(errs[0] / errs[1])
+    assert abs(measured - order) < 0.25, (errs, measured)
+    assert errs[1] < {1: 1e-2, 2: 3e-5, 3: 1e-7}[rk]
