@@ -1,0 +1,334 @@
+"""Benchmark: warm-started HJI reachability solves on the GB300.
+
+One bench step is one whole solve through the C ABI (set-up reductions for
+alpha and dt, init V0 = min(k, l), the fused ENO/WENO + Hamiltonian + LF +
+RK-stage + min(l) march, and the max|dV| convergence test until it stops) of
+the 1001 x 1001 double integrator with disturbance |d| <= 0.2, WENO5 / RK3,
+CFL 0.5, tol 1e-6, warm-started from the d = 0 solution (computed once,
+outside the timed region).  The metric is cell-updates/s: nodes x steps
+advanced per second.  Inputs are synthetic and seeded (workloads/).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32|f64]
+    python bench.py --impl reference   # the FP64 CPU oracle on a bounded sample
+
+Under torchrun (N > 1) every rank solves its own instance (independent
+problems: weak scaling, no collective on the data path); the job's value is
+the cell-updates of all ranks over the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+N_SIDE, DMAX = 1001, 0.2
+SOLVE = dict(scheme="weno5", rk=3, cfl=0.5, tol=1e-6, max_steps=200000, check_every=32)
+# Algorithmic work of one node through one RK stage of WENO5 in 2-D, counted
+# from the textbook formulas (FP operations: +, -, *, /, max, abs):
+#   per axis: 6 differences, 2 x 78 for the two WENO5 reconstructions
+#   (15 candidates, 33 smoothness, 11 epsilon, 9 raw weights, 10 normalise
+#   and combine), 2 scalings by 1/dx -> 164;  two axes -> 328;
+#   Hamiltonian (averaged gradient 4, drift 8, <p,f0> 3, control 6,
+#   disturbance 6) -> 27;  Lax-Friedrichs 6;  Euler stage 2;  RK combine 3;
+#   min(., l), |dV| and max 4.
+FLOPS_PER_NODE_STAGE = 328 + 27 + 6 + 2 + 3 + 4
+# Algorithmic HBM words per node per RK3 step with per-stage kernels:
+# stage 1 reads V, writes W1; stage 2 reads W1, V, writes W2; stage 3 reads
+# W2, V, l, writes V'.
+WORDS_PER_NODE_STEP = 9
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+
+        def reader():
+            for line in self.proc.stdout:
+                self.rows.append([c.strip() for c in line.split(",")])
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _flush_l2(torch, buf):
+    buf.add_(1)  # 512 MB written: larger than the 129 MB L2
+
+
+def cpu_baseline(n_steps=None, budget_s=15.0):
+    """The FP64 oracle as it stands, on a bounded sample of the same workload:
+    `n_steps` RK3 steps of the 1001^2 WENO5 march from the warm start."""
+    import oracle
+    gd, dyn, l = W.di_config(N_SIDE, dmax=DMAX)
+    P = oracle.problem(gd, dyn)
+    alpha, dt = oracle.alpha_dt(P, SOLVE["cfl"])
+    V = oracle.init(P, l, np.minimum(l, 0.5 + 0.0 * l))
+    cells = W.num_cells(gd)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        V, _ = oracle.step(P, "weno5", 3, dt, alpha, l, V)
+        steps += 1
+        el = time.perf_counter() - t0
+        if (n_steps is not None and steps >= n_steps) or (n_steps is None and el >= budget_s):
+            break
+    return {"value": cells * steps / el, "unit": "cell-updates/s", "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": "%d WENO5/RK3 FP64 steps of the 1001^2 double-integrator march "
+                      "(%.1f s on the host cores)" % (steps, el)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    samples = []
+    for _ in range(args.warmup):
+        cpu_baseline(n_steps=1)
+    t_all = 0.0
+    cells = 0
+    for _ in range(args.steps):
+        r = cpu_baseline(n_steps=4)
+        samples.append(r)
+        steps = int(r["sample"].split()[0])
+        t_all += W.num_cells(W.di_config(N_SIDE, dmax=DMAX)[0]) * steps / r["value"]
+        cells += W.num_cells(W.di_config(N_SIDE, dmax=DMAX)[0]) * steps
+    value = cells / t_all
+    line = {"impl": "reference", "metric": "cell-updates/s", "value": value,
+            "unit": "cell-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t_all / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "double integrator 1001x1001, |d|<=0.2, WENO5/RK3, cfl 0.5, "
+                                   "warm start; each step a bounded 4-step sample"},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s",
+                             "cores": samples[-1]["cores"], "kind": "oracle",
+                             "sample": samples[-1]["sample"]},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args()
+
+    rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_1903_07715_gb300 as hji
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    hji.load()
+
+    prec = args.precision
+    npdt = np.float32 if prec == "f32" else np.float64
+    tdt = torch.float32 if prec == "f32" else torch.float64
+    gd, dyn, l = W.di_config(N_SIDE, dmax=DMAX)
+    _, dyn0, _ = W.di_config(N_SIDE, dmax=0.0)
+    cells = W.num_cells(gd)
+    esize = np.dtype(npdt).itemsize
+
+    # Warm start k: the converged d = 0 solution (an input, computed untimed).
+    g = hji.Grid(gd, prec)
+    g.set_dynamics(dyn0)
+    l_dev = torch.from_numpy(l.astype(npdt)).cuda()
+    g.solve(l_dev, **SOLVE)
+    k_dev = torch.empty_like(l_dev)
+    g.value(k_dev)
+    g.set_dynamics(dyn)
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def timed_solves(n, host=False):
+        total_ms, updates, launches, stats = 0.0, 0, 0, []
+        if host:
+            l_h = torch.empty(l_dev.shape, dtype=tdt, pin_memory=True)
+            l_h.copy_(l_dev)
+            k_h = torch.empty(l_dev.shape, dtype=tdt, pin_memory=True)
+            k_h.copy_(k_dev)
+            out_h = torch.empty(l_dev.shape, dtype=tdt, pin_memory=True)
+            l_np, k_np, out_np = l_h.numpy(), k_h.numpy(), out_h.numpy()
+        for _ in range(n):
+            _flush_l2(torch, flush)
+            torch.cuda.synchronize()
+            if dist is not None:
+                dist.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if host:
+                st = g.solve(l_np, k_np, **SOLVE)
+                g.value(out_np)
+            else:
+                st = g.solve(l_dev, k_dev, **SOLVE)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            updates += cells * st["steps"]
+            launches += st["kernel_launches"]
+            stats.append(st)
+        return total_ms, updates, launches, stats
+
+    timed_solves(args.warmup)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ms, updates, launches, stats = timed_solves(args.steps)
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        u = torch.tensor([updates], device="cuda", dtype=torch.float64)
+        dist.all_reduce(u)
+        updates = float(u.item())
+    value = updates / (ms / 1000.0)
+
+    e2e_ms, e2e_updates, _, _ = timed_solves(max(1, args.steps), host=True)
+    e2e = {"value": e2e_updates / (e2e_ms / 1000.0), "unit": "cell-updates/s",
+           "h2d_bytes_per_step": 2 * cells * esize, "d2h_bytes_per_step": cells * esize}
+
+    steps_per_solve = statistics.mean(s["steps"] for s in stats)
+    stage_launches_with_work = steps_per_solve * SOLVE["rk"]
+    avg_stage_ms = (ms / args.steps) / stage_launches_with_work
+    flops = FLOPS_PER_NODE_STAGE * cells
+    achieved_tflops = flops / (avg_stage_ms * 1e-3) / 1e12
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    # FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock.
+    # FP64 peak: GB300 lists 1.25 TFLOP/s (at the 2070 MHz maximum clock).
+    if prec == "f32":
+        peak = 152 * 128 * 2 * 2070e6 / 1e12
+    else:
+        peak = 1.25
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved_tflops / peak, "traffic": None,
+                "kernel": "stage_kernel<%s,2,WENO5> (per-stage, 3 per RK3 step)" % prec,
+                "flops_per_node_stage": FLOPS_PER_NODE_STAGE,
+                "hbm_words_per_node_step": WORDS_PER_NODE_STEP,
+                "peak_source": "derived from unit counts at 2070 MHz max SM clock"
+                               if prec == "f32" else "GB300 datasheet FP64 rate"}
+
+    line = {"metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": "double integrator x1'=x2, x2'=u+d, |u|<=1, |d|<=0.2, "
+                                   "1001x1001 on [-2,2]^2, l=1-|x1|, WENO5/RK3, cfl 0.5, "
+                                   "tol 1e-6, warm start from the d=0 solution",
+                       "nodes": cells, "steps_per_solve": steps_per_solve,
+                       "precision": prec + " storage and stencil, FP64 dt/alpha and max|dV|",
+                       "l2": "flushed (512 MB write) before every timed solve; the 1001^2 "
+                             "fields stay L2-resident within a solve",
+                       "parallelism": "independent instance per GPU" if world > 1 else "1 GPU"},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk}
+
+    if rank == 0 and not args.no_variants:
+        line["time_to_converge"] = time_to_converge(hji, torch, gd, dyn, l, l_dev, k_dev, prec)
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(budget_s=12.0)
+    g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def time_to_converge(hji, torch, gd, dyn, l, l_dev, k_dev, prec):
+    """Warm vs standard time-to-converge on the bench workload, in the bench
+    precision and in FP64 (each one solve, device-resident inputs)."""
+    out = {}
+    for p in sorted({prec, "f64"}):
+        tdt = torch.float32 if p == "f32" else torch.float64
+        g = hji.Grid(gd, p)
+        g.set_dynamics(dyn)
+        ld, kd = l_dev.to(tdt), k_dev.to(tdt)
+        for name, k in (("standard", None), ("warm", kd)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = g.solve(ld, k, **SOLVE)
+            torch.cuda.synchronize()
+            out["%s_%s" % (p, name)] = {"ms": 1000 * (time.perf_counter() - t0),
+                                        "steps": st["steps"], "converged": st["converged"],
+                                        "intervals_0.01": st["tau"] / 0.01}
+        g.close()
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,195 @@
+/*
+ * hji.h - C ABI of the GB300 (sm_103a) solver for warm-start Hamilton-Jacobi-
+ * Isaacs reachability (Herbert, Ghosh, Bansal, Tomlin, arXiv:1903.07715).
+ *
+ * The library time-marches the infinite-horizon avoid HJI variational
+ * inequality of Sec. II-B, Eq. (7),
+ *     min{ D_t V + H(x, grad V), l(x) - V } = 0,
+ * backwards in time on a dense N-D grid (N <= 4), with the Hamiltonian of
+ * Eq. (6), H = max_u min_d <grad V, f(x,u,d)>, for control-affine dynamics
+ * (Eq. (1)) with box-bounded control and disturbance.  It starts from the
+ * standard initialisation V(x,0) = l(x) (Sec. II-B) or from a warm start
+ * V(x,0) = min(k(x), l(x)) (Sec. III, Eq. (14) and the proof of Thm. 1), and
+ * stops when the largest change of V over the grid in one step falls below a
+ * tolerance (Sec. IV), or at a horizon / step cap.
+ *
+ * Numerics (the paper delegates them to a level-set toolbox, Sec. II-B after
+ * Eq. (8)): upwind one-sided derivatives (ENO1, ENO2, HJ-WENO5), the
+ * Lax-Friedrichs numerical Hamiltonian with dissipation coefficients
+ * alpha_a = max over the grid of max_{u,d} |f_a|, TVD Runge-Kutta of order
+ * 1/2/3 with dt = cfl / max over the grid of sum_a max_{u,d}|f_a| / dx_a, and
+ * V <- min(V, l) after every full step.  Ghost nodes beyond a non-periodic
+ * edge extrapolate V linearly from the two edge nodes.
+ *
+ * Conventions for every entry point:
+ *   - Arrays are dense, C order (axis 0 slowest), element type double for
+ *     HJI_F64 grids and float for HJI_F32 grids.
+ *   - Node i of axis a sits at lo[a] + i * dx[a], dx[a] = (hi[a]-lo[a])/(n[a]-1),
+ *     or (hi[a]-lo[a])/n[a] on a periodic axis.
+ *   - `ptr_is_device` = 1: the pointer is CUDA device memory on the current
+ *     device; 0: host memory.  The library never keeps caller pointers beyond
+ *     a call; every call that reads or writes caller memory has finished with
+ *     it when it returns.
+ *   - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).
+ *     All device work of a call is ordered on it; calls return after that
+ *     work has finished.
+ *   - No exception or C++ object crosses this boundary.  Errors are returned
+ *     as hji_status; hji_last_error() gives a per-handle message.
+ *   - A handle is not thread-safe; separate handles may be used from
+ *     separate threads.
+ */
+#ifndef HJI_H
+#define HJI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HJI_MAX_DIM 4    /* state dimensions per grid            */
+#define HJI_MAX_INPUTS 4 /* control / disturbance components     */
+#define HJI_MAX_TERMS 8  /* nonlinear terms w * phi(x[axis])     */
+
+typedef struct hji_grid_s* hji_grid;
+
+typedef enum {
+    HJI_OK = 0,
+    HJI_E_INVALID = 1,       /* bad argument, NaN/Inf input, unsupported size          */
+    HJI_E_NOMEM = 2,         /* device allocation failed                               */
+    HJI_E_CUDA = 3,          /* a CUDA runtime call failed (see hji_last_error)        */
+    HJI_E_NOT_CONVERGED = 4, /* horizon or step cap reached first; value still valid   */
+    HJI_E_TIMEOUT = 5,       /* reserved: a bounded device wait gave up                */
+    HJI_E_STATE = 6,         /* call out of order (no dynamics set, no value yet, ...) */
+    HJI_E_NONFINITE = 7      /* the march produced NaN/Inf (e.g. cfl too large)         */
+} hji_status;
+
+typedef enum { HJI_F64 = 0, HJI_F32 = 1 } hji_precision;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc
+ * returns device memory of `bytes` bytes usable on `stream` (NULL on
+ * failure); free releases it.  NULL allocator: cudaMallocAsync/cudaFreeAsync. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*free)(void* ptr, void* stream, void* ctx);
+    void* ctx;
+} hji_allocator;
+
+/* Create a grid of ndim (1..4) axes with n[a] >= 3 nodes on [lo[a], hi[a]]
+ * (hi > lo), at most 2^31 - 1 nodes in all, periodic[a] != 0 for a periodic
+ * axis (may be NULL), storing V in `prec`.  Allocates the value buffers on
+ * the current device.  `alloc` may be NULL; if not, it is copied and must
+ * stay callable until hji_grid_destroy.
+ * Errors: HJI_E_INVALID (sizes, bounds), HJI_E_NOMEM, HJI_E_CUDA. */
+hji_status hji_grid_create(int ndim, const int64_t* n, const double* lo, const double* hi,
+                           const int* periodic, hji_precision prec, const hji_allocator* alloc,
+                           hji_grid* out);
+
+/* Release every device buffer of the grid.  NULL is accepted. */
+hji_status hji_grid_destroy(hji_grid g);
+
+typedef enum { HJI_FN_TAN = 0, HJI_FN_SIN = 1, HJI_FN_COS = 2 } hji_fn;
+
+/* Control-affine dynamics of Sec. II-A, Eq. (1), with n = the grid's ndim:
+ *   f(x,u,d) = c + A x + sum_t term_w[t] * phi_t(x[term_axis[t]]) e_{term_row[t]}
+ *              + G u + E d,
+ *   u in [ulo, uhi] (m components), d in [dlo, dhi] (q components).
+ * Layouts (row-major, dense): c[n], A[n*n] (A[i*n+j] multiplies x_j in f_i),
+ * G[n*m], E[n*q]; term arrays of length nterms, phi given as hji_fn.
+ * m in 0..4, q in 0..4, nterms in 0..8; c, A, E, term arrays may be NULL when
+ * unused (zero).  Requires ulo <= uhi and dlo <= dhi componentwise, all
+ * values finite.  The arrays are copied; the caller keeps ownership.
+ * Errors: HJI_E_INVALID. */
+typedef struct {
+    int m, q, nterms;
+    const double* c;
+    const double* A;
+    const double* G;
+    const double* E;
+    const int* term_row;
+    const int* term_axis;
+    const int* term_fn;
+    const double* term_w;
+    const double* ulo;
+    const double* uhi;
+    const double* dlo;
+    const double* dhi;
+} hji_dynamics;
+
+hji_status hji_dynamics_set(hji_grid g, const hji_dynamics* dyn);
+
+typedef enum { HJI_ENO1 = 1, HJI_ENO2 = 2, HJI_WENO5 = 5 } hji_scheme;
+
+typedef enum {
+    HJI_INIT_STANDARD = 0, /* V(x,0) = l(x)                                        */
+    HJI_INIT_USER_K = 1,   /* V(x,0) = min(k(x), l(x)), k given by the caller      */
+    HJI_INIT_RESIDENT = 2  /* V(x,0) = min(V_prev(x), l(x)): the grid's last value */
+} hji_init;
+
+/* scheme: ENO1 (needs n >= 3), ENO2 (n >= 5), WENO5 (n >= 7) per axis.
+ * rk_order: 1, 2 or 3.  cfl in (0, 1].  tol >= 0: stop once max|dV| < tol.
+ * horizon >= 0: stop once tau >= horizon (0 = none).  max_steps: step cap
+ * (<= 0 means 1,000,000).  check_every: steps per host check of the stop
+ * flag (<= 0 means 32); steps after the stop point never run. */
+typedef struct {
+    hji_scheme scheme;
+    int rk_order;
+    double cfl;
+    double tol;
+    double horizon;
+    int check_every;
+    int64_t max_steps;
+    hji_init init;
+} hji_solve_opts;
+
+typedef struct {
+    int64_t steps;       /* full Runge-Kutta steps taken                      */
+    double tau;          /* backward time reached (steps * dt)                */
+    double dt;           /* CFL step used                                     */
+    double final_max_dV; /* max |V^{n+1} - V^n| of the last step (FP64)       */
+    double wall_ms;      /* host wall time of the call                        */
+    double alpha[HJI_MAX_DIM]; /* Lax-Friedrichs coefficients                 */
+    int converged;       /* 1 if final_max_dV < tol ended the march           */
+    int64_t kernel_launches; /* device kernels this call launched (set-up,
+                                stages, and the no-op stages queued past the
+                                stop point)                                   */
+} hji_solve_stats;
+
+/* March the HJI VI on grid g for target l (grid-shaped) from the init mode
+ * in `o`; k is read only for HJI_INIT_USER_K (else may be NULL).  The result
+ * stays in the grid (read it with hji_value_get; HJI_INIT_RESIDENT starts
+ * the next solve from it).  Returns HJI_OK when converged,
+ * HJI_E_NOT_CONVERGED when a cap stopped it first (the value is still the
+ * last iterate), HJI_E_INVALID for bad options or NaN/Inf in l or k,
+ * HJI_E_STATE if no dynamics were set (or RESIDENT without a prior value),
+ * HJI_E_NONFINITE if the march blew up, HJI_E_NOMEM / HJI_E_CUDA.
+ * `stats` may be NULL. */
+hji_status hji_solve(hji_grid g, const void* l, const void* k, int ptr_is_device,
+                     const hji_solve_opts* o, void* cuda_stream, hji_solve_stats* stats);
+
+/* Several grids in one march: every RK stage of every grid is one persistent
+ * kernel launch over a shared tile list, captured in CUDA graphs; each grid
+ * stops on its own test while the others go on.  All grids must share
+ * precision and ndim; l[i], k[i] belong to grids[i] (k may be NULL, or hold
+ * NULL entries, unless o->init is HJI_INIT_USER_K).  stats has `count`
+ * entries or is NULL.  Returns HJI_OK if every grid converged, else the
+ * first non-OK per-grid status. */
+hji_status hji_batch_solve(int count, hji_grid* grids, const void* const* l,
+                           const void* const* k, int ptr_is_device, const hji_solve_opts* o,
+                           void* cuda_stream, hji_solve_stats* stats);
+
+/* Copy the grid's current value (grid-shaped, the grid's precision) to out.
+ * Errors: HJI_E_STATE (no value yet), HJI_E_INVALID, HJI_E_CUDA. */
+hji_status hji_value_get(hji_grid g, void* out, int ptr_is_device, void* cuda_stream);
+
+/* Grid facts: ndim, n[], and the number of nodes (may be NULL each). */
+hji_status hji_grid_info(hji_grid g, int* ndim, int64_t* n, int64_t* num_nodes);
+
+const char* hji_status_string(hji_status s);
+const char* hji_last_error(hji_grid g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HJI_H */

@@ -1,0 +1,701 @@
+// Host runtime behind the C ABI of include/hji.h: grid handles, validation,
+// device buffers, the per-solve set-up, the tile list, and the march loop.
+//
+// The march runs as CUDA graphs of `check_every` steps (every RK stage of
+// every grid in the batch is one persistent kernel launch over the shared
+// tile list).  Kernels skip the tiles of grids that have stopped, so the host
+// keeps one graph in flight ahead of the one it checks; it reads a single
+// device counter of still-marching grids per graph and never syncs per step.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hji_common.cuh"
+
+using hji::InstDesc;
+using hji::InstState;
+
+struct hji_grid_s {
+    int ndim = 0;
+    int64_t n[HJI_MAX_DIM] = {1, 1, 1, 1};
+    double lo[HJI_MAX_DIM] = {0, 0, 0, 0};
+    double hi[HJI_MAX_DIM] = {0, 0, 0, 0};
+    double dx[HJI_MAX_DIM] = {1, 1, 1, 1};
+    int periodic[HJI_MAX_DIM] = {0, 0, 0, 0};
+    hji_precision prec = HJI_F64;
+    size_t esize = 8;
+    int64_t ncells = 0;
+    int device = 0;
+    bool has_alloc = false;
+    hji_allocator alloc{};
+    void* V[2] = {nullptr, nullptr};
+    void* W1 = nullptr;
+    void* W2 = nullptr;
+    void* Vlo = nullptr;             // FP32 grids: low word of the compensated value
+    void* l = nullptr;
+    void* table = nullptr;
+    size_t table_bytes = 0;
+    InstState* state = nullptr;      // device
+    InstDesc* d_desc = nullptr;      // device descriptor for single-grid solves
+    int* d_active = nullptr;         // device counter for single-grid solves
+    unsigned long long* d_tiles = nullptr;
+    size_t tiles_cap = 0;
+    int* d_ntiles = nullptr;
+    int* h_active = nullptr;         // pinned host mirrors
+    InstState* h_state = nullptr;
+    bool has_dyn = false;
+    hji::Dyn dyn{};
+    bool has_value = false;
+    int cur = 0;
+    std::string err;
+    // Graph cache for single-grid solves.
+    cudaGraphExec_t graph = nullptr;
+    long long graph_key[6] = {0, 0, 0, 0, 0, 0};
+    cudaStream_t cap_stream = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+hji_status fail(hji_grid g, hji_status s, const std::string& msg) {
+    if (g) g->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+hji_status cuda_fail(hji_grid g, cudaError_t e, const char* where) {
+    return fail(g, HJI_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define HJI_CUDA(g, call)                                        \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail((g), e_, #call); \
+    } while (0)
+
+void* dev_alloc(hji_grid g, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 16;
+    if (g->has_alloc) return g->alloc.alloc(bytes, s, g->alloc.ctx);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(hji_grid g, void* p, cudaStream_t s) {
+    if (!p) return;
+    if (g->has_alloc) g->alloc.free(p, s, g->alloc.ctx);
+    else cudaFreeAsync(p, s);
+}
+
+int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
+    }
+    return sms;
+}
+
+bool finite_all(const double* p, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+struct StagePlan {
+    int in, out;
+    double aV, aE;
+    bool last;
+};
+
+int rk_plan(int rk, StagePlan* p) {
+    if (rk == 1) {
+        p[0] = {0, 3, 0.0, 1.0, true};
+        return 1;
+    }
+    if (rk == 2) {
+        p[0] = {0, 1, 0.0, 1.0, false};
+        p[1] = {1, 3, 0.5, 0.5, true};
+        return 2;
+    }
+    p[0] = {0, 1, 0.0, 1.0, false};
+    p[1] = {1, 2, 0.75, 0.25, false};
+    p[2] = {2, 3, 1.0 / 3.0, 2.0 / 3.0, true};
+    return 3;
+}
+
+hji::StageLauncher launcher(bool f32, int ndim, int scheme, bool last) {
+    return f32 ? hji::stage_launcher_f32(ndim, scheme, last)
+               : hji::stage_launcher_f64(ndim, scheme, last);
+}
+
+int stage_grid(bool f32, int ndim, int scheme, long long total_tiles) {
+    int per_sm = 1;
+    for (int last = 0; last < 2; ++last) {
+        const int b = f32 ? hji::stage_max_blocks_f32(ndim, scheme, last)
+                          : hji::stage_max_blocks_f64(ndim, scheme, last);
+        per_sm = last == 0 ? b : (b < per_sm ? b : per_sm);
+    }
+    long long g = (long long)num_sms() * per_sm;
+    if (g > total_tiles) g = total_tiles;
+    return g < 1 ? 1 : (int)g;
+}
+
+void tile_grid(int ndim, const int64_t* n, long long& tx, long long& ty, long long& planes) {
+    const int TX = ndim == 1 ? hji::TileShape<1>::TX : hji::TileShape<2>::TX;
+    const int TY = ndim == 1 ? hji::TileShape<1>::TY : hji::TileShape<2>::TY;
+    tx = (n[ndim - 1] + TX - 1) / TX;
+    ty = ndim >= 2 ? (n[ndim - 2] + TY - 1) / TY : 1;
+    planes = 1;
+    for (int a = 0; a < ndim - 2; ++a) planes *= n[a];
+}
+
+hji_status validate_opts(hji_grid g, const hji_solve_opts* o) {
+    if (!o) return fail(g, HJI_E_INVALID, "opts is NULL");
+    if (o->scheme != HJI_ENO1 && o->scheme != HJI_ENO2 && o->scheme != HJI_WENO5)
+        return fail(g, HJI_E_INVALID, "unknown scheme");
+    if (o->rk_order < 1 || o->rk_order > 3) return fail(g, HJI_E_INVALID, "rk_order must be 1, 2 or 3");
+    if (!(o->cfl > 0.0 && o->cfl <= 1.0)) return fail(g, HJI_E_INVALID, "cfl must be in (0, 1]");
+    if (!(o->tol >= 0.0) || !std::isfinite(o->tol)) return fail(g, HJI_E_INVALID, "tol must be finite and >= 0");
+    if (!(o->horizon >= 0.0) || !std::isfinite(o->horizon))
+        return fail(g, HJI_E_INVALID, "horizon must be finite and >= 0");
+    if (o->init != HJI_INIT_STANDARD && o->init != HJI_INIT_USER_K && o->init != HJI_INIT_RESIDENT)
+        return fail(g, HJI_E_INVALID, "unknown init mode");
+    return HJI_OK;
+}
+
+// Make sure the stage buffers and the term table exist for this solve.
+hji_status ensure_buffers(hji_grid g, int rk, cudaStream_t s) {
+    const size_t bytes = (size_t)g->ncells * g->esize;
+    if (rk >= 2 && !g->W1) {
+        g->W1 = dev_alloc(g, bytes, s);
+        if (!g->W1) return fail(g, HJI_E_NOMEM, "stage buffer allocation failed");
+    }
+    if (rk >= 3 && !g->W2) {
+        g->W2 = dev_alloc(g, bytes, s);
+        if (!g->W2) return fail(g, HJI_E_NOMEM, "stage buffer allocation failed");
+    }
+    long long nmax = 0;
+    for (int a = 0; a < g->ndim; ++a) nmax = g->n[a] > nmax ? g->n[a] : nmax;
+    const size_t tb = (size_t)HJI_MAX_TERMS * nmax * g->esize;
+    if (!g->table) {
+        g->table = dev_alloc(g, tb, s);
+        if (!g->table) return fail(g, HJI_E_NOMEM, "table allocation failed");
+        g->table_bytes = tb;
+    }
+    return HJI_OK;
+}
+
+InstDesc make_desc(hji_grid g, const hji_solve_opts* o, int* active) {
+    InstDesc D;
+    std::memset(&D, 0, sizeof(D));
+    D.ndim = g->ndim;
+    long long stride = 1;
+    for (int a = HJI_MAX_DIM - 1; a >= 0; --a) {
+        D.n[a] = (int)g->n[a];
+        D.periodic[a] = g->periodic[a];
+        D.lo[a] = g->lo[a];
+        D.dx[a] = g->dx[a];
+    }
+    for (int a = g->ndim - 1; a >= 0; --a) {
+        D.stride[a] = stride;
+        stride *= g->n[a];
+    }
+    D.ncells = g->ncells;
+    D.dyn = g->dyn;
+    D.cfl = o->cfl;
+    D.tol = o->tol;
+    D.horizon = o->horizon;
+    D.max_steps = o->max_steps > 0 ? o->max_steps : 1000000;
+    D.V[0] = g->V[0];
+    D.V[1] = g->V[1];
+    D.W1 = g->W1;
+    D.W2 = g->W2;
+    D.Vlo = g->Vlo;
+    D.l = g->l;
+    D.table = g->table;
+    long long nmax = 0;
+    for (int a = 0; a < g->ndim; ++a) nmax = g->n[a] > nmax ? g->n[a] : nmax;
+    D.table_stride = nmax;
+    D.history = nullptr;
+    D.history_len = 0;
+    long long tx, ty, planes;
+    tile_grid(g->ndim, g->n, tx, ty, planes);
+    D.tiles_x = tx;
+    D.tiles_y = ty;
+    D.tiles_per_plane = tx * ty;
+    D.ntiles = tx * ty * planes;
+    D.state = g->state;
+    D.active = active;
+    return D;
+}
+
+// Capture `steps` steps of the march (all RK stages) into a graph.
+hji_status capture_chunk(hji_grid g, cudaStream_t cap, bool f32, int ndim, int scheme, int rk,
+                         int steps, const hji::StageArgs& base, int grid, cudaGraphExec_t* out) {
+    StagePlan plan[3];
+    const int ns = rk_plan(rk, plan);
+    hji::StageLauncher L[3];
+    for (int i = 0; i < ns; ++i) {
+        L[i] = launcher(f32, ndim, scheme, plan[i].last);
+        if (!L[i]) return fail(g, HJI_E_INVALID, "no kernel for this ndim/scheme");
+    }
+    HJI_CUDA(g, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < steps && e == cudaSuccess; ++s) {
+        for (int i = 0; i < ns && e == cudaSuccess; ++i) {
+            hji::StageArgs a = base;
+            a.stage_in = plan[i].in;
+            a.stage_out = plan[i].out;
+            a.aV = plan[i].aV;
+            a.aE = plan[i].aE;
+            e = L[i](a, grid, cap);
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(g, e, "stage launch during capture");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(g, e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaGraphInstantiate");
+    return HJI_OK;
+}
+
+// The march shared by hji_solve (count == 1) and hji_batch_solve.
+hji_status run(int count, hji_grid* grids, const void* const* l, const void* const* k,
+               int ptr_is_device, const hji_solve_opts* o, cudaStream_t s, hji_solve_stats* stats) {
+    const auto t0 = std::chrono::steady_clock::now();
+    hji_grid g0 = grids[0];
+    hji_status st = validate_opts(g0, o);
+    if (st != HJI_OK) return st;
+    const bool f32 = g0->prec == HJI_F32;
+    const int ndim = g0->ndim;
+    const int gw = hji::ghost_width(o->scheme);
+    for (int i = 0; i < count; ++i) {
+        hji_grid g = grids[i];
+        if (!g) return fail(g0, HJI_E_INVALID, "NULL grid in batch");
+        if (g->prec != g0->prec || g->ndim != ndim)
+            return fail(g0, HJI_E_INVALID, "grids of a batch must share precision and ndim");
+        if (!g->has_dyn) return fail(g, HJI_E_STATE, "dynamics not set");
+        if (!l || !l[i]) return fail(g, HJI_E_INVALID, "l is NULL");
+        for (int a = 0; a < ndim; ++a)
+            if (g->n[a] < 2 * gw + 1)
+                return fail(g, HJI_E_INVALID, "grid too small for the scheme's stencil");
+        if (o->init == HJI_INIT_USER_K && (!k || !k[i]))
+            return fail(g, HJI_E_INVALID, "HJI_INIT_USER_K needs k");
+        if (o->init == HJI_INIT_RESIDENT && !g->has_value)
+            return fail(g, HJI_E_STATE, "HJI_INIT_RESIDENT without a previous value");
+        for (int j = 0; j < i; ++j)
+            if (grids[j] == g) return fail(g0, HJI_E_INVALID, "grid listed twice in a batch");
+        st = ensure_buffers(g, o->rk_order, s);
+        if (st != HJI_OK) return st;
+    }
+    const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+
+    // Batch-wide device scratch: descriptors, tile list, active counter.
+    std::vector<InstDesc> H(count);
+    InstDesc* d_desc = g0->d_desc;
+    int* d_active = g0->d_active;
+    unsigned long long* d_tiles = nullptr;
+    int* d_ntiles = g0->d_ntiles;
+    bool own_batch = count > 1;
+    long long total_tiles = 0;
+    for (int i = 0; i < count; ++i) {
+        long long tx, ty, planes;
+        tile_grid(ndim, grids[i]->n, tx, ty, planes);
+        total_tiles += tx * ty * planes;
+    }
+    if (total_tiles >= (1ll << 31)) return fail(g0, HJI_E_INVALID, "too many tiles");
+    if (own_batch) {
+        d_desc = (InstDesc*)dev_alloc(g0, sizeof(InstDesc) * count, s);
+        d_active = (int*)dev_alloc(g0, sizeof(int) * 2, s);
+        d_tiles = (unsigned long long*)dev_alloc(g0, sizeof(unsigned long long) * total_tiles, s);
+        if (!d_desc || !d_active || !d_tiles) {
+            dev_free(g0, d_desc, s);
+            dev_free(g0, d_active, s);
+            dev_free(g0, d_tiles, s);
+            return fail(g0, HJI_E_NOMEM, "batch scratch allocation failed");
+        }
+        d_ntiles = d_active + 1;
+    } else {
+        if (g0->tiles_cap < (size_t)total_tiles) {
+            dev_free(g0, g0->d_tiles, s);
+            g0->d_tiles = (unsigned long long*)dev_alloc(g0, sizeof(unsigned long long) * total_tiles, s);
+            if (!g0->d_tiles) {
+                g0->tiles_cap = 0;
+                return fail(g0, HJI_E_NOMEM, "tile list allocation failed");
+            }
+            g0->tiles_cap = (size_t)total_tiles;
+            if (g0->graph) {
+                cudaGraphExecDestroy(g0->graph);
+                g0->graph = nullptr;
+            }
+        }
+        d_tiles = g0->d_tiles;
+    }
+    auto cleanup = [&]() {
+        if (own_batch) {
+            dev_free(g0, d_desc, s);
+            dev_free(g0, d_active, s);
+            dev_free(g0, d_tiles, s);
+        }
+    };
+
+    std::vector<const void*> kptr(count, nullptr);
+    std::vector<unsigned long long> tiles;
+    tiles.reserve((size_t)total_tiles);
+    for (int i = 0; i < count; ++i) {
+        hji_grid g = grids[i];
+        const size_t bytes = (size_t)g->ncells * g->esize;
+        cudaError_t e = cudaMemcpyAsync(g->l, l[i], bytes, kind, s);
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_fail(g, e, "copy of l");
+        }
+        if (o->init == HJI_INIT_USER_K) {
+            if (ptr_is_device) {
+                kptr[i] = k[i];
+            } else {
+                e = cudaMemcpyAsync(g->V[1], k[i], bytes, cudaMemcpyHostToDevice, s);
+                if (e != cudaSuccess) {
+                    cleanup();
+                    return cuda_fail(g, e, "copy of k");
+                }
+                kptr[i] = g->V[1];
+            }
+        } else if (o->init == HJI_INIT_RESIDENT) {
+            kptr[i] = g->V[g->cur];
+        }
+        H[i] = make_desc(g, o, d_active);
+        for (long long t = 0; t < H[i].ntiles; ++t) tiles.push_back(hji::make_tile(i, t));
+        e = cudaMemsetAsync(g->state, 0, sizeof(InstState), s);
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_fail(g, e, "state reset");
+        }
+    }
+    int counts[2] = {count, (int)total_tiles};
+    cudaError_t e = cudaMemcpyAsync(d_desc, H.data(), sizeof(InstDesc) * count, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(unsigned long long) * total_tiles,
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_active, &counts[0], sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ntiles, &counts[1], sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = hji::launch_setup(d_desc, H.data(), count, f32, s);
+    if (e == cudaSuccess) e = hji::launch_init(d_desc, H.data(), count, f32, kptr.data(), s);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(g0, e, "set-up");
+    }
+    // One sync after set-up: reject NaN/Inf inputs and dynamics without a finite dt.
+    for (int i = 0; i < count; ++i) {
+        e = cudaMemcpyAsync(&grids[i]->h_state[0], grids[i]->state, sizeof(InstState),
+                            cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(g0, e, "set-up sync");
+    }
+    for (int i = 0; i < count; ++i) {
+        const InstState& S = grids[i]->h_state[0];
+        if (S.nonfinite) {
+            cleanup();
+            return fail(grids[i], HJI_E_INVALID, "l or k contains NaN or Inf");
+        }
+        if (S.status == 2) {
+            cleanup();
+            return fail(grids[i], HJI_E_INVALID, "dynamics vanish on the grid: no finite CFL step");
+        }
+    }
+
+    // The march: graphs of `chunk` steps, one in flight ahead of the check.
+    const int chunk = o->check_every > 0 ? o->check_every : 32;
+    const int grid = stage_grid(f32, ndim, o->scheme, total_tiles);
+    hji::StageArgs base{d_desc, d_tiles, d_ntiles, 0, 0, 0.0, 0.0};
+    cudaGraphExec_t exec = nullptr;
+    const long long key[6] = {(long long)o->scheme, o->rk_order, chunk, grid, (long long)(uintptr_t)d_tiles,
+                              (long long)total_tiles};
+    if (!own_batch && g0->graph && std::memcmp(key, g0->graph_key, sizeof(key)) == 0) {
+        exec = g0->graph;
+    } else {
+        if (!own_batch && g0->graph) {
+            cudaGraphExecDestroy(g0->graph);
+            g0->graph = nullptr;
+        }
+        st = capture_chunk(g0, g0->cap_stream, f32, ndim, o->scheme, o->rk_order, chunk, base, grid, &exec);
+        if (st != HJI_OK) {
+            cleanup();
+            return st;
+        }
+        if (!own_batch) {
+            g0->graph = exec;
+            std::memcpy(g0->graph_key, key, sizeof(key));
+        }
+    }
+    int* h_active = g0->h_active;  // two pinned slots
+    cudaEvent_t ev[2];
+    cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+    e = cudaSuccess;
+    long long graphs = 0;
+    for (long long it = 0;; ++it) {
+        ++graphs;
+        e = cudaGraphLaunch(exec, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_active[it & 1], d_active, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[it & 1], s);
+        if (e != cudaSuccess) break;
+        if (it > 0) {
+            e = cudaEventSynchronize(ev[(it - 1) & 1]);
+            if (e != cudaSuccess) break;
+            if (h_active[(it - 1) & 1] <= 0) break;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (own_batch) cudaGraphExecDestroy(exec);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(g0, e, "march");
+    }
+    for (int i = 0; i < count; ++i) {
+        e = cudaMemcpyAsync(grids[i]->h_state, grids[i]->state, sizeof(InstState), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(g0, e, "final state");
+    const double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    hji_status result = HJI_OK;
+    for (int i = 0; i < count; ++i) {
+        hji_grid g = grids[i];
+        const InstState& S = *g->h_state;
+        g->cur = S.cur;
+        g->has_value = true;
+        hji_status si = HJI_OK;
+        if (S.status == 1) {
+            si = fail(g, HJI_E_NONFINITE, "the march produced NaN or Inf");
+        } else if (!S.converged) {
+            si = fail(g, HJI_E_NOT_CONVERGED, "stopped by the horizon or the step cap");
+        }
+        if (result == HJI_OK && si != HJI_OK) result = si;
+        if (stats) {
+            hji_solve_stats& o_ = stats[i];
+            o_.steps = S.steps;
+            o_.tau = S.tau;
+            o_.dt = S.dt;
+            o_.final_max_dV = S.last_delta;
+            o_.wall_ms = wall;
+            for (int a = 0; a < HJI_MAX_DIM; ++a) o_.alpha[a] = a < g->ndim ? S.alpha[a] : 0.0;
+            o_.converged = S.converged;
+            long long setup = 0;
+            for (int j = 0; j < count; ++j) setup += 2 + (grids[j]->dyn.nterms > 0 ? 1 : 0);
+            o_.kernel_launches = setup + graphs * (long long)chunk * o->rk_order;
+        }
+    }
+    return result;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hji_status_string(hji_status s) {
+    switch (s) {
+        case HJI_OK: return "ok";
+        case HJI_E_INVALID: return "invalid argument";
+        case HJI_E_NOMEM: return "out of device memory";
+        case HJI_E_CUDA: return "CUDA error";
+        case HJI_E_NOT_CONVERGED: return "not converged";
+        case HJI_E_TIMEOUT: return "timeout";
+        case HJI_E_STATE: return "call out of order";
+        case HJI_E_NONFINITE: return "non-finite value";
+    }
+    return "unknown status";
+}
+
+const char* hji_last_error(hji_grid g) { return g ? g->err.c_str() : g_create_error.c_str(); }
+
+hji_status hji_grid_create(int ndim, const int64_t* n, const double* lo, const double* hi,
+                           const int* periodic, hji_precision prec, const hji_allocator* alloc,
+                           hji_grid* out) {
+    if (!out) return fail(nullptr, HJI_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (ndim < 1 || ndim > HJI_MAX_DIM) return fail(nullptr, HJI_E_INVALID, "ndim must be 1..4");
+    if (!n || !lo || !hi) return fail(nullptr, HJI_E_INVALID, "n, lo, hi must not be NULL");
+    if (prec != HJI_F64 && prec != HJI_F32) return fail(nullptr, HJI_E_INVALID, "unknown precision");
+    if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, HJI_E_INVALID, "allocator lacks alloc/free");
+    int64_t total = 1;
+    for (int a = 0; a < ndim; ++a) {
+        if (n[a] < 3) return fail(nullptr, HJI_E_INVALID, "every axis needs at least 3 nodes");
+        if (!std::isfinite(lo[a]) || !std::isfinite(hi[a]) || !(hi[a] > lo[a]))
+            return fail(nullptr, HJI_E_INVALID, "bounds must be finite with hi > lo");
+        total *= n[a];
+        if (total > 2147483647ll) return fail(nullptr, HJI_E_INVALID, "grid too large (max 2^31-1 nodes)");
+    }
+    hji_grid g = new (std::nothrow) hji_grid_s();
+    if (!g) return fail(nullptr, HJI_E_NOMEM, "host allocation failed");
+    g->ndim = ndim;
+    for (int a = 0; a < ndim; ++a) {
+        g->n[a] = n[a];
+        g->lo[a] = lo[a];
+        g->hi[a] = hi[a];
+        g->periodic[a] = periodic ? (periodic[a] != 0) : 0;
+        g->dx[a] = g->periodic[a] ? (hi[a] - lo[a]) / (double)n[a] : (hi[a] - lo[a]) / (double)(n[a] - 1);
+    }
+    g->prec = prec;
+    g->esize = prec == HJI_F32 ? 4 : 8;
+    g->ncells = total;
+    cudaGetDevice(&g->device);
+    if (alloc) {
+        g->has_alloc = true;
+        g->alloc = *alloc;
+    }
+    cudaStream_t s = nullptr;
+    const size_t bytes = (size_t)total * g->esize;
+    g->V[0] = dev_alloc(g, bytes, s);
+    g->V[1] = dev_alloc(g, bytes, s);
+    g->l = dev_alloc(g, bytes, s);
+    if (prec == HJI_F32) g->Vlo = dev_alloc(g, bytes, s);
+    g->state = (InstState*)dev_alloc(g, sizeof(InstState), s);
+    g->d_desc = (InstDesc*)dev_alloc(g, sizeof(InstDesc), s);
+    g->d_active = (int*)dev_alloc(g, sizeof(int) * 2, s);
+    bool ok = g->V[0] && g->V[1] && g->l && g->state && g->d_desc && g->d_active &&
+              (prec != HJI_F32 || g->Vlo);
+    g->d_ntiles = ok ? g->d_active + 1 : nullptr;
+    if (ok && cudaMallocHost(&g->h_state, sizeof(InstState) * 2) != cudaSuccess) ok = false;
+    if (ok && cudaMallocHost(&g->h_active, sizeof(int) * 2) != cudaSuccess) ok = false;
+    if (ok && cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) != cudaSuccess) ok = false;
+    if (ok && cudaStreamSynchronize(s) != cudaSuccess) ok = false;
+    if (!ok) {
+        cudaGetLastError();
+        hji_grid_destroy(g);
+        return fail(nullptr, HJI_E_NOMEM, "device allocation failed");
+    }
+    *out = g;
+    return HJI_OK;
+}
+
+hji_status hji_grid_destroy(hji_grid g) {
+    if (!g) return HJI_OK;
+    cudaStream_t s = nullptr;
+    cudaStreamSynchronize(s);
+    if (g->graph) cudaGraphExecDestroy(g->graph);
+    void* bufs[] = {g->V[0], g->V[1], g->W1, g->W2, g->Vlo, g->l, g->table, g->state,
+                    g->d_desc, g->d_active, g->d_tiles};
+    for (void* p : bufs) dev_free(g, p, s);
+    if (g->h_state) cudaFreeHost(g->h_state);
+    if (g->h_active) cudaFreeHost(g->h_active);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    cudaStreamSynchronize(s);
+    delete g;
+    return HJI_OK;
+}
+
+hji_status hji_dynamics_set(hji_grid g, const hji_dynamics* d) {
+    if (!g) return fail(nullptr, HJI_E_INVALID, "grid is NULL");
+    if (!d) return fail(g, HJI_E_INVALID, "dynamics is NULL");
+    const int n = g->ndim;
+    if (d->m < 0 || d->m > HJI_MAX_INPUTS || d->q < 0 || d->q > HJI_MAX_INPUTS)
+        return fail(g, HJI_E_INVALID, "m and q must be in 0..4");
+    if (d->nterms < 0 || d->nterms > HJI_MAX_TERMS) return fail(g, HJI_E_INVALID, "nterms must be in 0..8");
+    if (d->m > 0 && (!d->G || !d->ulo || !d->uhi)) return fail(g, HJI_E_INVALID, "m > 0 needs G, ulo, uhi");
+    if (d->q > 0 && (!d->E || !d->dlo || !d->dhi)) return fail(g, HJI_E_INVALID, "q > 0 needs E, dlo, dhi");
+    if (d->nterms > 0 && (!d->term_row || !d->term_axis || !d->term_fn || !d->term_w))
+        return fail(g, HJI_E_INVALID, "nterms > 0 needs the term arrays");
+    hji::Dyn D;
+    std::memset(&D, 0, sizeof(D));
+    D.m = d->m;
+    D.q = d->q;
+    D.nterms = d->nterms;
+    for (int i = 0; i < n; ++i) {
+        D.c[i] = d->c ? d->c[i] : 0.0;
+        for (int j = 0; j < n; ++j) D.A[i * HJI_MAX_DIM + j] = d->A ? d->A[i * n + j] : 0.0;
+        for (int j = 0; j < d->m; ++j) D.G[i * HJI_MAX_INPUTS + j] = d->G[i * d->m + j];
+        for (int j = 0; j < d->q; ++j) D.E[i * HJI_MAX_INPUTS + j] = d->E[i * d->q + j];
+    }
+    for (int j = 0; j < d->m; ++j) {
+        D.ulo[j] = d->ulo[j];
+        D.uhi[j] = d->uhi[j];
+        if (!(D.ulo[j] <= D.uhi[j])) return fail(g, HJI_E_INVALID, "ulo > uhi");
+    }
+    for (int j = 0; j < d->q; ++j) {
+        D.dlo[j] = d->dlo[j];
+        D.dhi[j] = d->dhi[j];
+        if (!(D.dlo[j] <= D.dhi[j])) return fail(g, HJI_E_INVALID, "dlo > dhi");
+    }
+    for (int t = 0; t < d->nterms; ++t) {
+        if (d->term_row[t] < 0 || d->term_row[t] >= n || d->term_axis[t] < 0 || d->term_axis[t] >= n)
+            return fail(g, HJI_E_INVALID, "term row/axis out of range");
+        if (d->term_fn[t] < HJI_FN_TAN || d->term_fn[t] > HJI_FN_COS)
+            return fail(g, HJI_E_INVALID, "unknown term function");
+        D.term_row[t] = d->term_row[t];
+        D.term_axis[t] = d->term_axis[t];
+        D.term_fn[t] = d->term_fn[t];
+        D.term_w[t] = d->term_w[t];
+    }
+    const double* arrs[] = {D.c, D.A, D.G, D.E, D.ulo, D.uhi, D.dlo, D.dhi, D.term_w};
+    const int lens[] = {HJI_MAX_DIM, HJI_MAX_DIM * HJI_MAX_DIM, HJI_MAX_DIM * HJI_MAX_INPUTS,
+                        HJI_MAX_DIM * HJI_MAX_INPUTS, HJI_MAX_INPUTS, HJI_MAX_INPUTS, HJI_MAX_INPUTS,
+                        HJI_MAX_INPUTS, HJI_MAX_TERMS};
+    for (int i = 0; i < 9; ++i)
+        if (!finite_all(arrs[i], lens[i])) return fail(g, HJI_E_INVALID, "dynamics contain NaN or Inf");
+    g->dyn = D;
+    g->has_dyn = true;
+    return HJI_OK;
+}
+
+hji_status hji_solve(hji_grid g, const void* l, const void* k, int ptr_is_device,
+                     const hji_solve_opts* o, void* cuda_stream, hji_solve_stats* stats) {
+    if (!g) return fail(nullptr, HJI_E_INVALID, "grid is NULL");
+    const void* la[1] = {l};
+    const void* ka[1] = {k};
+    return run(1, &g, la, ka, ptr_is_device, o, (cudaStream_t)cuda_stream, stats);
+}
+
+hji_status hji_batch_solve(int count, hji_grid* grids, const void* const* l, const void* const* k,
+                           int ptr_is_device, const hji_solve_opts* o, void* cuda_stream,
+                           hji_solve_stats* stats) {
+    if (count < 1 || count > 65535 || !grids) return fail(nullptr, HJI_E_INVALID, "count must be 1..65535");
+    if (!grids[0]) return fail(nullptr, HJI_E_INVALID, "NULL grid in batch");
+    return run(count, grids, l, k, ptr_is_device, o, (cudaStream_t)cuda_stream, stats);
+}
+
+hji_status hji_value_get(hji_grid g, void* out, int ptr_is_device, void* cuda_stream) {
+    if (!g) return fail(nullptr, HJI_E_INVALID, "grid is NULL");
+    if (!out) return fail(g, HJI_E_INVALID, "out is NULL");
+    if (!g->has_value) return fail(g, HJI_E_STATE, "no value yet: call hji_solve first");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t bytes = (size_t)g->ncells * g->esize;
+    HJI_CUDA(g, cudaMemcpyAsync(out, g->V[g->cur], bytes,
+                                ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    HJI_CUDA(g, cudaStreamSynchronize(s));
+    return HJI_OK;
+}
+
+hji_status hji_grid_info(hji_grid g, int* ndim, int64_t* n, int64_t* num_nodes) {
+    if (!g) return fail(nullptr, HJI_E_INVALID, "grid is NULL");
+    if (ndim) *ndim = g->ndim;
+    if (n)
+        for (int a = 0; a < g->ndim; ++a) n[a] = g->n[a];
+    if (num_nodes) *num_nodes = g->ncells;
+    return HJI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// Internal device-side data structures of the HJI reachability solver.
+//
+// One "instance" is one grid with its dynamics, value buffers and march state.
+// Every kernel works on a batch of instances through a flat tile list, so a
+// single grid is a batch of one and uneven grids share one launch.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hji.h"
+
+namespace hji {
+
+constexpr int MAXD = HJI_MAX_DIM;
+constexpr int MAXU = HJI_MAX_INPUTS;
+constexpr int MAXT = HJI_MAX_TERMS;
+constexpr int kThreads = 256;  // every stencil kernel uses 256-thread CTAs
+
+// Dynamics f(x,u,d) = c + A x + sum_t w_t phi_t(x[axis_t]) e_{row_t} + G u + E d
+// (Sec. II-A, Eq. (1), control-affine form), stored dense at the maximum
+// sizes so the kernels index with compile-time strides.
+struct Dyn {
+    int m, q, nterms, pad_;
+    double c[MAXD];
+    double A[MAXD * MAXD];  // A[i*MAXD + j]
+    double G[MAXD * MAXU];  // G[i*MAXU + j]
+    double E[MAXD * MAXU];  // E[i*MAXU + k]
+    double ulo[MAXU], uhi[MAXU], dlo[MAXU], dhi[MAXU];
+    double term_w[MAXT];
+    int term_row[MAXT], term_axis[MAXT], term_fn[MAXT];
+};
+
+// Mutable march state of one instance (device memory, written by kernels).
+struct InstState {
+    unsigned long long delta_bits;  // max|dV| of the step in flight (bits of a double >= 0)
+    unsigned int tiles_done;        // tiles of the step's last stage finished so far
+    int cur;                        // index (0/1) of the buffer holding V^n
+    int stop;                       // 1 once converged, capped or failed
+    int converged;                  // 1 if max|dV| < tol ended the march
+    int status;                     // 0 ok, 1 non-finite value, 2 no finite dt, 3 bad input
+    int pad_;
+    long long steps;                // full steps taken
+    double tau;                     // steps * dt, accumulated in FP64
+    double last_delta;              // max|dV| of the last finished step
+    // set-up reductions (alpha, CFL rate) for this solve
+    unsigned long long alpha_bits[MAXD];
+    unsigned long long rate_bits;
+    unsigned int setup_done;
+    unsigned int nonfinite;         // set by the init pass if l or k has NaN/Inf
+    double dt;
+    double alpha[MAXD];
+};
+
+// Read-only description of one instance for one solve.
+struct InstDesc {
+    int ndim;
+    int periodic[MAXD];
+    int n[MAXD];
+    long long stride[MAXD];   // element strides, C order
+    long long ncells;
+    double lo[MAXD], dx[MAXD];
+    Dyn dyn;
+    double cfl, tol, horizon;
+    long long max_steps;
+    void* V[2];               // ping-pong value buffers: V[cur] = V^n
+    void* W1;                 // stage buffers of the Runge-Kutta step: stage
+    void* W2;                 // states (FP64) or stage increments (FP32)
+    void* Vlo;                // FP32 only: low word of V = V[cur] + Vlo
+    void* l;                  // target function l(x)
+    void* table;              // per-term tables: table[t*n_max + i] = w_t phi_t(x_axis(i))
+    long long table_stride;
+    double* history;          // optional max|dV| per step (FP64), may be null
+    long long history_len;
+    long long tiles_x, tiles_y, tiles_per_plane, ntiles;  // tile grid of this instance
+    InstState* state;
+    int* active;              // batch-wide count of instances still marching (may be null)
+};
+
+// Tile list entry: instance index in the high 16 bits, tile index within the
+// instance in the low 48 bits.
+__host__ __device__ inline unsigned long long make_tile(int inst, long long local) {
+    return (static_cast<unsigned long long>(inst) << 48) |
+           (static_cast<unsigned long long>(local) & 0xFFFFFFFFFFFFull);
+}
+
+// Tile shape per dimensionality: 1-D tiles are 256 nodes of one row; N-D
+// tiles are 16 x 32 nodes of the two fastest axes at a fixed index of the
+// slower axes (which are read from global memory / L2 directly).
+template <int NDIM>
+struct TileShape {
+    static constexpr int TY = (NDIM == 1) ? 1 : 16;
+    static constexpr int TX = (NDIM == 1) ? 256 : 32;
+};
+
+inline int ghost_width(int scheme) { return scheme == HJI_ENO1 ? 1 : (scheme == HJI_ENO2 ? 2 : 3); }
+
+// Arguments of one Runge-Kutta stage launch.
+//
+// FP64 grids store stage states: the stencil input is W = V^n, W1 or W2 and
+// the stage writes aV V^n + aE (W + dt L(W)).
+// FP32 grids store stage increments D = W - V^n (small numbers keep full
+// relative precision) and V^n as an unevaluated sum hi + lo of two floats:
+// the stencil input is W = hi + D_in, a stage writes
+// D_out = aE (D_in + dt L(W)), and the last stage adds its increment to
+// (hi, lo) with an error-free two-sum.  Both are the same Runge-Kutta step:
+// aV + aE = 1 gives aV V + aE (W + dt L) = V + aE (D_in + dt L).
+struct StageArgs {
+    const InstDesc* insts;
+    const unsigned long long* tiles;
+    const int* ntiles;     // device scalar: tiles in the list
+    int stage_in;          // 0: V[cur], 1: W1/D1, 2: W2/D2 (stencil input)
+    int stage_out;         // 1: W1/D1, 2: W2/D2, 3: V[cur^1]
+    double aV, aE;
+};
+
+using StageLauncher = cudaError_t (*)(const StageArgs&, int grid, cudaStream_t);
+
+// Kernel dispatch tables (one per precision).
+StageLauncher stage_launcher_f64(int ndim, int scheme, bool last);
+StageLauncher stage_launcher_f32(int ndim, int scheme, bool last);
+int stage_max_blocks_f64(int ndim, int scheme, bool last);
+int stage_max_blocks_f32(int ndim, int scheme, bool last);
+
+// Set-up kernels (hji_setup.cu).
+cudaError_t launch_setup(const InstDesc* d_insts, const InstDesc* h_insts, int count, bool f32,
+                         cudaStream_t s);
+cudaError_t launch_init(const InstDesc* d_insts, const InstDesc* h_insts, int count, bool f32,
+                        const void* const* k, cudaStream_t s);
+
+}  // namespace hji

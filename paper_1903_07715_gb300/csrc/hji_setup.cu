@@ -1,0 +1,168 @@
+// Per-solve set-up passes, run once before the march:
+//   * term tables: w_t phi_t(x_axis) per node of the term's axis, so the
+//     stage kernel evaluates tan/sin/cos terms by a table read;
+//   * dissipation coefficients and CFL step: alpha_a = max over nodes of
+//     max_{u,d} |f_a(x,u,d)| and dt = cfl / max over nodes of
+//     sum_a max_{u,d}|f_a| / dx_a, reduced in FP64 (warp shuffle -> CTA ->
+//     64-bit atomics; the last CTA turns the maxima into dt);
+//   * initial value: V = l (Sec. II-B) or V = min(k, l) (Sec. III, proof of
+//     Thm. 1), flagging NaN/Inf in l or k.
+#include <cfloat>
+
+#include "hji_common.cuh"
+
+namespace hji {
+
+__device__ __forceinline__ double apply_fn(int fn, double x) {
+    if (fn == HJI_FN_TAN) return tan(x);
+    if (fn == HJI_FN_SIN) return sin(x);
+    return cos(x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) table_kernel(const InstDesc* __restrict__ d) {
+    const InstDesc& D = *d;
+    T* table = static_cast<T*>(D.table);
+    for (int t = blockIdx.y; t < D.dyn.nterms; t += gridDim.y) {
+        const int ax = D.dyn.term_axis[t];
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.n[ax];
+             i += gridDim.x * blockDim.x) {
+            const double x = D.lo[ax] + (double)i * D.dx[ax];
+            table[t * D.table_stride + i] = T(D.dyn.term_w[t] * apply_fn(D.dyn.term_fn[t], x));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) alpha_kernel(const InstDesc* __restrict__ d) {
+    const InstDesc& D = *d;
+    const int nd = D.ndim;
+    const Dyn& f = D.dyn;
+    double amax[MAXD] = {0.0, 0.0, 0.0, 0.0};
+    double rmax = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < D.ncells;
+         c += (long long)gridDim.x * blockDim.x) {
+        double x[MAXD];
+        long long r = c;
+        for (int a = nd - 1; a >= 0; --a) {
+            const long long i = r % D.n[a];
+            r /= D.n[a];
+            x[a] = D.lo[a] + (double)i * D.dx[a];
+        }
+        double rate = 0.0;
+        for (int a = 0; a < nd; ++a) {
+            // f_a is affine in (u, d): its range over the boxes is
+            // centre +- radius, so max |f_a| = |centre| + radius.
+            double centre = f.c[a], radius = 0.0;
+            for (int b = 0; b < nd; ++b) centre += f.A[a * MAXD + b] * x[b];
+            for (int t = 0; t < f.nterms; ++t)
+                if (f.term_row[t] == a) centre += f.term_w[t] * apply_fn(f.term_fn[t], x[f.term_axis[t]]);
+            for (int j = 0; j < f.m; ++j) {
+                centre += f.G[a * MAXU + j] * (0.5 * (f.ulo[j] + f.uhi[j]));
+                radius += fabs(f.G[a * MAXU + j]) * (0.5 * (f.uhi[j] - f.ulo[j]));
+            }
+            for (int k = 0; k < f.q; ++k) {
+                centre += f.E[a * MAXU + k] * (0.5 * (f.dlo[k] + f.dhi[k]));
+                radius += fabs(f.E[a * MAXU + k]) * (0.5 * (f.dhi[k] - f.dlo[k]));
+            }
+            const double al = fabs(centre) + radius;
+            amax[a] = fmax(amax[a], al);
+            rate += al / D.dx[a];
+        }
+        rmax = fmax(rmax, rate);
+    }
+    __shared__ double red[kThreads / 32][MAXD + 1];
+    for (int a = 0; a <= MAXD; ++a) {
+        double v = a < MAXD ? amax[a] : rmax;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][a] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        InstState* st = D.state;
+        for (int a = 0; a <= MAXD; ++a) {
+            double v = red[0][a];
+            for (int w = 1; w < kThreads / 32; ++w) v = fmax(v, red[w][a]);
+            unsigned long long* dst = a < MAXD ? &st->alpha_bits[a] : &st->rate_bits;
+            atomicMax(dst, static_cast<unsigned long long>(__double_as_longlong(v)));
+        }
+        __threadfence();
+        if (atomicAdd(&st->setup_done, 1u) + 1 == gridDim.x) {
+            __threadfence();
+            for (int a = 0; a < MAXD; ++a)
+                st->alpha[a] = __longlong_as_double((long long)atomicAdd(&st->alpha_bits[a], 0ull));
+            const double rate = __longlong_as_double((long long)atomicAdd(&st->rate_bits, 0ull));
+            if (rate > 0.0 && rate <= DBL_MAX) {
+                st->dt = D.cfl / rate;
+            } else {
+                st->dt = 0.0;
+                st->status = 2;
+                st->stop = 1;
+            }
+            __threadfence();
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    init_kernel(const InstDesc* __restrict__ d, const T* __restrict__ k) {
+    const InstDesc& D = *d;
+    const T* l = static_cast<const T*>(D.l);
+    T* V = static_cast<T*>(D.V[0]);
+    T* Vlo = static_cast<T*>(D.Vlo);  // FP32 grids: low word of V starts at zero
+    unsigned int bad = 0u;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < D.ncells;
+         c += (long long)gridDim.x * blockDim.x) {
+        const T lv = l[c];
+        T v = lv;
+        if (!isfinite(lv)) bad = 1u;
+        if (k != nullptr) {
+            const T kv = k[c];
+            if (!isfinite(kv)) bad = 1u;
+            v = kv < lv ? kv : lv;
+        }
+        V[c] = v;
+        if (Vlo != nullptr) Vlo[c] = T(0);
+    }
+    bad = __any_sync(0xffffffffu, bad) ? 1u : 0u;
+    if (bad && (threadIdx.x & 31) == 0) atomicOr(&D.state->nonfinite, 1u);
+}
+
+static int grid_for(long long work, int cap) {
+    long long b = (work + kThreads - 1) / kThreads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return static_cast<int>(b);
+}
+
+cudaError_t launch_setup(const InstDesc* d_insts, const InstDesc* h_insts, int count, bool f32,
+                         cudaStream_t s) {
+    for (int i = 0; i < count; ++i) {
+        const InstDesc& H = h_insts[i];
+        if (H.dyn.nterms > 0) {
+            long long nmax = 0;
+            for (int a = 0; a < H.ndim; ++a) nmax = H.n[a] > nmax ? H.n[a] : nmax;
+            dim3 grid(grid_for(nmax, 64), H.dyn.nterms);
+            if (f32)
+                table_kernel<float><<<grid, kThreads, 0, s>>>(d_insts + i);
+            else
+                table_kernel<double><<<grid, kThreads, 0, s>>>(d_insts + i);
+        }
+        alpha_kernel<<<grid_for(H.ncells, 1024), kThreads, 0, s>>>(d_insts + i);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const InstDesc* d_insts, const InstDesc* h_insts, int count, bool f32,
+                        const void* const* k, cudaStream_t s) {
+    for (int i = 0; i < count; ++i) {
+        const int g = grid_for(h_insts[i].ncells, 4096);
+        if (f32)
+            init_kernel<float><<<g, kThreads, 0, s>>>(d_insts + i, static_cast<const float*>(k[i]));
+        else
+            init_kernel<double><<<g, kThreads, 0, s>>>(d_insts + i, static_cast<const double*>(k[i]));
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace hji

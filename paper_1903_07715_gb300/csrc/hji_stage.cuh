@@ -1,0 +1,492 @@
+// The fused Runge-Kutta stage kernel: one launch advances one stage of every
+// live instance in the batch.  Per tile of nodes it
+//   1. stages the stencil input W (tile + ghost halo of the two fastest axes)
+//      in shared memory, building ghost nodes beyond the grid edge by linear
+//      extrapolation (or periodic wrap) while loading;
+//   2. forms the one-sided derivatives p-, p+ along every axis (ENO1, ENO2 or
+//      HJ-WENO5; slower axes read their stencil lines from L2 directly);
+//   3. evaluates the closed-form control-affine Hamiltonian of Eq. (6) at the
+//      averaged gradient plus the Lax-Friedrichs dissipation;
+//   4. combines the Euler stage W + dt L(W) with V^n (TVD Runge-Kutta);
+//   5. on the last stage applies min(., l) (Eq. (7)-(8)), reduces
+//      max|V^{n+1} - V^n| (warp shuffle -> CTA -> one 64-bit atomic), and the
+//      CTA finishing an instance's last tile advances that instance's step
+//      counter, tau, stop flag and buffer index.
+// Tiles of instances that have stopped are skipped, so launches queued after
+// convergence do no work and no step past the stop point ever runs.
+#pragma once
+
+#include <cfloat>
+
+#include "hji_common.cuh"
+
+namespace hji {
+
+template <typename T>
+struct Num;
+template <>
+struct Num<double> {
+    static __device__ __forceinline__ double weno_tiny() { return 1e-60; }
+};
+template <>
+struct Num<float> {
+    static __device__ __forceinline__ float weno_tiny() { return 1e-6f; }  // after normalising
+};
+
+template <int SCHEME>
+struct Ghost {
+    static constexpr int G = SCHEME == HJI_ENO1 ? 1 : (SCHEME == HJI_ENO2 ? 2 : 3);
+};
+
+// Of two second differences the one of smaller magnitude; a tie keeps the
+// lower-index one.  The comparison is made on undivided differences, which
+// selects exactly as comparing Q = S / (2 dx) would.
+template <typename T>
+__device__ __forceinline__ T smaller_mag(T a, T b) {
+    return fabs(a) <= fabs(b) ? a : b;
+}
+
+// HJ-WENO5 (Jiang and Peng) on undivided one-sided differences v1..v5.  The
+// nonlinear weights d_k / (S_k + eps)^2, normalised, are formed as
+// d_k q_k / sum_j d_j q_j with q_1 = (b2 b3)^2, q_2 = (b1 b3)^2,
+// q_3 = (b1 b2)^2, b_k = S_k + eps (the same ratios with one division).
+// eps = 1e-6 max(v^2) + tiny as in the textbook form; in FP32 the differences
+// are first scaled by 1/max|v| so that the products stay in range.
+template <typename T>
+__device__ __forceinline__ T weno5(T v1, T v2, T v3, T v4, T v5) {
+    T scale = T(1);
+    if constexpr (sizeof(T) == 4) {
+        T M = fmaxf(fmaxf(fmaxf(fabsf(v1), fabsf(v2)), fmaxf(fabsf(v3), fabsf(v4))), fabsf(v5));
+        if (M == 0.0f) return 0.0f;
+        T r = 1.0f / M;
+        v1 *= r; v2 *= r; v3 *= r; v4 *= r; v5 *= r;
+        scale = M;
+    }
+    const T phi1 = v1 * T(1.0 / 3.0) - v2 * T(7.0 / 6.0) + v3 * T(11.0 / 6.0);
+    const T phi2 = -v2 * T(1.0 / 6.0) + v3 * T(5.0 / 6.0) + v4 * T(1.0 / 3.0);
+    const T phi3 = v3 * T(1.0 / 3.0) + v4 * T(5.0 / 6.0) - v5 * T(1.0 / 6.0);
+    const T a = v1 - T(2) * v2 + v3, b = v1 - T(4) * v2 + T(3) * v3;
+    const T c = v2 - T(2) * v3 + v4, d = v2 - v4;
+    const T e = v3 - T(2) * v4 + v5, f = T(3) * v3 - T(4) * v4 + v5;
+    const T s1 = T(13.0 / 12.0) * a * a + T(0.25) * b * b;
+    const T s2 = T(13.0 / 12.0) * c * c + T(0.25) * d * d;
+    const T s3 = T(13.0 / 12.0) * e * e + T(0.25) * f * f;
+    T eps;
+    if constexpr (sizeof(T) == 4) {
+        eps = Num<T>::weno_tiny();  // max(v^2) == 1 after scaling
+    } else {
+        T vm = fmax(fmax(fmax(v1 * v1, v2 * v2), fmax(v3 * v3, v4 * v4)), v5 * v5);
+        eps = T(1e-6) * vm + Num<T>::weno_tiny();
+    }
+    const T b1 = s1 + eps, b2 = s2 + eps, b3 = s3 + eps;
+    const T b12 = b1 * b2, b13 = b1 * b3, b23 = b2 * b3;
+    const T w1 = T(0.1) * (b23 * b23);
+    const T w2 = T(0.6) * (b13 * b13);
+    const T w3 = T(0.3) * (b12 * b12);
+    const T num = w1 * phi1 + w2 * phi2 + w3 * phi3;
+    return scale * (num / (w1 + w2 + w3));
+}
+
+// (p-, p+) from a stencil line v[0..2G] centred at v[G].
+template <typename T, int SCHEME>
+__device__ __forceinline__ void one_sided(const T* v, T inv_dx, T& pm, T& pp) {
+    if constexpr (SCHEME == HJI_ENO1) {
+        pm = (v[1] - v[0]) * inv_dx;
+        pp = (v[2] - v[1]) * inv_dx;
+    } else if constexpr (SCHEME == HJI_ENO2) {
+        const T D0 = v[1] - v[0], D1 = v[2] - v[1], D2 = v[3] - v[2], D3 = v[4] - v[3];
+        const T Sm = D1 - D0, S0 = D2 - D1, Sp = D3 - D2;
+        pm = (D1 + T(0.5) * smaller_mag(Sm, S0)) * inv_dx;
+        pp = (D2 - T(0.5) * smaller_mag(S0, Sp)) * inv_dx;
+    } else {
+        const T D0 = v[1] - v[0], D1 = v[2] - v[1], D2 = v[3] - v[2];
+        const T D3 = v[4] - v[3], D4 = v[5] - v[4], D5 = v[6] - v[5];
+        pm = weno5<T>(D0, D1, D2, D3, D4) * inv_dx;
+        pp = weno5<T>(D5, D4, D3, D2, D1) * inv_dx;
+    }
+}
+
+// Stencil input at element offset i: v[i], plus the stage increment d[i]
+// when the grid stores increments (FP32); d is null otherwise.
+template <typename T>
+__device__ __forceinline__ T wval(const T* __restrict__ v, const T* __restrict__ d, long long i) {
+    T x = __ldg(v + i);
+    if (d != nullptr) x += __ldg(d + i);
+    return x;
+}
+
+// Value at node index j (possibly outside [0, n)) of a line with stride s
+// starting at element offset 0 of v (and d): periodic wrap, or linear
+// extrapolation from the two edge nodes.
+template <typename T>
+__device__ __forceinline__ T line_value(const T* __restrict__ v, const T* __restrict__ d, int j,
+                                        int n, long long s, int periodic) {
+    if (j >= 0 && j < n) return wval(v, d, (long long)j * s);
+    if (periodic) {
+        int w = j % n;
+        if (w < 0) w += n;
+        return wval(v, d, (long long)w * s);
+    }
+    const bool low = j < 0;
+    const int k = low ? -j : j - (n - 1);
+    const T e = wval(v, d, (long long)(low ? 0 : n - 1) * s);
+    const T i1 = wval(v, d, (long long)(low ? 1 : n - 2) * s);
+    return e + T(k) * (e - i1);
+}
+
+// Shared-memory copy of what a tile needs from its instance, in precision T.
+template <typename T>
+struct TileCtx {
+    int inst;
+    int stop;
+    int cur;
+    int m, q, nterms;
+    int n[MAXD];
+    int periodic[MAXD];
+    long long stride[MAXD];
+    long long tiles_x, tiles_per_plane, ntiles;
+    T lo[MAXD], dx[MAXD], inv_dx[MAXD], half_alpha[MAXD];
+    T c[MAXD], A[MAXD * MAXD], G[MAXD * MAXU], E[MAXD * MAXU];
+    T ulo[MAXU], uhi[MAXU], dlo[MAXU], dhi[MAXU];
+    int term_row[MAXT], term_axis[MAXT];
+    T dt;
+    const T* win;   // stencil input (FP64: the stage state; FP32: V^n hi word)
+    const T* din;   // FP32: stage increment added to win (null for stage 1)
+    const T* vcur;
+    T* wout;
+    T* vlo;         // FP32: low word of V^n, updated in place by the last stage
+    const T* l;
+    const T* table;
+    long long table_stride;
+};
+
+// Fill the tile context; called by every thread of the CTA (each copies a
+// slice), followed by __syncthreads() at the call site.
+static_assert(MAXD == 4 && MAXU == 4 && MAXT == 8 && kThreads > 96,
+              "load_ctx hands out slices for these sizes");
+template <typename T>
+__device__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict__ insts, int inst,
+                         const StageArgs& a) {
+    const InstDesc& D = insts[inst];
+    const int t = threadIdx.x;
+    if (t < MAXD * MAXD) C.A[t] = T(D.dyn.A[t]);
+    else if (t < 32) C.G[t - 16] = T(D.dyn.G[t - 16]);
+    else if (t < 48) C.E[t - 32] = T(D.dyn.E[t - 32]);
+    else if (t < 52) C.ulo[t - 48] = T(D.dyn.ulo[t - 48]);
+    else if (t < 56) C.uhi[t - 52] = T(D.dyn.uhi[t - 52]);
+    else if (t < 60) C.dlo[t - 56] = T(D.dyn.dlo[t - 56]);
+    else if (t < 64) C.dhi[t - 60] = T(D.dyn.dhi[t - 60]);
+    else if (t < 72) {
+        C.term_row[t - 64] = D.dyn.term_row[t - 64];
+        C.term_axis[t - 64] = D.dyn.term_axis[t - 64];
+    } else if (t < 76) {
+        const int i = t - 72;
+        InstState* st = D.state;
+        C.n[i] = D.n[i];
+        C.periodic[i] = D.periodic[i];
+        C.stride[i] = D.stride[i];
+        C.lo[i] = T(D.lo[i]);
+        C.dx[i] = T(D.dx[i]);
+        C.inv_dx[i] = T(1.0 / D.dx[i]);
+        C.half_alpha[i] = T(0.5 * st->alpha[i]);
+        C.c[i] = T(D.dyn.c[i]);
+    } else if (t == 96) {
+        InstState* st = D.state;
+        const int cur = *((volatile int*)&st->cur);
+        C.inst = inst;
+        C.stop = *((volatile int*)&st->stop);
+        C.cur = cur;
+        C.m = D.dyn.m;
+        C.q = D.dyn.q;
+        C.nterms = D.dyn.nterms;
+        C.dt = T(*((volatile double*)&st->dt));
+        C.tiles_x = D.tiles_x;
+        C.tiles_per_plane = D.tiles_per_plane;
+        C.ntiles = D.ntiles;
+        const T* vc = static_cast<const T*>(D.V[cur]);
+        const T* stage =
+            a.stage_in == 0 ? nullptr : static_cast<const T*>(a.stage_in == 1 ? D.W1 : D.W2);
+        C.vcur = vc;
+        if constexpr (sizeof(T) == 4) {
+            C.win = vc;
+            C.din = stage;
+        } else {
+            C.win = stage ? stage : vc;
+            C.din = nullptr;
+        }
+        C.vlo = static_cast<T*>(D.Vlo);
+        C.wout = a.stage_out == 3 ? static_cast<T*>(D.V[cur ^ 1])
+                                  : static_cast<T*>(a.stage_out == 1 ? D.W1 : D.W2);
+        C.l = static_cast<const T*>(D.l);
+        C.table = static_cast<const T*>(D.table);
+        C.table_stride = D.table_stride;
+    }
+}
+
+// Finish one step of an instance: called by the single thread whose tile was
+// the instance's last one in this (last) stage.
+__device__ inline void finish_step(const InstDesc& D) {
+    InstState* st = D.state;
+    __threadfence();
+    const double d = __longlong_as_double((long long)atomicAdd(&st->delta_bits, 0ull));
+    const long long steps = st->steps + 1;
+    const double tau = st->tau + st->dt;
+    st->last_delta = d;
+    st->steps = steps;
+    st->tau = tau;
+    st->cur ^= 1;
+    if (D.history != nullptr && steps - 1 < D.history_len) D.history[steps - 1] = d;
+    st->delta_bits = 0ull;
+    st->tiles_done = 0u;
+    if (!(d <= DBL_MAX)) {  // NaN or Inf
+        st->status = 1;
+        st->stop = 1;
+    } else if (d < D.tol) {
+        st->converged = 1;
+        st->stop = 1;
+    } else if (D.horizon > 0.0 && tau >= D.horizon) {
+        st->stop = 1;
+    } else if (steps >= D.max_steps) {
+        st->stop = 1;
+    }
+    if (st->stop && D.active != nullptr) atomicSub(D.active, 1);
+    __threadfence();
+}
+
+template <typename T, int NDIM, int SCHEME, bool LAST>
+__global__ void __launch_bounds__(kThreads)
+    stage_kernel(const StageArgs a) {
+    constexpr int G = Ghost<SCHEME>::G;
+    constexpr int TY = TileShape<NDIM>::TY;
+    constexpr int TX = TileShape<NDIM>::TX;
+    constexpr int GY = (NDIM >= 2) ? G : 0;
+    constexpr int SW = TX + 2 * G;   // shared tile width
+    constexpr int SH = TY + 2 * GY;  // shared tile height
+    constexpr int ROWS_PER_PASS = kThreads / TX;
+    constexpr int CELLS = (TY + ROWS_PER_PASS - 1) / ROWS_PER_PASS;
+    constexpr int AX = NDIM - 1;  // fastest axis
+    constexpr int AY = NDIM >= 2 ? NDIM - 2 : 0;  // second fastest axis (used if NDIM >= 2)
+
+    constexpr bool INCR = sizeof(T) == 4;  // FP32: increments + compensated V
+    __shared__ TileCtx<T> C;
+    __shared__ T tile[SH * SW];
+    __shared__ double red[kThreads / 32];
+
+    const int ntiles = *a.ntiles;
+    const int tx = threadIdx.x % TX;
+    const int ty = threadIdx.x / TX;
+    int loaded = -1;
+
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const unsigned long long entry = a.tiles[t];
+        const int inst = static_cast<int>(entry >> 48);
+        const long long local = static_cast<long long>(entry & 0xFFFFFFFFFFFFull);
+        if (inst != loaded) {
+            __syncthreads();  // everyone is done with the previous context
+            load_ctx<T>(C, a.insts, inst, a);
+            __syncthreads();
+            loaded = inst;
+        }
+        if (C.stop) continue;  // uniform across the CTA
+
+        // Tile coordinates: plane index over the slow axes, then (by, bx).
+        const long long plane = local / C.tiles_per_plane;
+        const long long rem = local - plane * C.tiles_per_plane;
+        const int by = static_cast<int>(rem / C.tiles_x);
+        const int bx = static_cast<int>(rem - (long long)by * C.tiles_x);
+        int sidx[MAXD];  // slow-axis indices
+        long long base = 0;
+        {
+            long long p = plane;
+            for (int ax = NDIM - 3; ax >= 0; --ax) {
+                sidx[ax] = static_cast<int>(p % C.n[ax]);
+                p /= C.n[ax];
+                base += (long long)sidx[ax] * C.stride[ax];
+            }
+        }
+        const int nx = C.n[AX];
+        const int ny = NDIM >= 2 ? C.n[AY] : 1;
+        const long long sy = NDIM >= 2 ? C.stride[AY] : 0;
+        const int y0 = by * TY, x0 = bx * TX;
+        const T* __restrict__ win = C.win + base;
+        const T* __restrict__ din = C.din ? C.din + base : nullptr;
+
+        // 1. Stage the input tile with its ghost halo.
+        for (int s = threadIdx.x; s < SH * SW; s += kThreads) {
+            const int r = s / SW, cidx = s - r * SW;
+            const int gy = y0 - GY + r, gx = x0 - G + cidx;
+            const bool iny = (NDIM < 2) || (gy >= 0 && gy < ny);
+            const bool inx = gx >= 0 && gx < nx;
+            T v;
+            if (iny && inx) {
+                v = wval<T>(win, din, (long long)gy * sy + gx);
+            } else if (iny) {
+                const long long r0 = (long long)gy * sy;
+                v = line_value<T>(win + r0, din ? din + r0 : nullptr, gx, nx, 1, C.periodic[AX]);
+            } else if (inx) {
+                v = line_value<T>(win + gx, din ? din + gx : nullptr, gy, ny, sy, C.periodic[AY]);
+            } else {
+                v = T(0);  // corner of the halo: never used by an axis-aligned stencil
+            }
+            tile[s] = v;
+        }
+        __syncthreads();
+
+        // 2-5. Each thread updates CELLS nodes of the tile.
+        T dmax = T(0);
+#pragma unroll
+        for (int k = 0; k < CELLS; ++k) {
+            const int ry = ty + k * ROWS_PER_PASS;
+            const int gy = y0 + ry, gx = x0 + tx;
+            if (ry >= TY || gy >= ny || gx >= nx) continue;
+            T pm[NDIM], pp[NDIM];
+            T line[2 * G + 1];
+            const T* trow = tile + (ry + GY) * SW + (tx + G);
+#pragma unroll
+            for (int o = -G; o <= G; ++o) line[o + G] = trow[o];
+            const T wc = line[G];
+            one_sided<T, SCHEME>(line, C.inv_dx[AX], pm[AX], pp[AX]);
+            if constexpr (NDIM >= 2) {
+#pragma unroll
+                for (int o = -G; o <= G; ++o) line[o + G] = trow[o * SW];
+                one_sided<T, SCHEME>(line, C.inv_dx[AY], pm[AY], pp[AY]);
+            }
+            const long long off = (long long)gy * sy + gx;  // within the plane
+#pragma unroll
+            for (int ax = 0; ax < NDIM - 2; ++ax) {
+                const long long l0 = off - (long long)sidx[ax] * C.stride[ax];
+                const T* lp = win + l0;
+                const T* ld = din ? din + l0 : nullptr;
+#pragma unroll
+                for (int o = -G; o <= G; ++o)
+                    line[o + G] = line_value<T>(lp, ld, sidx[ax] + o, C.n[ax], C.stride[ax],
+                                                C.periodic[ax]);
+                one_sided<T, SCHEME>(line, C.inv_dx[ax], pm[ax], pp[ax]);
+            }
+            // Node coordinates and the drift f0(x) = c + A x + terms.
+            int idx[NDIM];
+#pragma unroll
+            for (int ax = 0; ax < NDIM - 2; ++ax) idx[ax] = sidx[ax];
+            if constexpr (NDIM >= 2) idx[AY] = gy;
+            idx[AX] = gx;
+            T x[NDIM], pbar[NDIM];
+#pragma unroll
+            for (int ax = 0; ax < NDIM; ++ax) {
+                x[ax] = C.lo[ax] + T(idx[ax]) * C.dx[ax];
+                pbar[ax] = T(0.5) * (pp[ax] + pm[ax]);
+            }
+            T h = T(0);
+#pragma unroll
+            for (int i = 0; i < NDIM; ++i) {
+                T fi = C.c[i];
+#pragma unroll
+                for (int j = 0; j < NDIM; ++j) fi += C.A[i * MAXD + j] * x[j];
+                h += pbar[i] * fi;
+            }
+            for (int tt = 0; tt < C.nterms; ++tt) {
+                const int ax = C.term_axis[tt];
+                h += pbar[C.term_row[tt]] * __ldg(C.table + tt * C.table_stride + idx[ax]);
+            }
+            // max_u <G^T p, u> and min_d <E^T p, d> over the boxes (Eq. (6)).
+            for (int j = 0; j < C.m; ++j) {
+                T s = T(0);
+#pragma unroll
+                for (int i = 0; i < NDIM; ++i) s += C.G[i * MAXU + j] * pbar[i];
+                h += fmax(s * C.ulo[j], s * C.uhi[j]);
+            }
+            for (int j = 0; j < C.q; ++j) {
+                T r = T(0);
+#pragma unroll
+                for (int i = 0; i < NDIM; ++i) r += C.E[i * MAXU + j] * pbar[i];
+                h += fmin(r * C.dlo[j], r * C.dhi[j]);
+            }
+            // Lax-Friedrichs: L = H(pbar) + sum alpha_a (p+ - p-) / 2.
+            T L = h;
+#pragma unroll
+            for (int ax = 0; ax < NDIM; ++ax) L += C.half_alpha[ax] * (pp[ax] - pm[ax]);
+            // Runge-Kutta stage combination.
+            const long long gidx = base + off;
+            if constexpr (INCR) {
+                const T dc = din ? __ldg(din + off) : T(0);
+                const T inc = T(a.aE) * (dc + C.dt * L);
+                if constexpr (!LAST) {
+                    C.wout[gidx] = inc;
+                } else {
+                    // V^n + inc as an unevaluated float pair (error-free
+                    // two-sum), then min(., l) of Eq. (7)-(8).
+                    const T hi = __ldg(C.vcur + gidx);
+                    const T lo = C.vlo[gidx];
+                    const T sl = lo + inc;
+                    T nh = hi + sl;
+                    const T bb = nh - hi;
+                    T nl = (hi - (nh - bb)) + (sl - bb);
+                    const T lv = __ldg(C.l + gidx);
+                    if (nh > lv || (nh == lv && nl > T(0))) {
+                        nh = lv;
+                        nl = T(0);
+                    }
+                    const T ch = fabs((nh - hi) + (nl - lo));
+                    dmax = (ch > dmax || ch != ch) ? ch : dmax;
+                    C.wout[gidx] = nh;
+                    C.vlo[gidx] = nl;
+                }
+            } else {
+                const T eul = wc + C.dt * L;
+                T out;
+                T vn = wc;
+                if (a.aV != 0.0) {
+                    vn = __ldg(C.vcur + gidx);
+                    out = T(a.aV) * vn + T(a.aE) * eul;
+                } else {
+                    out = eul;
+                }
+                if constexpr (LAST) {
+                    const T lv = __ldg(C.l + gidx);
+                    out = fmin(out, lv);
+                    const T ch = fabs(out - vn);
+                    dmax = (ch > dmax || ch != ch) ? ch : dmax;
+                }
+                C.wout[gidx] = out;
+            }
+        }
+
+        if constexpr (LAST) {
+            // CTA max of |dV| (NaN wins), then the instance-wide reduction.
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T other = __shfl_xor_sync(0xffffffffu, dmax, o);
+                dmax = (other > dmax || other != other) ? other : dmax;
+            }
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = static_cast<double>(dmax);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double m = red[0];
+                for (int w = 1; w < kThreads / 32; ++w) m = (red[w] > m || red[w] != red[w]) ? red[w] : m;
+                const InstDesc& D = a.insts[inst];
+                InstState* st = D.state;
+                atomicMax(&st->delta_bits, static_cast<unsigned long long>(__double_as_longlong(m)));
+                __threadfence();
+                const unsigned int prev = atomicAdd(&st->tiles_done, 1u);
+                if (prev + 1 == static_cast<unsigned int>(C.ntiles)) finish_step(D);
+            }
+        }
+        __syncthreads();  // tile buffer reuse
+    }
+}
+
+template <typename T, int NDIM, int SCHEME, bool LAST>
+cudaError_t launch_stage(const StageArgs& a, int grid, cudaStream_t s) {
+    stage_kernel<T, NDIM, SCHEME, LAST><<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int NDIM, int SCHEME, bool LAST>
+int max_blocks_stage() {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stage_kernel<T, NDIM, SCHEME, LAST>,
+                                                      kThreads, 0) != cudaSuccess)
+        return 1;
+    return b > 0 ? b : 1;
+}
+
+}  // namespace hji
