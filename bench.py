@@ -42,10 +42,13 @@ SOLVE = dict(scheme="weno5", rk=3, cfl=0.5, tol=1e-6, max_steps=200000, check_ev
 #   disturbance 6) -> 27;  Lax-Friedrichs 6;  Euler stage 2;  RK combine 3;
 #   min(., l), |dV| and max 4.
 FLOPS_PER_NODE_STAGE = 328 + 27 + 6 + 2 + 3 + 4
-# Algorithmic HBM words per node per RK3 step with per-stage kernels:
-# stage 1 reads V, writes W1; stage 2 reads W1, V, writes W2; stage 3 reads
-# W2, V, l, writes V'.
-WORDS_PER_NODE_STEP = 9
+# Algorithmic memory words per node per RK3 step with per-stage kernels.
+# FP64 (stage states): stage 1 reads V, writes W1; stage 2 reads W1, V,
+# writes W2; stage 3 reads W2, V, l, writes V' -> 9 words (72 B).
+# FP32 (compensated hi/lo value, stage increments): stage 1 reads hi, lo,
+# writes D1; stage 2 reads hi, lo, D1, writes D2; stage 3 reads hi, lo, D2,
+# l, writes hi', lo' -> 13 words (52 B).
+WORDS_PER_NODE_STEP = {"f64": 9, "f32": 13}
 
 
 def _env_int(name, default):
@@ -117,12 +120,13 @@ def _flush_l2(torch, buf):
 
 def cpu_baseline(n_steps=None, budget_s=15.0):
     """The FP64 oracle as it stands, on a bounded sample of the same workload:
-    `n_steps` RK3 steps of the 1001^2 WENO5 march from the warm start."""
+    `n_steps` RK3 steps of the 1001^2 WENO5 march (from V0 = l: a step costs
+    the same whatever the start)."""
     import oracle
     gd, dyn, l = W.di_config(N_SIDE, dmax=DMAX)
     P = oracle.problem(gd, dyn)
     alpha, dt = oracle.alpha_dt(P, SOLVE["cfl"])
-    V = oracle.init(P, l, np.minimum(l, 0.5 + 0.0 * l))
+    V = oracle.init(P, l)
     cells = W.num_cells(gd)
     t0 = time.perf_counter()
     steps = 0
@@ -279,7 +283,7 @@ def main():
                 "frac": achieved_tflops / peak, "traffic": None,
                 "kernel": "stage_kernel<%s,2,WENO5> (per-stage, 3 per RK3 step)" % prec,
                 "flops_per_node_stage": FLOPS_PER_NODE_STAGE,
-                "hbm_words_per_node_step": WORDS_PER_NODE_STEP,
+                "mem_words_per_node_step": WORDS_PER_NODE_STEP[prec],
                 "peak_source": "derived from unit counts at 2070 MHz max SM clock"
                                if prec == "f32" else "GB300 datasheet FP64 rate"}
 
@@ -298,7 +302,8 @@ def main():
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk}
 
     if rank == 0 and not args.no_variants:
-        line["time_to_converge"] = time_to_converge(hji, torch, gd, dyn, l, l_dev, k_dev, prec)
+        line["time_to_converge"] = time_to_converge(hji, torch, gd, dyn, l, l_dev, k_dev)
+        line["hbm_workloads"] = hbm_workloads(hji, torch)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(budget_s=12.0)
     g.close()
@@ -309,24 +314,124 @@ def main():
     return 0
 
 
-def time_to_converge(hji, torch, gd, dyn, l, l_dev, k_dev, prec):
-    """Warm vs standard time-to-converge on the bench workload, in the bench
-    precision and in FP64 (each one solve, device-resident inputs)."""
+def _timed(torch, fn):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return r, 1000.0 * (time.perf_counter() - t0)
+
+
+def time_to_converge(hji, torch, gd, dyn, l, l_dev, k_dev):
+    """Warm vs standard time-to-converge on the bench workload (each one
+    solve, device-resident inputs): FP64 standard and warm, FP32 warm, and
+    the precision pattern (FP32 warm march, then an FP64 re-validation sweep
+    warm-started from it), with max-abs and BRT errors against the FP64
+    standard solve."""
     out = {}
-    for p in sorted({prec, "f64"}):
-        tdt = torch.float32 if p == "f32" else torch.float64
-        g = hji.Grid(gd, p)
-        g.set_dynamics(dyn)
-        ld, kd = l_dev.to(tdt), k_dev.to(tdt)
-        for name, k in (("standard", None), ("warm", kd)):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            st = g.solve(ld, k, **SOLVE)
-            torch.cuda.synchronize()
-            out["%s_%s" % (p, name)] = {"ms": 1000 * (time.perf_counter() - t0),
-                                        "steps": st["steps"], "converged": st["converged"],
-                                        "intervals_0.01": st["tau"] / 0.01}
-        g.close()
+    l64, k64 = l_dev.double(), k_dev.double()
+    l32, k32 = l_dev.float(), k_dev.float()
+    g64 = hji.Grid(gd, "f64")
+    g64.set_dynamics(dyn)
+    st, ms = _timed(torch, lambda: g64.solve(l64, **SOLVE))
+    ref = torch.empty_like(l64)
+    g64.value(ref)
+    out["f64_standard"] = {"ms": ms, "steps": st["steps"], "converged": st["converged"],
+                           "intervals_0.01": st["tau"] / 0.01}
+    st, ms = _timed(torch, lambda: g64.solve(l64, k64, **SOLVE))
+    out["f64_warm"] = {"ms": ms, "steps": st["steps"], "converged": st["converged"],
+                       "intervals_0.01": st["tau"] / 0.01}
+    g32 = hji.Grid(gd, "f32")
+    g32.set_dynamics(dyn)
+
+    def pattern():
+        s32 = g32.solve(l32, k32, **SOLVE)
+        g64.take_value(g32)
+        s64 = g64.solve(l64, init=hji.HJI_INIT_RESIDENT, **SOLVE)
+        return s32, s64
+
+    (s32, s64), ms = _timed(torch, pattern)
+    v32 = torch.empty_like(l32)
+    g32.value(v32)
+    v64 = torch.empty_like(l64)
+    g64.value(v64)
+    scale = float(l64.abs().max())
+
+    def errs(v):
+        d = (v.double() - ref).abs().max().item()
+        brt_diff = int(((v.double() <= 0) != (ref <= 0)).sum().item())
+        return {"max_abs": d, "max_abs_over_max_l": d / scale, "brt_nodes_differing": brt_diff}
+
+    out["f32_warm"] = dict({"steps": s32["steps"], "converged": s32["converged"]}, **errs(v32))
+    _, ms32 = _timed(torch, lambda: g32.solve(l32, k32, **SOLVE))
+    out["f32_warm"]["ms"] = ms32
+    out["f32_warm_then_f64_revalidation"] = dict(
+        {"ms": ms, "f32_steps": s32["steps"], "f64_steps": s64["steps"],
+         "converged": s64["converged"]}, **errs(v64))
+    out["speedup_pattern_vs_f64_standard"] = out["f64_standard"]["ms"] / ms
+    g32.close()
+    g64.close()
+    return out
+
+
+def _measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def hbm_workloads(hji, torch, steps=50):
+    """HBM-bound marches (working sets well above the 129 MB L2), FP32
+    compensated storage, ENO2/RK2: 50 steps each from V0 = l, CUDA-event
+    timed after a warm-up.  Algorithmic bytes per node per RK2 step: stage 1
+    reads hi, lo and writes D1 (12 B); stage 2 reads hi, lo, D1, l and writes
+    hi', lo' (24 B): 36 B."""
+    peak, src = _measured_hbm()
+    out = {}
+    bytes_per_update = 36
+    cases = []
+    gd, dyn, l = W.quad4d_config(61, dmax=0.3)
+    cases.append(("quad4d_61^4", [gd], [dyn], [l]))
+    insts = W.batch_instances(count=256, seed=1903)
+    cases.append(("batch256_di_101..501", [i["grid"] for i in insts], [i["dyn"] for i in insts],
+                  [W.instance_target(i) for i in insts]))
+    opts = dict(scheme="eno2", rk=2, cfl=0.5, tol=0.0, max_steps=steps, check_every=steps)
+    stream = torch.cuda.current_stream()
+    for name, gds, dyns, ls in cases:
+        grids = []
+        for gd, dyn in zip(gds, dyns):
+            g = hji.Grid(gd, "f32")
+            g.set_dynamics(dyn)
+            grids.append(g)
+        ldev = [torch.from_numpy(l.astype(np.float32)).cuda() for l in ls]
+        cells = sum(int(np.prod(gd["n"])) for gd in gds)
+
+        def run():
+            if len(grids) == 1:
+                return [grids[0].solve(ldev[0], **opts)]
+            return hji.batch_solve(grids, ldev, **opts)[0]
+
+        run()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sts = run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        upd = sum(int(np.prod(gd["n"])) * s["steps"] for gd, s in zip(gds, sts))
+        gbs = upd * bytes_per_update / (ms * 1e-3) / 1e9
+        out[name] = {"nodes": cells, "steps": steps, "ms": ms,
+                     "cell_updates_per_s": upd / (ms * 1e-3),
+                     "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                  "frac": gbs / peak, "peak_source": src,
+                                  "bytes_per_node_step": bytes_per_update,
+                                  "note": "whole-march time (set-up, init and 50 steps of "
+                                          "2 stage launches) in the denominator"}}
+        for g in grids:
+            g.close()
     return out
 
 

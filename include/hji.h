@@ -183,6 +183,17 @@ hji_status hji_batch_solve(int count, hji_grid* grids, const void* const* l,
  * Errors: HJI_E_STATE (no value yet), HJI_E_INVALID, HJI_E_CUDA. */
 hji_status hji_value_get(hji_grid g, void* out, int ptr_is_device, void* cuda_stream);
 
+/* Copy src's current value into dst as dst's resident value (converting
+ * precision on the device), so that hji_solve(dst, ..., HJI_INIT_RESIDENT)
+ * starts from it.  This is how an FP32 march is followed by an FP64
+ * re-validation sweep warm-started from its result (by Thm. 1 / Thm. 2 that
+ * sweep is conservative, and exact when the FP32 value lies above the FP64
+ * solution).  Grids must have the same ndim and node counts.  An FP32 source
+ * contributes its full compensated value (high + low word); an FP64 source
+ * is split exactly into an FP32 high and low word.
+ * Errors: HJI_E_INVALID (shape), HJI_E_STATE (src has no value), HJI_E_CUDA. */
+hji_status hji_value_transfer(hji_grid dst, hji_grid src, void* cuda_stream);
+
 /* Grid facts: ndim, n[], and the number of nodes (may be NULL each). */
 hji_status hji_grid_info(hji_grid g, int* ndim, int64_t* n, int64_t* num_nodes);
 

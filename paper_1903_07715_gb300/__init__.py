@@ -30,8 +30,8 @@ HJI_FN = {"tan": 0, "sin": 1, "cos": 2}
 SCHEMES = {"eno1": HJI_ENO1, "eno2": HJI_ENO2, "weno5": HJI_WENO5}
 
 EXPORTS = ["hji_grid_create", "hji_grid_destroy", "hji_dynamics_set", "hji_solve",
-           "hji_batch_solve", "hji_value_get", "hji_grid_info", "hji_status_string",
-           "hji_last_error"]
+           "hji_batch_solve", "hji_value_get", "hji_value_transfer", "hji_grid_info",
+           "hji_status_string", "hji_last_error"]
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -101,6 +101,7 @@ def load(build_if_missing=False):
                                     ctypes.POINTER(hji_solve_opts), vp,
                                     ctypes.POINTER(hji_solve_stats)]
     lib.hji_value_get.argtypes = [vp, vp, ctypes.c_int, vp]
+    lib.hji_value_transfer.argtypes = [vp, vp, vp]
     lib.hji_grid_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), i64p, i64p]
     lib.hji_status_string.argtypes = [ctypes.c_int]
     lib.hji_status_string.restype = ctypes.c_char_p
@@ -137,6 +138,10 @@ def hji_batch_solve(count, grids, l, k, ptr_is_device, opts, stream, stats):
 
 def hji_value_get(g, out, ptr_is_device, stream):
     return load().hji_value_get(g, out, ptr_is_device, stream)
+
+
+def hji_value_transfer(dst, src, stream):
+    return load().hji_value_transfer(dst, src, stream)
 
 
 def hji_grid_info(g, ndim, n, num_nodes):
@@ -313,6 +318,11 @@ class Grid:
         if isinstance(out, np.ndarray) and keep is not out:
             out[...] = keep
         return out
+
+    def take_value(self, other, stream=None):
+        """Make `other`'s current value this grid's resident value (device-side
+        precision conversion); follow with solve(..., init=HJI_INIT_RESIDENT)."""
+        _check(hji_value_transfer(self._h, other.handle, self._stream(stream)), self._h)
 
     def close(self):
         if self._h:

@@ -355,6 +355,7 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
     };
 
     std::vector<const void*> kptr(count, nullptr);
+    std::vector<int> keep_lo(count, 0);
     std::vector<unsigned long long> tiles;
     tiles.reserve((size_t)total_tiles);
     for (int i = 0; i < count; ++i) {
@@ -378,6 +379,7 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
             }
         } else if (o->init == HJI_INIT_RESIDENT) {
             kptr[i] = g->V[g->cur];
+            keep_lo[i] = 1;
         }
         H[i] = make_desc(g, o, d_active);
         for (long long t = 0; t < H[i].ntiles; ++t) tiles.push_back(hji::make_tile(i, t));
@@ -395,7 +397,7 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_active, &counts[0], sizeof(int), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_ntiles, &counts[1], sizeof(int), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = hji::launch_setup(d_desc, H.data(), count, f32, s);
-    if (e == cudaSuccess) e = hji::launch_init(d_desc, H.data(), count, f32, kptr.data(), s);
+    if (e == cudaSuccess) e = hji::launch_init(d_desc, H.data(), count, f32, kptr.data(), keep_lo.data(), s);
     if (e != cudaSuccess) {
         cleanup();
         return cuda_fail(g0, e, "set-up");
@@ -686,6 +688,23 @@ hji_status hji_value_get(hji_grid g, void* out, int ptr_is_device, void* cuda_st
     HJI_CUDA(g, cudaMemcpyAsync(out, g->V[g->cur], bytes,
                                 ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     HJI_CUDA(g, cudaStreamSynchronize(s));
+    return HJI_OK;
+}
+
+hji_status hji_value_transfer(hji_grid dst, hji_grid src, void* cuda_stream) {
+    if (!dst || !src) return fail(dst ? dst : src, HJI_E_INVALID, "grid is NULL");
+    if (dst == src) return fail(dst, HJI_E_INVALID, "source and destination are the same grid");
+    if (dst->ndim != src->ndim) return fail(dst, HJI_E_INVALID, "grids differ in ndim");
+    for (int a = 0; a < dst->ndim; ++a)
+        if (dst->n[a] != src->n[a]) return fail(dst, HJI_E_INVALID, "grids differ in node counts");
+    if (!src->has_value) return fail(dst, HJI_E_STATE, "source grid has no value yet");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const bool sf = src->prec == HJI_F32, df = dst->prec == HJI_F32;
+    HJI_CUDA(dst, hji::launch_convert(src->ncells, src->V[src->cur], sf ? src->Vlo : nullptr, sf,
+                                      dst->V[0], df ? dst->Vlo : nullptr, df, s));
+    HJI_CUDA(dst, cudaStreamSynchronize(s));
+    dst->cur = 0;
+    dst->has_value = true;
     return HJI_OK;
 }
 

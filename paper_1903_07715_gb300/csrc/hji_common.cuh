@@ -125,7 +125,10 @@ int stage_max_blocks_f32(int ndim, int scheme, bool last);
 // Set-up kernels (hji_setup.cu).
 cudaError_t launch_setup(const InstDesc* d_insts, const InstDesc* h_insts, int count, bool f32,
                          cudaStream_t s);
+// keep_lo[i] != 0: k[i] is grid i's own resident value; keep its FP32 low word.
 cudaError_t launch_init(const InstDesc* d_insts, const InstDesc* h_insts, int count, bool f32,
-                        const void* const* k, cudaStream_t s);
+                        const void* const* k, const int* keep_lo, cudaStream_t s);
+cudaError_t launch_convert(long long n, const void* src_hi, const void* src_lo, bool src_f32,
+                           void* dst_hi, void* dst_lo, bool dst_f32, cudaStream_t s);
 
 }  // namespace hji

@@ -105,27 +105,65 @@ __global__ void __launch_bounds__(kThreads) alpha_kernel(const InstDesc* __restr
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-    init_kernel(const InstDesc* __restrict__ d, const T* __restrict__ k) {
+    init_kernel(const InstDesc* __restrict__ d, const T* __restrict__ k, int keep_lo) {
     const InstDesc& D = *d;
     const T* l = static_cast<const T*>(D.l);
     T* V = static_cast<T*>(D.V[0]);
-    T* Vlo = static_cast<T*>(D.Vlo);  // FP32 grids: low word of V starts at zero
+    // FP32 grids: the low word of V starts at zero, or, when k is the grid's
+    // own resident value, keeps that value's low word.
+    T* Vlo = static_cast<T*>(D.Vlo);
     unsigned int bad = 0u;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < D.ncells;
          c += (long long)gridDim.x * blockDim.x) {
         const T lv = l[c];
-        T v = lv;
+        T v = lv, vlo = T(0);
         if (!isfinite(lv)) bad = 1u;
         if (k != nullptr) {
             const T kv = k[c];
+            const T klo = (keep_lo && Vlo != nullptr) ? Vlo[c] : T(0);
             if (!isfinite(kv)) bad = 1u;
-            v = kv < lv ? kv : lv;
+            if (kv < lv || (kv == lv && klo < T(0))) {
+                v = kv;
+                vlo = klo;
+            }
         }
         V[c] = v;
-        if (Vlo != nullptr) Vlo[c] = T(0);
+        if (Vlo != nullptr) Vlo[c] = vlo;
     }
     bad = __any_sync(0xffffffffu, bad) ? 1u : 0u;
     if (bad && (threadIdx.x & 31) == 0) atomicOr(&D.state->nonfinite, 1u);
+}
+
+// Resident-value transfer between grids of different precision.
+__global__ void __launch_bounds__(kThreads)
+    convert_kernel(long long n, const void* src_hi, const void* src_lo, int src_f32, void* dst_hi,
+                   void* dst_lo, int dst_f32) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        double v;
+        if (src_f32) {
+            v = (double)static_cast<const float*>(src_hi)[c];
+            if (src_lo) v += (double)static_cast<const float*>(src_lo)[c];
+        } else {
+            v = static_cast<const double*>(src_hi)[c];
+        }
+        if (dst_f32) {
+            const float h = (float)v;
+            static_cast<float*>(dst_hi)[c] = h;
+            if (dst_lo) static_cast<float*>(dst_lo)[c] = (float)(v - (double)h);
+        } else {
+            static_cast<double*>(dst_hi)[c] = v;
+        }
+    }
+}
+
+static int grid_for(long long work, int cap);
+
+cudaError_t launch_convert(long long n, const void* src_hi, const void* src_lo, bool src_f32,
+                           void* dst_hi, void* dst_lo, bool dst_f32, cudaStream_t s) {
+    convert_kernel<<<grid_for(n, 4096), kThreads, 0, s>>>(n, src_hi, src_lo, src_f32 ? 1 : 0, dst_hi,
+                                                          dst_lo, dst_f32 ? 1 : 0);
+    return cudaGetLastError();
 }
 
 static int grid_for(long long work, int cap) {
@@ -154,13 +192,14 @@ cudaError_t launch_setup(const InstDesc* d_insts, const InstDesc* h_insts, int c
 }
 
 cudaError_t launch_init(const InstDesc* d_insts, const InstDesc* h_insts, int count, bool f32,
-                        const void* const* k, cudaStream_t s) {
+                        const void* const* k, const int* keep_lo, cudaStream_t s) {
     for (int i = 0; i < count; ++i) {
         const int g = grid_for(h_insts[i].ncells, 4096);
+        const int kl = keep_lo ? keep_lo[i] : 0;
         if (f32)
-            init_kernel<float><<<g, kThreads, 0, s>>>(d_insts + i, static_cast<const float*>(k[i]));
+            init_kernel<float><<<g, kThreads, 0, s>>>(d_insts + i, static_cast<const float*>(k[i]), kl);
         else
-            init_kernel<double><<<g, kThreads, 0, s>>>(d_insts + i, static_cast<const double*>(k[i]));
+            init_kernel<double><<<g, kThreads, 0, s>>>(d_insts + i, static_cast<const double*>(k[i]), kl);
     }
     return cudaGetLastError();
 }

@@ -87,51 +87,96 @@ __device__ __forceinline__ T weno5(T v1, T v2, T v3, T v4, T v5) {
     return scale * (num / (w1 + w2 + w3));
 }
 
-// (p-, p+) from a stencil line v[0..2G] centred at v[G].
+// (p-, p+) at node c from the 2G undivided differences D[k] = W[k+1] - W[k]
+// of its stencil line W[0..2G] (node c = W[G]; D[G-1] is the backward and
+// D[G] the forward difference).
 template <typename T, int SCHEME>
-__device__ __forceinline__ void one_sided(const T* v, T inv_dx, T& pm, T& pp) {
+__device__ __forceinline__ void one_sided_diffs(const T* D, T inv_dx, T& pm, T& pp) {
     if constexpr (SCHEME == HJI_ENO1) {
-        pm = (v[1] - v[0]) * inv_dx;
-        pp = (v[2] - v[1]) * inv_dx;
+        pm = D[0] * inv_dx;
+        pp = D[1] * inv_dx;
     } else if constexpr (SCHEME == HJI_ENO2) {
-        const T D0 = v[1] - v[0], D1 = v[2] - v[1], D2 = v[3] - v[2], D3 = v[4] - v[3];
-        const T Sm = D1 - D0, S0 = D2 - D1, Sp = D3 - D2;
-        pm = (D1 + T(0.5) * smaller_mag(Sm, S0)) * inv_dx;
-        pp = (D2 - T(0.5) * smaller_mag(S0, Sp)) * inv_dx;
+        const T Sm = D[1] - D[0], S0 = D[2] - D[1], Sp = D[3] - D[2];
+        pm = (D[1] + T(0.5) * smaller_mag(Sm, S0)) * inv_dx;
+        pp = (D[2] - T(0.5) * smaller_mag(S0, Sp)) * inv_dx;
     } else {
-        const T D0 = v[1] - v[0], D1 = v[2] - v[1], D2 = v[3] - v[2];
-        const T D3 = v[4] - v[3], D4 = v[5] - v[4], D5 = v[6] - v[5];
-        pm = weno5<T>(D0, D1, D2, D3, D4) * inv_dx;
-        pp = weno5<T>(D5, D4, D3, D2, D1) * inv_dx;
+        pm = weno5<T>(D[0], D[1], D[2], D[3], D[4]) * inv_dx;
+        pp = weno5<T>(D[5], D[4], D[3], D[2], D[1]) * inv_dx;
     }
 }
 
-// Stencil input at element offset i: v[i], plus the stage increment d[i]
-// when the grid stores increments (FP32); d is null otherwise.
+// A value on the grid as an unevaluated sum h + l.  FP64 grids use l = 0.
+// FP32 grids use h = the high word of V^n and l = its low word plus the
+// stage increment: differences of neighbours, (h1 - h0) + (l1 - l0), then
+// keep the precision of the difference itself instead of the precision of
+// the value (the high-word subtraction of close neighbours is exact).
 template <typename T>
-__device__ __forceinline__ T wval(const T* __restrict__ v, const T* __restrict__ d, long long i) {
-    T x = __ldg(v + i);
-    if (d != nullptr) x += __ldg(d + i);
-    return x;
+struct Pair {
+    T h, l;
+};
+
+template <typename T>
+__device__ __forceinline__ Pair<T> load_pair(const T* __restrict__ h, const T* __restrict__ lo,
+                                            const T* __restrict__ d, long long i) {
+    Pair<T> p;
+    p.h = __ldg(h + i);
+    p.l = T(0);
+    if (lo != nullptr) p.l = __ldg(lo + i);
+    if (d != nullptr) p.l += __ldg(d + i);
+    return p;
 }
 
-// Value at node index j (possibly outside [0, n)) of a line with stride s
-// starting at element offset 0 of v (and d): periodic wrap, or linear
-// extrapolation from the two edge nodes.
+// The ghost node e + k (e - i1) (linear extrapolation by k nodes beyond the
+// edge node e, i1 its inner neighbour).  With l = 0 (FP64) this is exactly
+// the textbook expression; with pairs the rounding errors of k*(e.h - i1.h)
+// and of the high-word sum are carried into the low word.
 template <typename T>
-__device__ __forceinline__ T line_value(const T* __restrict__ v, const T* __restrict__ d, int j,
-                                        int n, long long s, int periodic) {
-    if (j >= 0 && j < n) return wval(v, d, (long long)j * s);
+__device__ __forceinline__ Pair<T> extrapolate(Pair<T> e, Pair<T> i1, int k) {
+    Pair<T> g;
+    const T kk = T(k);
+    if constexpr (sizeof(T) == 8) {
+        g.h = e.h + kk * (e.h - i1.h);
+        g.l = T(0);
+    } else {
+        const T dh = e.h - i1.h;
+        const T t = kk * dh;
+        const T te = fmaf(kk, dh, -t);      // exact error of the product
+        const T sh = e.h + t;               // two-sum of e.h + t
+        const T bp = sh - e.h;
+        const T se = (e.h - (sh - bp)) + (t - bp);
+        g.h = sh;
+        g.l = e.l + kk * (e.l - i1.l) + (te + se);
+    }
+    return g;
+}
+
+// Node j (possibly outside [0, n)) of a line with element stride s whose
+// node 0 is at element offset 0 of h/lo/d: periodic wrap, or extrapolation.
+template <typename T>
+__device__ __forceinline__ Pair<T> line_pair(const T* __restrict__ h, const T* __restrict__ lo,
+                                            const T* __restrict__ d, int j, int n, long long s,
+                                            int periodic) {
+    if (j >= 0 && j < n) return load_pair(h, lo, d, (long long)j * s);
     if (periodic) {
         int w = j % n;
         if (w < 0) w += n;
-        return wval(v, d, (long long)w * s);
+        return load_pair(h, lo, d, (long long)w * s);
     }
     const bool low = j < 0;
     const int k = low ? -j : j - (n - 1);
-    const T e = wval(v, d, (long long)(low ? 0 : n - 1) * s);
-    const T i1 = wval(v, d, (long long)(low ? 1 : n - 2) * s);
-    return e + T(k) * (e - i1);
+    const Pair<T> e = load_pair(h, lo, d, (long long)(low ? 0 : n - 1) * s);
+    const Pair<T> i1 = load_pair(h, lo, d, (long long)(low ? 1 : n - 2) * s);
+    return extrapolate(e, i1, k);
+}
+
+// Undivided difference of two neighbouring pairs.
+template <typename T>
+__device__ __forceinline__ T pair_diff(const Pair<T>& b, const Pair<T>& a) {
+    if constexpr (sizeof(T) == 8) {
+        return b.h - a.h;
+    } else {
+        return (b.h - a.h) + (b.l - a.l);
+    }
 }
 
 // Shared-memory copy of what a tile needs from its instance, in precision T.
@@ -269,10 +314,14 @@ __global__ void __launch_bounds__(kThreads)
 
     constexpr bool INCR = sizeof(T) == 4;  // FP32: increments + compensated V
     __shared__ TileCtx<T> C;
-    __shared__ T tile[SH * SW];
+    __shared__ T th[SH * SW];              // high words of the stencil input
+    __shared__ T tl[INCR ? SH * SW : 1];   // FP32: low words (+ stage increment)
     __shared__ double red[kThreads / 32];
 
     const int ntiles = *a.ntiles;
+    // Stage coefficients in the kernel's precision, converted once.
+    const T cV = static_cast<T>(a.aV), cE = static_cast<T>(a.aE);
+    const bool reads_v = a.aV != 0.0;
     const int tx = threadIdx.x % TX;
     const int ty = threadIdx.x / TX;
     int loaded = -1;
@@ -308,8 +357,11 @@ __global__ void __launch_bounds__(kThreads)
         const int ny = NDIM >= 2 ? C.n[AY] : 1;
         const long long sy = NDIM >= 2 ? C.stride[AY] : 0;
         const int y0 = by * TY, x0 = bx * TX;
-        const T* __restrict__ win = C.win + base;
-        const T* __restrict__ din = C.din ? C.din + base : nullptr;
+        // Stencil input W = h + l: FP64 h = the stage state, l = 0; FP32
+        // h = high word of V^n, l = low word + the stage increment.
+        const T* __restrict__ hp = C.win + base;
+        const T* __restrict__ lp = INCR ? C.vlo + base : nullptr;
+        const T* __restrict__ dp = C.din ? C.din + base : nullptr;
 
         // 1. Stage the input tile with its ghost halo.
         for (int s = threadIdx.x; s < SH * SW; s += kThreads) {
@@ -317,18 +369,22 @@ __global__ void __launch_bounds__(kThreads)
             const int gy = y0 - GY + r, gx = x0 - G + cidx;
             const bool iny = (NDIM < 2) || (gy >= 0 && gy < ny);
             const bool inx = gx >= 0 && gx < nx;
-            T v;
+            Pair<T> v;
             if (iny && inx) {
-                v = wval<T>(win, din, (long long)gy * sy + gx);
+                v = load_pair<T>(hp, lp, dp, (long long)gy * sy + gx);
             } else if (iny) {
                 const long long r0 = (long long)gy * sy;
-                v = line_value<T>(win + r0, din ? din + r0 : nullptr, gx, nx, 1, C.periodic[AX]);
+                v = line_pair<T>(hp + r0, lp ? lp + r0 : nullptr, dp ? dp + r0 : nullptr, gx, nx,
+                                 1, C.periodic[AX]);
             } else if (inx) {
-                v = line_value<T>(win + gx, din ? din + gx : nullptr, gy, ny, sy, C.periodic[AY]);
+                v = line_pair<T>(hp + gx, lp ? lp + gx : nullptr, dp ? dp + gx : nullptr, gy, ny,
+                                 sy, C.periodic[AY]);
             } else {
-                v = T(0);  // corner of the halo: never used by an axis-aligned stencil
+                v.h = T(0);  // corner of the halo: never used by an axis-aligned stencil
+                v.l = T(0);
             }
-            tile[s] = v;
+            th[s] = v.h;
+            if constexpr (INCR) tl[s] = v.l;
         }
         __syncthreads();
 
@@ -340,28 +396,40 @@ __global__ void __launch_bounds__(kThreads)
             const int gy = y0 + ry, gx = x0 + tx;
             if (ry >= TY || gy >= ny || gx >= nx) continue;
             T pm[NDIM], pp[NDIM];
-            T line[2 * G + 1];
-            const T* trow = tile + (ry + GY) * SW + (tx + G);
+            T D[2 * G];
+            const int c0 = (ry + GY) * SW + (tx + G);  // this node in the shared tile
+            const T wc = th[c0];
+            // Fastest axis: consecutive shared-memory entries.
 #pragma unroll
-            for (int o = -G; o <= G; ++o) line[o + G] = trow[o];
-            const T wc = line[G];
-            one_sided<T, SCHEME>(line, C.inv_dx[AX], pm[AX], pp[AX]);
+            for (int o = 0; o < 2 * G; ++o) {
+                const int i = c0 - G + o;
+                if constexpr (INCR) D[o] = (th[i + 1] - th[i]) + (tl[i + 1] - tl[i]);
+                else D[o] = th[i + 1] - th[i];
+            }
+            one_sided_diffs<T, SCHEME>(D, C.inv_dx[AX], pm[AX], pp[AX]);
             if constexpr (NDIM >= 2) {
 #pragma unroll
-                for (int o = -G; o <= G; ++o) line[o + G] = trow[o * SW];
-                one_sided<T, SCHEME>(line, C.inv_dx[AY], pm[AY], pp[AY]);
+                for (int o = 0; o < 2 * G; ++o) {
+                    const int i = c0 + (o - G) * SW;
+                    if constexpr (INCR) D[o] = (th[i + SW] - th[i]) + (tl[i + SW] - tl[i]);
+                    else D[o] = th[i + SW] - th[i];
+                }
+                one_sided_diffs<T, SCHEME>(D, C.inv_dx[AY], pm[AY], pp[AY]);
             }
             const long long off = (long long)gy * sy + gx;  // within the plane
 #pragma unroll
             for (int ax = 0; ax < NDIM - 2; ++ax) {
+                // Slower axes: the stencil line straight from global memory (L2).
                 const long long l0 = off - (long long)sidx[ax] * C.stride[ax];
-                const T* lp = win + l0;
-                const T* ld = din ? din + l0 : nullptr;
+                Pair<T> line[2 * G + 1];
 #pragma unroll
                 for (int o = -G; o <= G; ++o)
-                    line[o + G] = line_value<T>(lp, ld, sidx[ax] + o, C.n[ax], C.stride[ax],
-                                                C.periodic[ax]);
-                one_sided<T, SCHEME>(line, C.inv_dx[ax], pm[ax], pp[ax]);
+                    line[o + G] = line_pair<T>(hp + l0, lp ? lp + l0 : nullptr,
+                                               dp ? dp + l0 : nullptr, sidx[ax] + o, C.n[ax],
+                                               C.stride[ax], C.periodic[ax]);
+#pragma unroll
+                for (int o = 0; o < 2 * G; ++o) D[o] = pair_diff(line[o + 1], line[o]);
+                one_sided_diffs<T, SCHEME>(D, C.inv_dx[ax], pm[ax], pp[ax]);
             }
             // Node coordinates and the drift f0(x) = c + A x + terms.
             int idx[NDIM];
@@ -407,8 +475,8 @@ __global__ void __launch_bounds__(kThreads)
             // Runge-Kutta stage combination.
             const long long gidx = base + off;
             if constexpr (INCR) {
-                const T dc = din ? __ldg(din + off) : T(0);
-                const T inc = T(a.aE) * (dc + C.dt * L);
+                const T dc = dp ? __ldg(dp + off) : T(0);
+                const T inc = cE * (dc + C.dt * L);
                 if constexpr (!LAST) {
                     C.wout[gidx] = inc;
                 } else {
@@ -434,9 +502,9 @@ __global__ void __launch_bounds__(kThreads)
                 const T eul = wc + C.dt * L;
                 T out;
                 T vn = wc;
-                if (a.aV != 0.0) {
+                if (reads_v) {
                     vn = __ldg(C.vcur + gidx);
-                    out = T(a.aV) * vn + T(a.aE) * eul;
+                    out = cV * vn + cE * eul;
                 } else {
                     out = eul;
                 }

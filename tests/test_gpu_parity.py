@@ -159,7 +159,7 @@ def test_resident_warm_start_matches_user_k(orc, hji_lib, torch_cuda):
 
 
 @pytest.mark.parametrize("n,scheme,rk,dmax", [(101, "eno2", 2, 0.0), (101, "weno5", 3, 0.2),
-                                              (201, "weno5", 3, 0.2), (101, "eno1", 1, 0.1)])
+                                              (201, "weno5", 3, 0.2), (101, "eno2", 3, 0.1)])
 def test_fp32_matches_fp64_oracle_at_convergence(orc, hji_lib, torch_cuda, n, scheme, rk, dmax):
     """FP32 storage (increments + compensated value) with FP64 dt/alpha and
     max|dV|: max-abs <= 1e-4 max|l| and the same BRT to one cell."""
@@ -171,6 +171,23 @@ def test_fp32_matches_fp64_oracle_at_convergence(orc, hji_lib, torch_cuda, n, sc
     assert st["converged"], st
     V = g.value().astype(np.float64)
     g.close()
+    assert np.abs(V - Vo).max() <= 1e-4 * np.abs(l).max()
+    assert brt_hausdorff(V, Vo) <= 1.0
+
+
+@pytest.mark.parametrize("scheme,rk", [("eno1", 1), ("eno2", 2), ("weno5", 3)])
+def test_fp32_matches_fp64_oracle_fixed_horizon(orc, hji_lib, torch_cuda, scheme, rk):
+    """FP32 vs the FP64 oracle after the same number of steps (tau = 2).  ENO1's
+    max|dV| decays so slowly near 1e-6 that its stopping step is ill-posed, so
+    a fixed horizon is the comparison for every scheme here."""
+    gd, dyn, l = W.di_config(101, dmax=0.1)
+    Vo, so = orc.solve(orc.problem(gd, dyn), l, scheme=scheme, rk=rk, cfl=0.5, tol=0.0,
+                       horizon=2.0)
+    g = _grid(hji_lib, gd, dyn, "f32")
+    st = g.solve(l.astype(np.float32), scheme=scheme, rk=rk, cfl=0.5, tol=0.0, horizon=2.0)
+    V = g.value().astype(np.float64)
+    g.close()
+    assert st["steps"] == so["steps"]
     assert np.abs(V - Vo).max() <= 1e-4 * np.abs(l).max()
     assert brt_hausdorff(V, Vo) <= 1.0
 
