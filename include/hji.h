@@ -183,6 +183,30 @@ hji_status hji_batch_solve(int count, hji_grid* grids, const void* const* l,
  * Errors: HJI_E_STATE (no value yet), HJI_E_INVALID, HJI_E_CUDA. */
 hji_status hji_value_get(hji_grid g, void* out, int ptr_is_device, void* cuda_stream);
 
+/* Allocation-free one-shot solve.  The paper has no counterpart: this entry
+ * serves callers that may not allocate device memory themselves (code whose
+ * device memory is owned by a host framework, real-time loops that forbid
+ * allocator calls, processes whose allocator is exhausted).  The caller
+ * passes device pointers: l (input), k (input, read for HJI_INIT_USER_K;
+ * NULL otherwise) and v_out (output, grid-shaped, the grid's precision; for
+ * HJI_INIT_RESIDENT it also holds the previous value on entry).  Grid,
+ * dynamics and options mean what they mean for hji_grid_create,
+ * hji_dynamics_set and hji_solve.  Every scratch buffer lives in one static
+ * device array of HJI_NOALLOC_SCRATCH_BYTES bytes that each GPU loading the
+ * library holds until exit; a grid that needs more (about 3 values per node
+ * for FP64 RK3, 4 for FP32 RK3, plus small tables) returns HJI_E_INVALID.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, once per device); make it before any stream
+ * capture.  Calls share the array: calls whose GPU work overlaps race.  No
+ * cudaMalloc, cudaFree or other allocating routine is called.  Errors as for
+ * hji_solve; the message is in hji_noalloc_last_error(). */
+#define HJI_NOALLOC_SCRATCH_BYTES (32u << 20)
+hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double* lo, const double* hi,
+                             const int* periodic, hji_precision prec, const hji_dynamics* dyn,
+                             const void* l, const void* k, void* v_out,
+                             const hji_solve_opts* o, void* cuda_stream, hji_solve_stats* stats);
+const char* hji_noalloc_last_error(void);
+
 /* Copy src's current value into dst as dst's resident value (converting
  * precision on the device), so that hji_solve(dst, ..., HJI_INIT_RESIDENT)
  * starts from it.  This is how an FP32 march is followed by an FP64

@@ -31,7 +31,7 @@ SCHEMES = {"eno1": HJI_ENO1, "eno2": HJI_ENO2, "weno5": HJI_WENO5}
 
 EXPORTS = ["hji_grid_create", "hji_grid_destroy", "hji_dynamics_set", "hji_solve",
            "hji_batch_solve", "hji_value_get", "hji_value_transfer", "hji_grid_info",
-           "hji_status_string", "hji_last_error"]
+           "hji_status_string", "hji_last_error", "hji_solve_noalloc", "hji_noalloc_last_error"]
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -107,8 +107,14 @@ def load(build_if_missing=False):
     lib.hji_status_string.restype = ctypes.c_char_p
     lib.hji_last_error.argtypes = [vp]
     lib.hji_last_error.restype = ctypes.c_char_p
+    lib.hji_solve_noalloc.argtypes = [ctypes.c_int, i64p, dp, dp, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.c_int, ctypes.POINTER(hji_dynamics), vp, vp, vp,
+                                      ctypes.POINTER(hji_solve_opts), vp,
+                                      ctypes.POINTER(hji_solve_stats)]
+    lib.hji_noalloc_last_error.argtypes = []
+    lib.hji_noalloc_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("hji_status_string", "hji_last_error"):
+        if name not in ("hji_status_string", "hji_last_error", "hji_noalloc_last_error"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -146,6 +152,15 @@ def hji_value_transfer(dst, src, stream):
 
 def hji_grid_info(g, ndim, n, num_nodes):
     return load().hji_grid_info(g, ndim, n, num_nodes)
+
+
+def hji_solve_noalloc(ndim, n, lo, hi, periodic, prec, dyn, l, k, v_out, opts, stream, stats):
+    return load().hji_solve_noalloc(ndim, n, lo, hi, periodic, prec, dyn, l, k, v_out, opts,
+                                    stream, stats)
+
+
+def hji_noalloc_last_error():
+    return load().hji_noalloc_last_error().decode()
 
 
 def hji_status_string(s):
