@@ -114,6 +114,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def reduce_over_ranks(dist, torch, ms, updates, device):
+    """Job-level timing for independent per-rank instances: the slowest
+    rank's time and the sum of every rank's cell-updates."""
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(updates)], device=device, dtype=torch.float64)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def _flush_l2(torch, buf):
     buf.add_(1)  # 512 MB written: larger than the 129 MB L2
 
@@ -182,6 +192,10 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--workload", default="di1001", choices=["di1001", "quad61", "batch256"],
+                    help="di1001: whole warm-started solves of the 1001^2 double integrator "
+                         "(default); quad61 / batch256: 50-step FP32 marches of the HBM-bound "
+                         "61^4 quadrotor subsystem / 256 uneven double integrators")
     args = ap.parse_args()
 
     rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
@@ -198,6 +212,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     hji.load()
+    if args.workload != "di1001":
+        return run_hbm_workload(args, hji, torch, dist, rank, world, local_rank)
 
     prec = args.precision
     npdt = np.float32 if prec == "f32" else np.float64
@@ -255,12 +271,7 @@ def main():
     ms, updates, launches, stats = timed_solves(args.steps)
     clk = clocks.stop()
     if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        u = torch.tensor([updates], device="cuda", dtype=torch.float64)
-        dist.all_reduce(u)
-        updates = float(u.item())
+        ms, updates = reduce_over_ranks(dist, torch, ms, updates, "cuda")
     value = updates / (ms / 1000.0)
 
     e2e_ms, e2e_updates, _, _ = timed_solves(max(1, args.steps), host=True)
@@ -374,6 +385,32 @@ def time_to_converge(hji, torch, gd, dyn, l, l_dev, k_dev):
     return out
 
 
+def run_hbm_workload(args, hji, torch, dist, rank, world, local_rank):
+    """Main line for the HBM-bound workloads: each bench step is one 50-step
+    FP32 ENO2/RK2 march (set-up, init from V0 = l, 100 stage launches)."""
+    name = "quad4d_61^4" if args.workload == "quad61" else "batch256_di_101..501"
+    clocks = ClockSampler(local_rank)
+    res = hbm_workloads(hji, torch, steps=50, only=name, repeats=args.steps, warmup=args.warmup,
+                        clocks=clocks)[name]
+    ms, upd = res["ms_total"], res["updates_total"]
+    if dist is not None:
+        ms, upd = reduce_over_ranks(dist, torch, ms, upd, "cuda")
+    line = {"metric": "cell-updates/s", "value": upd / (ms * 1e-3), "unit": "cell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": name + ", FP32 ENO2/RK2, cfl 0.5, 50 steps from V0 = l per "
+                                          "bench step", "nodes": res["nodes"],
+                       "l2": "inputs larger than L2"},
+            "e2e": None, "gpu_launches": res["launches"], "roofline": res["roofline"],
+            "clocks": res["clocks"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def _measured_hbm():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -382,7 +419,7 @@ def _measured_hbm():
         return 6800.0, "fallback"
 
 
-def hbm_workloads(hji, torch, steps=50):
+def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=None):
     """HBM-bound marches (working sets well above the 129 MB L2), FP32
     compensated storage, ENO2/RK2: 50 steps each from V0 = l, CUDA-event
     timed after a warm-up.  Algorithmic bytes per node per RK2 step: stage 1
@@ -392,11 +429,13 @@ def hbm_workloads(hji, torch, steps=50):
     out = {}
     bytes_per_update = 36
     cases = []
-    gd, dyn, l = W.quad4d_config(61, dmax=0.3)
-    cases.append(("quad4d_61^4", [gd], [dyn], [l]))
-    insts = W.batch_instances(count=256, seed=1903)
-    cases.append(("batch256_di_101..501", [i["grid"] for i in insts], [i["dyn"] for i in insts],
-                  [W.instance_target(i) for i in insts]))
+    if only in (None, "quad4d_61^4"):
+        gd, dyn, l = W.quad4d_config(61, dmax=0.3)
+        cases.append(("quad4d_61^4", [gd], [dyn], [l]))
+    if only in (None, "batch256_di_101..501"):
+        insts = W.batch_instances(count=256, seed=1903)
+        cases.append(("batch256_di_101..501", [i["grid"] for i in insts],
+                      [i["dyn"] for i in insts], [W.instance_target(i) for i in insts]))
     opts = dict(scheme="eno2", rk=2, cfl=0.5, tol=0.0, max_steps=steps, check_every=steps)
     stream = torch.cuda.current_stream()
     for name, gds, dyns, ls in cases:
@@ -413,21 +452,29 @@ def hbm_workloads(hji, torch, steps=50):
                 return [grids[0].solve(ldev[0], **opts)]
             return hji.batch_solve(grids, ldev, **opts)[0]
 
-        run()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sts = run()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        upd = sum(int(np.prod(gd["n"])) * s["steps"] for gd, s in zip(gds, sts))
+        for _ in range(max(1, warmup)):
+            run()
+        if clocks is not None:
+            clocks.start()
+        ms, upd, launches = 0.0, 0, 0
+        for _ in range(repeats):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sts = run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            upd += sum(int(np.prod(gd["n"])) * s["steps"] for gd, s in zip(gds, sts))
+            launches += max(s["kernel_launches"] for s in sts)
+        clk = clocks.stop() if clocks is not None else None
         gbs = upd * bytes_per_update / (ms * 1e-3) / 1e9
-        out[name] = {"nodes": cells, "steps": steps, "ms": ms,
-                     "cell_updates_per_s": upd / (ms * 1e-3),
+        out[name] = {"nodes": cells, "steps": steps, "ms": ms / repeats,
+                     "cell_updates_per_s": upd / (ms * 1e-3), "ms_total": ms,
+                     "updates_total": upd, "launches": launches, "clocks": clk,
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                                   "frac": gbs / peak, "peak_source": src,
-                                  "bytes_per_node_step": bytes_per_update,
+                                  "bytes_per_node_step": bytes_per_update, "traffic": None,
                                   "note": "whole-march time (set-up, init and 50 steps of "
                                           "2 stage launches) in the denominator"}}
         for g in grids:

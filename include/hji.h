@@ -218,6 +218,53 @@ const char* hji_noalloc_last_error(void);
  * Errors: HJI_E_INVALID (shape), HJI_E_STATE (src has no value), HJI_E_CUDA. */
 hji_status hji_value_transfer(hji_grid dst, hji_grid src, void* cuda_stream);
 
+/* ---- Continuous-batching engine (serving) ----
+ * One engine marches many requests at once: each request is a grid (its
+ * dynamics already set with hji_dynamics_set), a target l and an init mode
+ * (typically HJI_INIT_RESIDENT: warm-start from the solution the grid kept
+ * from its previous request, Sec. III).  Requests wait in a queue and are
+ * admitted into slots while others are marching, as long as a slot is free
+ * and the device bytes of the admitted grids stay within the budget; every
+ * chunk of check_every steps advances all admitted requests with one
+ * persistent kernel launch per RK stage (a CUDA graph that reads the
+ * device-side tile list, so admissions and departures need no re-capture);
+ * a request leaves when its own test stops it and its slot refills at the
+ * next step.  A request's arithmetic does not depend on what else is in the
+ * batch, so its result equals a solo hji_solve bit for bit.
+ * All grids of an engine share ndim and precision; the options (scheme,
+ * rk_order, cfl, tol, horizon, max_steps, check_every) are the engine's.
+ * hji_engine_step never blocks on the chunk it launches: it waits for the
+ * previous chunk, retires and admits, then launches the next, so engines on
+ * different streams overlap on the device when stepped in turn. */
+typedef struct hji_engine_s* hji_engine;
+
+/* max_slots: 1..65535 concurrent requests; budget_bytes: device bytes the
+ * admitted grids may hold together (0 = no limit).  Errors: HJI_E_INVALID,
+ * HJI_E_NOMEM, HJI_E_CUDA. */
+hji_status hji_engine_create(int ndim, hji_precision prec, const hji_solve_opts* o, int max_slots,
+                             size_t budget_bytes, void* cuda_stream, hji_engine* out);
+
+/* Queue a request.  l (grid-shaped, host or device) is copied into the grid
+ * now, on the engine's stream; k likewise for HJI_INIT_USER_K.  A grid may
+ * have one request queued or marching at a time (HJI_E_STATE otherwise), and
+ * must not be used outside the engine until that request is polled.  A
+ * grid larger than the whole budget is refused with HJI_E_INVALID. */
+hji_status hji_engine_submit(hji_engine e, hji_grid g, const void* l, const void* k,
+                             int ptr_is_device, hji_init init, int64_t tag);
+
+/* Wait for the chunk in flight, retire finished requests, admit queued ones,
+ * launch the next chunk.  *active / *queued (may be NULL) report the slots
+ * in use and the requests waiting after the call. */
+hji_status hji_engine_step(hji_engine e, int* active, int* queued);
+
+/* Finished requests since the last poll: up to `cap` of (tag, stats,
+ * status); *count receives how many were written. */
+hji_status hji_engine_poll(hji_engine e, int64_t* tags, hji_solve_stats* stats,
+                           hji_status* status, int cap, int* count);
+
+hji_status hji_engine_destroy(hji_engine e);
+const char* hji_engine_last_error(hji_engine e);
+
 /* Grid facts: ndim, n[], and the number of nodes (may be NULL each). */
 hji_status hji_grid_info(hji_grid g, int* ndim, int64_t* n, int64_t* num_nodes);
 

@@ -31,7 +31,9 @@ SCHEMES = {"eno1": HJI_ENO1, "eno2": HJI_ENO2, "weno5": HJI_WENO5}
 
 EXPORTS = ["hji_grid_create", "hji_grid_destroy", "hji_dynamics_set", "hji_solve",
            "hji_batch_solve", "hji_value_get", "hji_value_transfer", "hji_grid_info",
-           "hji_status_string", "hji_last_error", "hji_solve_noalloc", "hji_noalloc_last_error"]
+           "hji_status_string", "hji_last_error", "hji_solve_noalloc", "hji_noalloc_last_error",
+           "hji_engine_create", "hji_engine_submit", "hji_engine_step", "hji_engine_poll",
+           "hji_engine_destroy", "hji_engine_last_error"]
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -113,8 +115,18 @@ def load(build_if_missing=False):
                                       ctypes.POINTER(hji_solve_stats)]
     lib.hji_noalloc_last_error.argtypes = []
     lib.hji_noalloc_last_error.restype = ctypes.c_char_p
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.hji_engine_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(hji_solve_opts),
+                                      ctypes.c_int, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+    lib.hji_engine_submit.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64]
+    lib.hji_engine_step.argtypes = [vp, ip, ip]
+    lib.hji_engine_poll.argtypes = [vp, i64p, ctypes.POINTER(hji_solve_stats), ip, ctypes.c_int, ip]
+    lib.hji_engine_destroy.argtypes = [vp]
+    lib.hji_engine_last_error.argtypes = [vp]
+    lib.hji_engine_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("hji_status_string", "hji_last_error", "hji_noalloc_last_error"):
+        if name not in ("hji_status_string", "hji_last_error", "hji_noalloc_last_error",
+                        "hji_engine_last_error"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -161,6 +173,30 @@ def hji_solve_noalloc(ndim, n, lo, hi, periodic, prec, dyn, l, k, v_out, opts, s
 
 def hji_noalloc_last_error():
     return load().hji_noalloc_last_error().decode()
+
+
+def hji_engine_create(ndim, prec, opts, max_slots, budget_bytes, stream, out):
+    return load().hji_engine_create(ndim, prec, opts, max_slots, budget_bytes, stream, out)
+
+
+def hji_engine_submit(e, g, l, k, ptr_is_device, init, tag):
+    return load().hji_engine_submit(e, g, l, k, ptr_is_device, init, tag)
+
+
+def hji_engine_step(e, active, queued):
+    return load().hji_engine_step(e, active, queued)
+
+
+def hji_engine_poll(e, tags, stats, status, cap, count):
+    return load().hji_engine_poll(e, tags, stats, status, cap, count)
+
+
+def hji_engine_destroy(e):
+    return load().hji_engine_destroy(e)
+
+
+def hji_engine_last_error(e):
+    return load().hji_engine_last_error(e).decode()
 
 
 def hji_status_string(s):
@@ -378,3 +414,69 @@ def batch_solve(grids, ls, ks=None, init=None, stream=None, **opts):
     if rc not in (HJI_OK, HJI_E_NOT_CONVERGED):
         raise HJIError(rc, hji_last_error(grids[0].handle))
     return [_stats_dict(s) for s in stats], rc
+
+
+class Engine:
+    """Continuous-batching engine (hji_engine_*): requests are admitted into
+    slots while others march; see include/hji.h."""
+
+    def __init__(self, ndim, precision="f32", max_slots=64, budget_bytes=0, stream=None,
+                 **opts):
+        self._h = ctypes.c_void_p()
+        self.prec = HJI_F64 if precision == "f64" else HJI_F32
+        o = solve_opts(**opts)
+        rc = hji_engine_create(ndim, self.prec, ctypes.byref(o), max_slots, budget_bytes,
+                               Grid._stream(stream), ctypes.byref(self._h))
+        if rc != HJI_OK:
+            raise HJIError(rc, hji_engine_last_error(None))
+        self._keep = {}
+
+    def submit(self, grid, l, k=None, init=None, tag=0):
+        lp, ldev, lk = grid._ptr(l)
+        kp, kdev, kk = grid._ptr(k)
+        if init is None:
+            init = HJI_INIT_USER_K if k is not None else HJI_INIT_STANDARD
+        rc = hji_engine_submit(self._h, grid.handle, lp, kp, ldev, init, int(tag))
+        if rc != HJI_OK:
+            raise HJIError(rc, hji_engine_last_error(self._h))
+        self._keep[int(tag)] = (lk, kk)
+
+    def step(self):
+        a, q = ctypes.c_int(), ctypes.c_int()
+        rc = hji_engine_step(self._h, ctypes.byref(a), ctypes.byref(q))
+        if rc != HJI_OK:
+            raise HJIError(rc, hji_engine_last_error(self._h))
+        return a.value, q.value
+
+    def poll(self, cap=256):
+        tags = (ctypes.c_int64 * cap)()
+        stats = (hji_solve_stats * cap)()
+        status = (ctypes.c_int * cap)()
+        n = ctypes.c_int()
+        rc = hji_engine_poll(self._h, tags, stats, status, cap, ctypes.byref(n))
+        if rc != HJI_OK:
+            raise HJIError(rc, hji_engine_last_error(self._h))
+        out = []
+        for i in range(n.value):
+            self._keep.pop(int(tags[i]), None)
+            out.append((int(tags[i]), _stats_dict(stats[i]), int(status[i])))
+        return out
+
+    def drain(self):
+        done = []
+        while True:
+            a, q = self.step()
+            done += self.poll()
+            if a == 0 and q == 0:
+                return done + self.poll()
+
+    def close(self):
+        if self._h:
+            hji_engine_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <new>
 #include <string>
 #include <vector>
@@ -56,6 +57,52 @@ struct hji_grid_s {
     cudaGraphExec_t graph = nullptr;
     long long graph_key[6] = {0, 0, 0, 0, 0, 0};
     cudaStream_t cap_stream = nullptr;
+};
+
+struct hji_engine_s {
+    int ndim = 0;
+    hji_precision prec = HJI_F64;
+    hji_solve_opts o{};
+    int chunk = 32;
+    int max_slots = 0;
+    size_t budget = 0;
+    size_t in_use = 0;
+    cudaStream_t s = nullptr;
+    cudaStream_t cap = nullptr;
+    InstDesc* d_desc = nullptr;       // max_slots descriptors
+    int* d_counts = nullptr;          // [0] marching instances, [1] tiles in the list
+    unsigned long long* d_tiles = nullptr;
+    size_t tiles_cap = 0;
+    int* h_counts = nullptr;          // pinned mirror of d_counts
+    cudaGraphExec_t graph = nullptr;
+    int grid = 0;
+    cudaEvent_t ev = nullptr;
+    bool inflight = false;
+    int launched_active = 0;          // instances marching when the chunk was launched
+    struct Slot {
+        bool used = false;
+        hji_grid g = nullptr;
+        int64_t tag = 0;
+        size_t bytes = 0;
+        hji_init init = HJI_INIT_STANDARD;
+        std::chrono::steady_clock::time_point t0;
+    };
+    struct Req {
+        hji_grid g;
+        int64_t tag;
+        hji_init init;
+        bool has_k;
+    };
+    struct Done {
+        int64_t tag;
+        hji_solve_stats st;
+        hji_status status;
+    };
+    std::vector<Slot> slots;
+    std::vector<InstDesc> h_desc;
+    std::deque<Req> queue;
+    std::vector<Done> done;
+    std::string err;
 };
 
 namespace {
@@ -258,6 +305,9 @@ hji_status capture_chunk(hji_grid g, cudaStream_t cap, bool f32, int ndim, int s
             a.stage_out = plan[i].out;
             a.aV = plan[i].aV;
             a.aE = plan[i].aE;
+            a.aVf = (float)plan[i].aV;
+            a.aEf = (float)plan[i].aE;
+            a.reads_v = plan[i].aV != 0.0 ? 1 : 0;
             e = L[i](a, grid, cap);
         }
     }
@@ -428,7 +478,7 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
     // The march: graphs of `chunk` steps, one in flight ahead of the check.
     const int chunk = o->check_every > 0 ? o->check_every : 32;
     const int grid = stage_grid(f32, ndim, o->scheme, total_tiles);
-    hji::StageArgs base{d_desc, d_tiles, d_ntiles, 0, 0, 0.0, 0.0};
+    hji::StageArgs base{d_desc, d_tiles, d_ntiles, 0, 0, 0.0, 0.0, 0.0f, 0.0f, 0};
     cudaGraphExec_t exec = nullptr;
     const long long key[6] = {(long long)o->scheme, o->rk_order, chunk, grid, (long long)(uintptr_t)d_tiles,
                               (long long)total_tiles};
@@ -705,6 +755,256 @@ hji_status hji_value_transfer(hji_grid dst, hji_grid src, void* cuda_stream) {
     HJI_CUDA(dst, cudaStreamSynchronize(s));
     dst->cur = 0;
     dst->has_value = true;
+    return HJI_OK;
+}
+
+static hji_status efail(hji_engine e, hji_status st, const std::string& msg) {
+    if (e) e->err = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+static size_t grid_bytes(hji_grid g, int rk) {
+    const size_t field = (size_t)g->ncells * g->esize;
+    size_t n = 3 + (rk >= 2 ? 1 : 0) + (rk >= 3 ? 1 : 0) + (g->prec == HJI_F32 ? 1 : 0);
+    return n * field + g->table_bytes;
+}
+
+const char* hji_engine_last_error(hji_engine e) { return e ? e->err.c_str() : g_create_error.c_str(); }
+
+hji_status hji_engine_create(int ndim, hji_precision prec, const hji_solve_opts* o, int max_slots,
+                             size_t budget_bytes, void* cuda_stream, hji_engine* out) {
+    if (!out) return efail(nullptr, HJI_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (ndim < 1 || ndim > HJI_MAX_DIM) return efail(nullptr, HJI_E_INVALID, "ndim must be 1..4");
+    if (prec != HJI_F64 && prec != HJI_F32) return efail(nullptr, HJI_E_INVALID, "unknown precision");
+    if (max_slots < 1 || max_slots > 65535) return efail(nullptr, HJI_E_INVALID, "max_slots must be 1..65535");
+    hji_status st = validate_opts(nullptr, o);
+    if (st != HJI_OK) return st;
+    hji_engine e = new (std::nothrow) hji_engine_s();
+    if (!e) return efail(nullptr, HJI_E_NOMEM, "host allocation failed");
+    e->ndim = ndim;
+    e->prec = prec;
+    e->o = *o;
+    e->chunk = o->check_every > 0 ? o->check_every : 32;
+    e->max_slots = max_slots;
+    e->budget = budget_bytes;
+    e->s = (cudaStream_t)cuda_stream;
+    e->slots.resize(max_slots);
+    e->h_desc.resize(max_slots);
+    bool ok = cudaMalloc(&e->d_desc, sizeof(InstDesc) * max_slots) == cudaSuccess &&
+              cudaMalloc(&e->d_counts, sizeof(int) * 2) == cudaSuccess &&
+              cudaMallocHost(&e->h_counts, sizeof(int) * 2) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&e->ev, cudaEventDisableTiming) == cudaSuccess &&
+              cudaMemset(e->d_counts, 0, sizeof(int) * 2) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        hji_engine_destroy(e);
+        return efail(nullptr, HJI_E_NOMEM, "engine allocation failed");
+    }
+    e->grid = stage_grid(prec == HJI_F32, ndim, o->scheme, 1ll << 40);
+    *out = e;
+    return HJI_OK;
+}
+
+hji_status hji_engine_destroy(hji_engine e) {
+    if (!e) return HJI_OK;
+    cudaStreamSynchronize(e->s);
+    if (e->graph) cudaGraphExecDestroy(e->graph);
+    if (e->d_desc) cudaFree(e->d_desc);
+    if (e->d_counts) cudaFree(e->d_counts);
+    if (e->d_tiles) cudaFree(e->d_tiles);
+    if (e->h_counts) cudaFreeHost(e->h_counts);
+    if (e->cap) cudaStreamDestroy(e->cap);
+    if (e->ev) cudaEventDestroy(e->ev);
+    delete e;
+    return HJI_OK;
+}
+
+hji_status hji_engine_submit(hji_engine e, hji_grid g, const void* l, const void* k,
+                             int ptr_is_device, hji_init init, int64_t tag) {
+    if (!e) return efail(nullptr, HJI_E_INVALID, "engine is NULL");
+    if (!g || !l) return efail(e, HJI_E_INVALID, "grid and l must not be NULL");
+    if (g->ndim != e->ndim || g->prec != e->prec)
+        return efail(e, HJI_E_INVALID, "grid ndim/precision differ from the engine's");
+    if (!g->has_dyn) return efail(e, HJI_E_STATE, "dynamics not set");
+    if (init == HJI_INIT_USER_K && !k) return efail(e, HJI_E_INVALID, "HJI_INIT_USER_K needs k");
+    if (init == HJI_INIT_RESIDENT && !g->has_value)
+        return efail(e, HJI_E_STATE, "HJI_INIT_RESIDENT without a previous value");
+    if (init != HJI_INIT_STANDARD && init != HJI_INIT_USER_K && init != HJI_INIT_RESIDENT)
+        return efail(e, HJI_E_INVALID, "unknown init mode");
+    const int gw = hji::ghost_width(e->o.scheme);
+    for (int a = 0; a < g->ndim; ++a)
+        if (g->n[a] < 2 * gw + 1) return efail(e, HJI_E_INVALID, "grid too small for the stencil");
+    for (const auto& r : e->queue)
+        if (r.g == g) return efail(e, HJI_E_STATE, "grid already has a queued request");
+    for (const auto& sl : e->slots)
+        if (sl.used && sl.g == g) return efail(e, HJI_E_STATE, "grid already has a marching request");
+    hji_status st = ensure_buffers(g, e->o.rk_order, e->s);
+    if (st != HJI_OK) return efail(e, st, g->err);
+    if (e->budget && grid_bytes(g, e->o.rk_order) > e->budget)
+        return efail(e, HJI_E_INVALID, "grid larger than the engine's whole budget");
+    const size_t bytes = (size_t)g->ncells * g->esize;
+    const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t ce = cudaMemcpyAsync(g->l, l, bytes, kind, e->s);
+    if (ce == cudaSuccess && init == HJI_INIT_USER_K) ce = cudaMemcpyAsync(g->V[1], k, bytes, kind, e->s);
+    if (ce == cudaSuccess && !ptr_is_device) ce = cudaStreamSynchronize(e->s);
+    if (ce != cudaSuccess) return efail(e, HJI_E_CUDA, std::string("copy of l/k: ") + cudaGetErrorString(ce));
+    e->queue.push_back({g, tag, init, init == HJI_INIT_USER_K});
+    return HJI_OK;
+}
+
+static hji_status engine_retire(hji_engine e) {
+    int marching = 0;
+    for (const auto& sl : e->slots) marching += sl.used ? 1 : 0;
+    if (marching == 0 || e->h_counts[0] >= e->launched_active) return HJI_OK;
+    // Something stopped during the last chunk: find it from the states.
+    for (int i = 0; i < e->max_slots; ++i) {
+        auto& sl = e->slots[i];
+        if (!sl.used) continue;
+        cudaError_t ce = cudaMemcpyAsync(sl.g->h_state, sl.g->state, sizeof(InstState), cudaMemcpyDeviceToHost, e->s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->s);
+        if (ce != cudaSuccess) return efail(e, HJI_E_CUDA, std::string("state read: ") + cudaGetErrorString(ce));
+        const InstState& S = *sl.g->h_state;
+        if (!S.stop) continue;
+        hji_engine_s::Done d;
+        d.tag = sl.tag;
+        std::memset(&d.st, 0, sizeof(d.st));
+        d.st.steps = S.steps;
+        d.st.tau = S.tau;
+        d.st.dt = S.dt;
+        d.st.final_max_dV = S.last_delta;
+        d.st.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - sl.t0).count();
+        for (int a = 0; a < HJI_MAX_DIM; ++a) d.st.alpha[a] = a < sl.g->ndim ? S.alpha[a] : 0.0;
+        d.st.converged = S.converged;
+        if (S.nonfinite) d.status = HJI_E_INVALID;
+        else if (S.status == 2) d.status = HJI_E_INVALID;
+        else if (S.status == 1) d.status = HJI_E_NONFINITE;
+        else d.status = S.converged ? HJI_OK : HJI_E_NOT_CONVERGED;
+        sl.g->cur = S.cur;
+        sl.g->has_value = S.steps > 0 || sl.g->has_value;
+        e->done.push_back(d);
+        e->in_use -= sl.bytes;
+        sl = hji_engine_s::Slot();
+    }
+    return HJI_OK;
+}
+
+hji_status hji_engine_step(hji_engine e, int* active, int* queued) {
+    if (!e) return efail(nullptr, HJI_E_INVALID, "engine is NULL");
+    cudaError_t ce = cudaSuccess;
+    if (e->inflight) {
+        ce = cudaEventSynchronize(e->ev);
+        e->inflight = false;
+        if (ce != cudaSuccess) return efail(e, HJI_E_CUDA, std::string("chunk: ") + cudaGetErrorString(ce));
+        hji_status st = engine_retire(e);
+        if (st != HJI_OK) return st;
+    }
+    // Admit what fits (slots and budget), then publish the tile list and the
+    // marching count, and only then launch the admitted requests' set-up, so
+    // a set-up that stops an instance (no finite dt) decrements the published
+    // count.
+    const bool f32 = e->prec == HJI_F32;
+    std::vector<int> admitted;
+    while (!e->queue.empty()) {
+        const auto req = e->queue.front();
+        const size_t need = grid_bytes(req.g, e->o.rk_order);
+        if (e->budget && e->in_use + need > e->budget) break;
+        int slot = -1;
+        for (int i = 0; i < e->max_slots; ++i)
+            if (!e->slots[i].used) {
+                slot = i;
+                break;
+            }
+        if (slot < 0) break;
+        e->queue.pop_front();
+        e->h_desc[slot] = make_desc(req.g, &e->o, e->d_counts);
+        auto& sl = e->slots[slot];
+        sl.used = true;
+        sl.g = req.g;
+        sl.tag = req.tag;
+        sl.bytes = need;
+        sl.init = req.init;
+        sl.t0 = std::chrono::steady_clock::now();
+        e->in_use += need;
+        admitted.push_back(slot);
+    }
+    int marching = 0;
+    for (const auto& sl : e->slots) marching += sl.used ? 1 : 0;
+    if (!admitted.empty() || marching != e->launched_active) {
+        // Rebuild the tile list of the admitted slots (slot index = instance).
+        std::vector<unsigned long long> tiles;
+        for (int i = 0; i < e->max_slots; ++i)
+            if (e->slots[i].used)
+                for (long long t = 0; t < e->h_desc[i].ntiles; ++t) tiles.push_back(hji::make_tile(i, t));
+        if (tiles.size() > e->tiles_cap) {
+            if (e->d_tiles) cudaFreeAsync(e->d_tiles, e->s);
+            size_t cap = tiles.size() * 2;
+            if (cudaMallocAsync(&e->d_tiles, cap * sizeof(unsigned long long), e->s) != cudaSuccess) {
+                cudaGetLastError();
+                e->d_tiles = nullptr;
+                e->tiles_cap = 0;
+                return efail(e, HJI_E_NOMEM, "tile list allocation failed");
+            }
+            e->tiles_cap = cap;
+            if (e->graph) {
+                cudaGraphExecDestroy(e->graph);
+                e->graph = nullptr;
+            }
+        }
+        int counts[2] = {marching, (int)tiles.size()};
+        if (!tiles.empty())
+            ce = cudaMemcpyAsync(e->d_tiles, tiles.data(), tiles.size() * sizeof(unsigned long long),
+                                 cudaMemcpyHostToDevice, e->s);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(e->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, e->s);
+        if (ce != cudaSuccess) return efail(e, HJI_E_CUDA, std::string("tile list: ") + cudaGetErrorString(ce));
+    }
+    for (int slot : admitted) {
+        hji_grid g = e->slots[slot].g;
+        const hji_init init = e->slots[slot].init;
+        InstDesc& D = e->h_desc[slot];
+        const void* k = init == HJI_INIT_USER_K ? g->V[1] : (init == HJI_INIT_RESIDENT ? g->V[g->cur] : nullptr);
+        const int keep = init == HJI_INIT_RESIDENT ? 1 : 0;
+        const void* karr[1] = {k};
+        ce = cudaMemsetAsync(g->state, 0, sizeof(InstState), e->s);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(e->d_desc + slot, &D, sizeof(InstDesc), cudaMemcpyHostToDevice, e->s);
+        if (ce == cudaSuccess) ce = hji::launch_setup(e->d_desc + slot, &D, 1, f32, e->s);
+        if (ce == cudaSuccess) ce = hji::launch_init(e->d_desc + slot, &D, 1, f32, karr, &keep, e->s);
+        if (ce != cudaSuccess) return efail(e, HJI_E_CUDA, std::string("admission: ") + cudaGetErrorString(ce));
+    }
+    e->launched_active = marching;
+    if (marching > 0) {
+        if (!e->graph) {
+            hji::StageArgs base{e->d_desc, e->d_tiles, e->d_counts + 1, 0, 0, 0.0, 0.0, 0.0f, 0.0f, 0};
+            hji_status st = capture_chunk(nullptr, e->cap, f32, e->ndim, e->o.scheme, e->o.rk_order,
+                                          e->chunk, base, e->grid, &e->graph);
+            if (st != HJI_OK) return efail(e, st, g_create_error);
+        }
+        ce = cudaGraphLaunch(e->graph, e->s);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(e->h_counts, e->d_counts, sizeof(int) * 2, cudaMemcpyDeviceToHost, e->s);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e->ev, e->s);
+        if (ce != cudaSuccess) return efail(e, HJI_E_CUDA, std::string("launch: ") + cudaGetErrorString(ce));
+        e->inflight = true;
+    }
+    if (active) *active = marching;
+    if (queued) *queued = (int)e->queue.size();
+    return HJI_OK;
+}
+
+hji_status hji_engine_poll(hji_engine e, int64_t* tags, hji_solve_stats* stats, hji_status* status,
+                           int cap, int* count) {
+    if (!e || !count) return efail(e, HJI_E_INVALID, "engine and count must not be NULL");
+    int n = 0;
+    while (n < cap && !e->done.empty()) {
+        const auto& d = e->done.front();
+        if (tags) tags[n] = d.tag;
+        if (stats) stats[n] = d.st;
+        if (status) status[n] = d.status;
+        e->done.erase(e->done.begin());
+        ++n;
+    }
+    *count = n;
     return HJI_OK;
 }
 

@@ -112,6 +112,8 @@ struct StageArgs {
     int stage_in;          // 0: V[cur], 1: W1/D1, 2: W2/D2 (stencil input)
     int stage_out;         // 1: W1/D1, 2: W2/D2, 3: V[cur^1]
     double aV, aE;
+    float aVf, aEf;        // the same coefficients for FP32 kernels
+    int reads_v;           // aV != 0
 };
 
 using StageLauncher = cudaError_t (*)(const StageArgs&, int grid, cudaStream_t);

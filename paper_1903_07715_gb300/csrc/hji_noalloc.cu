@@ -274,7 +274,8 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
     for (;;) {
         for (int st = 0; st < chunk && e == cudaSuccess; ++st) {
             for (int i = 0; i < ns && e == cudaSuccess; ++i) {
-                hji::StageArgs a{d_desc, d_tiles, d_ints + 1, ins[i], outs[i], aV[i], aE[i]};
+                hji::StageArgs a{d_desc, d_tiles, d_ints + 1, ins[i], outs[i], aV[i], aE[i],
+                                 (float)aV[i], (float)aE[i], aV[i] != 0.0 ? 1 : 0};
                 e = L[i](a, (int)grid, s);
                 ++launches;
             }

@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(kThreads) alpha_kernel(const InstDesc* __restr
                 st->dt = 0.0;
                 st->status = 2;
                 st->stop = 1;
+                if (D.active != nullptr) atomicSub(D.active, 1);
             }
             __threadfence();
         }

@@ -28,10 +28,6 @@ template <>
 struct Num<double> {
     static __device__ __forceinline__ double weno_tiny() { return 1e-60; }
 };
-template <>
-struct Num<float> {
-    static __device__ __forceinline__ float weno_tiny() { return 1e-6f; }  // after normalising
-};
 
 template <int SCHEME>
 struct Ghost {
@@ -46,22 +42,18 @@ __device__ __forceinline__ T smaller_mag(T a, T b) {
     return fabs(a) <= fabs(b) ? a : b;
 }
 
-// HJ-WENO5 (Jiang and Peng) on undivided one-sided differences v1..v5.  The
-// nonlinear weights d_k / (S_k + eps)^2, normalised, are formed as
+// HJ-WENO5 (Jiang and Peng) on undivided one-sided differences v1..v5, with
+// eps = 1e-6 max(v^2) + tiny as in the textbook form (the relative part is
+// scale free, so undivided differences give the divided-difference weights).
+// FP64 forms the normalised weights d_k / (S_k + eps)^2 as
 // d_k q_k / sum_j d_j q_j with q_1 = (b2 b3)^2, q_2 = (b1 b3)^2,
-// q_3 = (b1 b2)^2, b_k = S_k + eps (the same ratios with one division).
-// eps = 1e-6 max(v^2) + tiny as in the textbook form; in FP32 the differences
-// are first scaled by 1/max|v| so that the products stay in range.
+// q_3 = (b1 b2)^2, b_k = S_k + eps: one division.  FP32 uses the fast
+// reciprocals r_k = 1/b_k, a_k = d_k r_k^2 and 1/sum a_k; tiny = 1e-18 keeps
+// sum a_k below 2^126 (the range of the fast division) while exceeding
+// 1e-6 max(v^2) only where every |v| < 1e-6 (flat data, where the weights do
+// not matter).
 template <typename T>
 __device__ __forceinline__ T weno5(T v1, T v2, T v3, T v4, T v5) {
-    T scale = T(1);
-    if constexpr (sizeof(T) == 4) {
-        T M = fmaxf(fmaxf(fmaxf(fabsf(v1), fabsf(v2)), fmaxf(fabsf(v3), fabsf(v4))), fabsf(v5));
-        if (M == 0.0f) return 0.0f;
-        T r = 1.0f / M;
-        v1 *= r; v2 *= r; v3 *= r; v4 *= r; v5 *= r;
-        scale = M;
-    }
     const T phi1 = v1 * T(1.0 / 3.0) - v2 * T(7.0 / 6.0) + v3 * T(11.0 / 6.0);
     const T phi2 = -v2 * T(1.0 / 6.0) + v3 * T(5.0 / 6.0) + v4 * T(1.0 / 3.0);
     const T phi3 = v3 * T(1.0 / 3.0) + v4 * T(5.0 / 6.0) - v5 * T(1.0 / 6.0);
@@ -71,20 +63,25 @@ __device__ __forceinline__ T weno5(T v1, T v2, T v3, T v4, T v5) {
     const T s1 = T(13.0 / 12.0) * a * a + T(0.25) * b * b;
     const T s2 = T(13.0 / 12.0) * c * c + T(0.25) * d * d;
     const T s3 = T(13.0 / 12.0) * e * e + T(0.25) * f * f;
-    T eps;
+    const T vm = fmax(fmax(fmax(v1 * v1, v2 * v2), fmax(v3 * v3, v4 * v4)), v5 * v5);
     if constexpr (sizeof(T) == 4) {
-        eps = Num<T>::weno_tiny();  // max(v^2) == 1 after scaling
+        const float eps = 1e-6f * vm + 1e-18f;
+        const float r1 = __fdividef(1.0f, s1 + eps);
+        const float r2 = __fdividef(1.0f, s2 + eps);
+        const float r3 = __fdividef(1.0f, s3 + eps);
+        const float a1 = 0.1f * (r1 * r1), a2 = 0.6f * (r2 * r2), a3 = 0.3f * (r3 * r3);
+        const float num = a1 * phi1 + a2 * phi2 + a3 * phi3;
+        return __fdividef(num, a1 + a2 + a3);
     } else {
-        T vm = fmax(fmax(fmax(v1 * v1, v2 * v2), fmax(v3 * v3, v4 * v4)), v5 * v5);
-        eps = T(1e-6) * vm + Num<T>::weno_tiny();
+        const T eps = T(1e-6) * vm + Num<T>::weno_tiny();
+        const T b1 = s1 + eps, b2 = s2 + eps, b3 = s3 + eps;
+        const T b12 = b1 * b2, b13 = b1 * b3, b23 = b2 * b3;
+        const T w1 = T(0.1) * (b23 * b23);
+        const T w2 = T(0.6) * (b13 * b13);
+        const T w3 = T(0.3) * (b12 * b12);
+        const T num = w1 * phi1 + w2 * phi2 + w3 * phi3;
+        return num / (w1 + w2 + w3);
     }
-    const T b1 = s1 + eps, b2 = s2 + eps, b3 = s3 + eps;
-    const T b12 = b1 * b2, b13 = b1 * b3, b23 = b2 * b3;
-    const T w1 = T(0.1) * (b23 * b23);
-    const T w2 = T(0.6) * (b13 * b13);
-    const T w3 = T(0.3) * (b12 * b12);
-    const T num = w1 * phi1 + w2 * phi2 + w3 * phi3;
-    return scale * (num / (w1 + w2 + w3));
 }
 
 // (p-, p+) at node c from the 2G undivided differences D[k] = W[k+1] - W[k]
@@ -299,7 +296,7 @@ __device__ inline void finish_step(const InstDesc& D) {
 }
 
 template <typename T, int NDIM, int SCHEME, bool LAST>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && NDIM <= 2) ? 6 : 1)
     stage_kernel(const StageArgs a) {
     constexpr int G = Ghost<SCHEME>::G;
     constexpr int TY = TileShape<NDIM>::TY;
@@ -314,14 +311,25 @@ __global__ void __launch_bounds__(kThreads)
 
     constexpr bool INCR = sizeof(T) == 4;  // FP32: increments + compensated V
     __shared__ TileCtx<T> C;
+    constexpr int DXW = SW - 1;            // differences along the fastest axis
+    constexpr int DYH = SH - 1;            // differences along the second axis
     __shared__ T th[SH * SW];              // high words of the stencil input
     __shared__ T tl[INCR ? SH * SW : 1];   // FP32: low words (+ stage increment)
-    __shared__ double red[kThreads / 32];
+    __shared__ T dxs[TY * DXW];            // dxs[r][c] = W(r, c+1) - W(r, c), tile rows
+    __shared__ T dys[NDIM >= 2 ? DYH * TX : 1];  // dys[r][c] = W(r+1, c) - W(r, c)
+    __shared__ T red[kThreads / 32];
 
     const int ntiles = *a.ntiles;
-    // Stage coefficients in the kernel's precision, converted once.
-    const T cV = static_cast<T>(a.aV), cE = static_cast<T>(a.aE);
-    const bool reads_v = a.aV != 0.0;
+    // Stage coefficients in the kernel's precision (no conversion in FP32).
+    T cV, cE;
+    if constexpr (INCR) {
+        cV = a.aVf;
+        cE = a.aEf;
+    } else {
+        cV = a.aV;
+        cE = a.aE;
+    }
+    const bool reads_v = a.reads_v != 0;
     const int tx = threadIdx.x % TX;
     const int ty = threadIdx.x / TX;
     int loaded = -1;
@@ -387,6 +395,22 @@ __global__ void __launch_bounds__(kThreads)
             if constexpr (INCR) tl[s] = v.l;
         }
         __syncthreads();
+        // Each neighbour difference once per tile (FP32: on the hi/lo pairs).
+        for (int i = threadIdx.x; i < TY * DXW; i += kThreads) {
+            const int r = i / DXW, c = i - r * DXW;
+            const int s0 = (r + GY) * SW + c;
+            if constexpr (INCR) dxs[i] = (th[s0 + 1] - th[s0]) + (tl[s0 + 1] - tl[s0]);
+            else dxs[i] = th[s0 + 1] - th[s0];
+        }
+        if constexpr (NDIM >= 2) {
+            for (int i = threadIdx.x; i < DYH * TX; i += kThreads) {
+                const int r = i / TX, c = i - r * TX;
+                const int s0 = r * SW + c + G;
+                if constexpr (INCR) dys[i] = (th[s0 + SW] - th[s0]) + (tl[s0 + SW] - tl[s0]);
+                else dys[i] = th[s0 + SW] - th[s0];
+            }
+        }
+        __syncthreads();
 
         // 2-5. Each thread updates CELLS nodes of the tile.
         T dmax = T(0);
@@ -399,21 +423,13 @@ __global__ void __launch_bounds__(kThreads)
             T D[2 * G];
             const int c0 = (ry + GY) * SW + (tx + G);  // this node in the shared tile
             const T wc = th[c0];
-            // Fastest axis: consecutive shared-memory entries.
+            // Fastest and second axes: the precomputed differences.
 #pragma unroll
-            for (int o = 0; o < 2 * G; ++o) {
-                const int i = c0 - G + o;
-                if constexpr (INCR) D[o] = (th[i + 1] - th[i]) + (tl[i + 1] - tl[i]);
-                else D[o] = th[i + 1] - th[i];
-            }
+            for (int o = 0; o < 2 * G; ++o) D[o] = dxs[ry * DXW + tx + o];
             one_sided_diffs<T, SCHEME>(D, C.inv_dx[AX], pm[AX], pp[AX]);
             if constexpr (NDIM >= 2) {
 #pragma unroll
-                for (int o = 0; o < 2 * G; ++o) {
-                    const int i = c0 + (o - G) * SW;
-                    if constexpr (INCR) D[o] = (th[i + SW] - th[i]) + (tl[i + SW] - tl[i]);
-                    else D[o] = th[i + SW] - th[i];
-                }
+                for (int o = 0; o < 2 * G; ++o) D[o] = dys[(ry + o) * TX + tx];
                 one_sided_diffs<T, SCHEME>(D, C.inv_dx[AY], pm[AY], pp[AY]);
             }
             const long long off = (long long)gy * sy + gx;  // within the plane
@@ -525,11 +541,12 @@ __global__ void __launch_bounds__(kThreads)
                 const T other = __shfl_xor_sync(0xffffffffu, dmax, o);
                 dmax = (other > dmax || other != other) ? other : dmax;
             }
-            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = static_cast<double>(dmax);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dmax;
             __syncthreads();
             if (threadIdx.x == 0) {
-                double m = red[0];
-                for (int w = 1; w < kThreads / 32; ++w) m = (red[w] > m || red[w] != red[w]) ? red[w] : m;
+                T mt = red[0];
+                for (int w = 1; w < kThreads / 32; ++w) mt = (red[w] > mt || red[w] != red[w]) ? red[w] : mt;
+                const double m = static_cast<double>(mt);
                 const InstDesc& D = a.insts[inst];
                 InstState* st = D.state;
                 atomicMax(&st->delta_bits, static_cast<unsigned long long>(__double_as_longlong(m)));

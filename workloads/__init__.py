@@ -209,3 +209,27 @@ def poisson_requests(rate=50.0, duration=60.0, seed=7715, quad_side=(31, 61),
         value = float(rng.uniform(*mass_scale)) if change == "mass" else float(rng.uniform(*dmax))
         out.append({"t": t, "kind": kind, "side": side, "change": change, "value": value})
     return out
+
+
+def serving_system(kind, side):
+    """A resident system of the serving workload: (grid, dynamics factory
+    taking (change, value), target l).  Double integrator: `mass` scales the
+    control gain to 1/m, `disturbance` sets |d| on the velocity equation.
+    Quadrotor 4-D subsystem: `disturbance` sets |d| on v; `mass` leaves the
+    dynamics as they are (the horizontal subsystem of Eq. (22) has no mass
+    term), so that update converges from the resident value at once."""
+    if kind == "di":
+        gd = grid([side, side], [-2.0, -2.0], [2.0, 2.0])
+        l = target_strip(gd, 0, 1.0)
+
+        def dyn(change, value):
+            if change == "mass":
+                return double_integrator(umax=1.0, b=1.0 / value, dmax=0.0)
+            return double_integrator(umax=1.0, dmax=value)
+        return gd, dyn, l
+    gd = grid([side] * 4, QUAD4D_BOX[0], QUAD4D_BOX[1])
+    l = target_strip(gd, 0, 4.0)
+
+    def dyn(change, value):
+        return quad4d(dmax=value if change == "disturbance" else 0.0)
+    return gd, dyn, l
