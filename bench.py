@@ -315,6 +315,7 @@ def main():
     if rank == 0 and not args.no_variants:
         line["time_to_converge"] = time_to_converge(hji, torch, gd, dyn, l, l_dev, k_dev)
         line["hbm_workloads"] = hbm_workloads(hji, torch)
+        line["serving"] = serving(hji, torch)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(budget_s=12.0)
     g.close()
@@ -409,6 +410,34 @@ def run_hbm_workload(args, hji, torch, dist, rank, world, local_rank):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def serving(hji, torch, duration=6.0, rate=50.0, time_cap=90.0):
+    """Config-5 serving: a Poisson stream (rate 50/s, seed 7715) of mass /
+    disturbance updates for quadrotor 4-D subsystems (sides 31, 41, 51, 61)
+    and 2-D double integrators (sides 201..1001 in steps of 200), each
+    warm-started from its system's resident previous value.  Every system is
+    solved once before the clock starts (untimed), so each timed request is
+    an update of a resident solution.  FP32 storage, FP64 convergence test,
+    ENO2/RK2, tol 1e-6 max|l|."""
+    from paper_1903_07715_gb300.serve import ReachabilityServer, summarize
+    quad_sides, di_sides = [31, 41, 51, 61], [201, 401, 601, 801, 1001]
+    rng = np.random.Generator(np.random.PCG64(7715))
+    reqs = W.poisson_requests(rate=rate, duration=duration, seed=7715)
+    for r in reqs:  # the stream's sizes, quantised to the resident systems
+        r["side"] = int(rng.choice(quad_sides if r["kind"] == "quad4d" else di_sides))
+    opts = dict(scheme="eno2", rk=2, cfl=0.5, tol=4e-6, max_steps=20000, check_every=16)
+    srv = ReachabilityServer(W.serving_system, precision="f32", max_slots=64, opts=opts)
+    warm = [{"t": 0.0, "kind": k, "side": s, "change": "disturbance", "value": 0.0}
+            for k, sides in (("quad4d", quad_sides), ("di", di_sides)) for s in sides]
+    srv.run(warm, time_cap=time_cap)
+    records, wall = srv.run(reqs, time_cap=time_cap)
+    srv.close()
+    out = summarize(records, wall)
+    out.update({"rate_per_s": rate, "stream_s": duration, "systems": len(warm),
+                "mix": "50% quad4d (31..61^4), 50% double integrator (201..1001^2); mass x "
+                       "U[1,1.5] or |d| ~ U[0,0.3]"})
+    return out
 
 
 def _measured_hbm():

@@ -131,7 +131,8 @@ typedef enum {
  * rk_order: 1, 2 or 3.  cfl in (0, 1].  tol >= 0: stop once max|dV| < tol.
  * horizon >= 0: stop once tau >= horizon (0 = none).  max_steps: step cap
  * (<= 0 means 1,000,000).  check_every: steps per host check of the stop
- * flag (<= 0 means 32); steps after the stop point never run. */
+ * flag (<= 0 means 32); steps after the stop point never run.  Results do
+ * not depend on check_every or the tile shape. */
 typedef struct {
     hji_scheme scheme;
     int rk_order;
@@ -141,6 +142,8 @@ typedef struct {
     int check_every;
     int64_t max_steps;
     hji_init init;
+    int tile_variant; /* 0: the autotuned (else default) tile shape;
+                         1..HJI_TILE_VARIANTS: force shape tile_variant-1 (2-D) */
 } hji_solve_opts;
 
 typedef struct {
@@ -264,6 +267,20 @@ hji_status hji_engine_poll(hji_engine e, int64_t* tags, hji_solve_stats* stats,
 
 hji_status hji_engine_destroy(hji_engine e);
 const char* hji_engine_last_error(hji_engine e);
+
+/* Tile-shape autotuner.  2-D grids can be marched with HJI_TILE_VARIANTS
+ * tile shapes (16x32, 8x32 and 32x32 nodes); this times `steps` steps of a
+ * standard march of grid g (dynamics set, target l) with each and remembers
+ * the fastest for this precision, ndim, scheme, RK order and grid-size class
+ * (log2 of the node count).  Later hji_solve, hji_batch_solve and engines
+ * of that class use it (the nearest tuned size class; untuned: variant 0).
+ * The timing march overwrites g's value.  chosen (may be NULL) receives the
+ * variant; ms_per_step (may be NULL, HJI_TILE_VARIANTS entries) the wall
+ * time per step of each variant (-1 where not applicable).  Grids of other
+ * dimensionality have one shape (chosen = 0). */
+#define HJI_TILE_VARIANTS 3
+hji_status hji_autotune(hji_grid g, const void* l, int ptr_is_device, const hji_solve_opts* o,
+                        int steps, void* cuda_stream, int* chosen, double* ms_per_step);
 
 /* Grid facts: ndim, n[], and the number of nodes (may be NULL each). */
 hji_status hji_grid_info(hji_grid g, int* ndim, int64_t* n, int64_t* num_nodes);

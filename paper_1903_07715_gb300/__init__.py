@@ -20,6 +20,7 @@ import numpy as np
 from . import build as _build
 
 HJI_MAX_DIM, HJI_MAX_INPUTS, HJI_MAX_TERMS = 4, 4, 8
+HJI_TILE_VARIANTS = 3
 
 HJI_OK, HJI_E_INVALID, HJI_E_NOMEM, HJI_E_CUDA = 0, 1, 2, 3
 HJI_E_NOT_CONVERGED, HJI_E_TIMEOUT, HJI_E_STATE, HJI_E_NONFINITE = 4, 5, 6, 7
@@ -33,7 +34,7 @@ EXPORTS = ["hji_grid_create", "hji_grid_destroy", "hji_dynamics_set", "hji_solve
            "hji_batch_solve", "hji_value_get", "hji_value_transfer", "hji_grid_info",
            "hji_status_string", "hji_last_error", "hji_solve_noalloc", "hji_noalloc_last_error",
            "hji_engine_create", "hji_engine_submit", "hji_engine_step", "hji_engine_poll",
-           "hji_engine_destroy", "hji_engine_last_error"]
+           "hji_engine_destroy", "hji_engine_last_error", "hji_autotune"]
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -59,7 +60,7 @@ class hji_solve_opts(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int), ("rk_order", ctypes.c_int), ("cfl", ctypes.c_double),
                 ("tol", ctypes.c_double), ("horizon", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("max_steps", ctypes.c_int64),
-                ("init", ctypes.c_int)]
+                ("init", ctypes.c_int), ("tile_variant", ctypes.c_int)]
 
 
 class hji_solve_stats(ctypes.Structure):
@@ -122,6 +123,9 @@ def load(build_if_missing=False):
     lib.hji_engine_step.argtypes = [vp, ip, ip]
     lib.hji_engine_poll.argtypes = [vp, i64p, ctypes.POINTER(hji_solve_stats), ip, ctypes.c_int, ip]
     lib.hji_engine_destroy.argtypes = [vp]
+    lib.hji_autotune.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(hji_solve_opts),
+                                 ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_double)]
     lib.hji_engine_last_error.argtypes = [vp]
     lib.hji_engine_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -173,6 +177,10 @@ def hji_solve_noalloc(ndim, n, lo, hi, periodic, prec, dyn, l, k, v_out, opts, s
 
 def hji_noalloc_last_error():
     return load().hji_noalloc_last_error().decode()
+
+
+def hji_autotune(g, l, ptr_is_device, opts, steps, stream, chosen, ms_per_step):
+    return load().hji_autotune(g, l, ptr_is_device, opts, steps, stream, chosen, ms_per_step)
 
 
 def hji_engine_create(ndim, prec, opts, max_slots, budget_bytes, stream, out):
@@ -285,9 +293,9 @@ def _stats_dict(st):
 
 
 def solve_opts(scheme="eno2", rk=2, cfl=0.5, tol=1e-6, horizon=0.0, max_steps=0,
-               check_every=32, init=HJI_INIT_STANDARD):
+               check_every=32, init=HJI_INIT_STANDARD, tile_variant=0):
     return hji_solve_opts(SCHEMES[scheme] if isinstance(scheme, str) else scheme, rk, cfl, tol,
-                          horizon, check_every, max_steps, init)
+                          horizon, check_every, max_steps, init, tile_variant)
 
 
 class Grid:
@@ -369,6 +377,17 @@ class Grid:
         if isinstance(out, np.ndarray) and keep is not out:
             out[...] = keep
         return out
+
+    def autotune(self, l, steps=20, stream=None, **opts):
+        """hji_autotune: time each tile shape on this grid, remember the
+        fastest for its class; returns (chosen, ms per step per variant)."""
+        lp, ldev, keep = self._ptr(l)
+        o = solve_opts(**opts)
+        chosen = ctypes.c_int()
+        ms = (ctypes.c_double * HJI_TILE_VARIANTS)()
+        _check(hji_autotune(self._h, lp, ldev, ctypes.byref(o), int(steps), self._stream(stream),
+                            ctypes.byref(chosen), ms), self._h)
+        return chosen.value, list(ms)
 
     def take_value(self, other, stream=None):
         """Make `other`'s current value this grid's resident value (device-side

@@ -11,6 +11,8 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -55,7 +57,7 @@ struct hji_grid_s {
     std::string err;
     // Graph cache for single-grid solves.
     cudaGraphExec_t graph = nullptr;
-    long long graph_key[6] = {0, 0, 0, 0, 0, 0};
+    long long graph_key[7] = {0, 0, 0, 0, 0, 0, 0};
     cudaStream_t cap_stream = nullptr;
 };
 
@@ -76,6 +78,7 @@ struct hji_engine_s {
     int* h_counts = nullptr;          // pinned mirror of d_counts
     cudaGraphExec_t graph = nullptr;
     int grid = 0;
+    int variant = 0;
     cudaEvent_t ev = nullptr;
     bool inflight = false;
     int launched_active = 0;          // instances marching when the chunk was launched
@@ -180,16 +183,16 @@ int rk_plan(int rk, StagePlan* p) {
     return 3;
 }
 
-hji::StageLauncher launcher(bool f32, int ndim, int scheme, bool last) {
-    return f32 ? hji::stage_launcher_f32(ndim, scheme, last)
-               : hji::stage_launcher_f64(ndim, scheme, last);
+hji::StageLauncher launcher(bool f32, int ndim, int scheme, bool last, int variant) {
+    return f32 ? hji::stage_launcher_f32(ndim, scheme, last, variant)
+               : hji::stage_launcher_f64(ndim, scheme, last, variant);
 }
 
-int stage_grid(bool f32, int ndim, int scheme, long long total_tiles) {
+int stage_grid(bool f32, int ndim, int scheme, long long total_tiles, int variant) {
     int per_sm = 1;
     for (int last = 0; last < 2; ++last) {
-        const int b = f32 ? hji::stage_max_blocks_f32(ndim, scheme, last)
-                          : hji::stage_max_blocks_f64(ndim, scheme, last);
+        const int b = f32 ? hji::stage_max_blocks_f32(ndim, scheme, last, variant)
+                          : hji::stage_max_blocks_f64(ndim, scheme, last, variant);
         per_sm = last == 0 ? b : (b < per_sm ? b : per_sm);
     }
     long long g = (long long)num_sms() * per_sm;
@@ -197,9 +200,49 @@ int stage_grid(bool f32, int ndim, int scheme, long long total_tiles) {
     return g < 1 ? 1 : (int)g;
 }
 
-void tile_grid(int ndim, const int64_t* n, long long& tx, long long& ty, long long& planes) {
-    const int TX = ndim == 1 ? hji::TileShape<1>::TX : hji::TileShape<2>::TX;
-    const int TY = ndim == 1 ? hji::TileShape<1>::TY : hji::TileShape<2>::TY;
+// ---- tile-shape choices made by hji_autotune, per problem class ----
+std::mutex g_tune_mu;
+std::map<std::vector<long long>, int> g_tune;
+int g_force_variant = -1;  // set only while hji_autotune times a variant
+
+int size_bucket(long long cells) {
+    int b = 0;
+    while (cells > 1) {
+        cells >>= 1;
+        ++b;
+    }
+    return b;
+}
+
+std::vector<long long> tune_key(hji_precision prec, int ndim, const hji_solve_opts* o, int bucket) {
+    return {(long long)prec, ndim, (long long)o->scheme, o->rk_order, bucket};
+}
+
+// The tile shape for a launch: the autotuned choice for this class (the
+// nearest tuned size bucket), else variant 0.
+int pick_variant(hji_precision prec, int ndim, const hji_solve_opts* o, long long cells) {
+    if (ndim != 2) return 0;
+    if (g_force_variant >= 0) return g_force_variant;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const int b = size_bucket(cells);
+    int best = 0, dist = 1 << 30;
+    for (const auto& kv : g_tune) {
+        const auto& k = kv.first;
+        if (k[0] != (long long)prec || k[1] != ndim || k[2] != (long long)o->scheme || k[3] != o->rk_order)
+            continue;
+        const int d = (int)(k[4] > b ? k[4] - b : b - k[4]);
+        if (d < dist) {
+            dist = d;
+            best = kv.second;
+        }
+    }
+    return best;
+}
+
+void tile_grid(int ndim, const int64_t* n, long long& tx, long long& ty, long long& planes,
+               int variant) {
+    int TY, TX;
+    hji::tile_dims(ndim, variant, TY, TX);
     tx = (n[ndim - 1] + TX - 1) / TX;
     ty = ndim >= 2 ? (n[ndim - 2] + TY - 1) / TY : 1;
     planes = 1;
@@ -217,6 +260,8 @@ hji_status validate_opts(hji_grid g, const hji_solve_opts* o) {
         return fail(g, HJI_E_INVALID, "horizon must be finite and >= 0");
     if (o->init != HJI_INIT_STANDARD && o->init != HJI_INIT_USER_K && o->init != HJI_INIT_RESIDENT)
         return fail(g, HJI_E_INVALID, "unknown init mode");
+    if (o->tile_variant < 0 || o->tile_variant > hji::kTileVariants)
+        return fail(g, HJI_E_INVALID, "tile_variant must be 0..HJI_TILE_VARIANTS");
     return HJI_OK;
 }
 
@@ -242,7 +287,7 @@ hji_status ensure_buffers(hji_grid g, int rk, cudaStream_t s) {
     return HJI_OK;
 }
 
-InstDesc make_desc(hji_grid g, const hji_solve_opts* o, int* active) {
+InstDesc make_desc(hji_grid g, const hji_solve_opts* o, int* active, int variant) {
     InstDesc D;
     std::memset(&D, 0, sizeof(D));
     D.ndim = g->ndim;
@@ -276,7 +321,7 @@ InstDesc make_desc(hji_grid g, const hji_solve_opts* o, int* active) {
     D.history = nullptr;
     D.history_len = 0;
     long long tx, ty, planes;
-    tile_grid(g->ndim, g->n, tx, ty, planes);
+    tile_grid(g->ndim, g->n, tx, ty, planes, variant);
     D.tiles_x = tx;
     D.tiles_y = ty;
     D.tiles_per_plane = tx * ty;
@@ -288,12 +333,13 @@ InstDesc make_desc(hji_grid g, const hji_solve_opts* o, int* active) {
 
 // Capture `steps` steps of the march (all RK stages) into a graph.
 hji_status capture_chunk(hji_grid g, cudaStream_t cap, bool f32, int ndim, int scheme, int rk,
-                         int steps, const hji::StageArgs& base, int grid, cudaGraphExec_t* out) {
+                         int steps, const hji::StageArgs& base, int grid, int variant,
+                         cudaGraphExec_t* out) {
     StagePlan plan[3];
     const int ns = rk_plan(rk, plan);
     hji::StageLauncher L[3];
     for (int i = 0; i < ns; ++i) {
-        L[i] = launcher(f32, ndim, scheme, plan[i].last);
+        L[i] = launcher(f32, ndim, scheme, plan[i].last, variant);
         if (!L[i]) return fail(g, HJI_E_INVALID, "no kernel for this ndim/scheme");
     }
     HJI_CUDA(g, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
@@ -355,6 +401,12 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
     }
     const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
 
+    // The tile shape for this launch (autotuned per class, else variant 0).
+    long long cells_all = 0;
+    for (int i = 0; i < count; ++i) cells_all += grids[i]->ncells;
+    int variant = pick_variant(g0->prec, ndim, o, cells_all / count);
+    if (o->tile_variant > 0 && g_force_variant < 0)
+        variant = (ndim == 2 && o->tile_variant <= hji::kTileVariants) ? o->tile_variant - 1 : 0;
     // Batch-wide device scratch: descriptors, tile list, active counter.
     std::vector<InstDesc> H(count);
     InstDesc* d_desc = g0->d_desc;
@@ -365,7 +417,7 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
     long long total_tiles = 0;
     for (int i = 0; i < count; ++i) {
         long long tx, ty, planes;
-        tile_grid(ndim, grids[i]->n, tx, ty, planes);
+        tile_grid(ndim, grids[i]->n, tx, ty, planes, variant);
         total_tiles += tx * ty * planes;
     }
     if (total_tiles >= (1ll << 31)) return fail(g0, HJI_E_INVALID, "too many tiles");
@@ -431,7 +483,7 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
             kptr[i] = g->V[g->cur];
             keep_lo[i] = 1;
         }
-        H[i] = make_desc(g, o, d_active);
+        H[i] = make_desc(g, o, d_active, variant);
         for (long long t = 0; t < H[i].ntiles; ++t) tiles.push_back(hji::make_tile(i, t));
         e = cudaMemsetAsync(g->state, 0, sizeof(InstState), s);
         if (e != cudaSuccess) {
@@ -477,11 +529,11 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
 
     // The march: graphs of `chunk` steps, one in flight ahead of the check.
     const int chunk = o->check_every > 0 ? o->check_every : 32;
-    const int grid = stage_grid(f32, ndim, o->scheme, total_tiles);
+    const int grid = stage_grid(f32, ndim, o->scheme, total_tiles, variant);
     hji::StageArgs base{d_desc, d_tiles, d_ntiles, 0, 0, 0.0, 0.0, 0.0f, 0.0f, 0};
     cudaGraphExec_t exec = nullptr;
-    const long long key[6] = {(long long)o->scheme, o->rk_order, chunk, grid, (long long)(uintptr_t)d_tiles,
-                              (long long)total_tiles};
+    const long long key[7] = {(long long)o->scheme, o->rk_order, chunk, grid, (long long)(uintptr_t)d_tiles,
+                              (long long)total_tiles, variant};
     if (!own_batch && g0->graph && std::memcmp(key, g0->graph_key, sizeof(key)) == 0) {
         exec = g0->graph;
     } else {
@@ -489,7 +541,8 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
             cudaGraphExecDestroy(g0->graph);
             g0->graph = nullptr;
         }
-        st = capture_chunk(g0, g0->cap_stream, f32, ndim, o->scheme, o->rk_order, chunk, base, grid, &exec);
+        st = capture_chunk(g0, g0->cap_stream, f32, ndim, o->scheme, o->rk_order, chunk, base, grid,
+                           variant, &exec);
         if (st != HJI_OK) {
             cleanup();
             return st;
@@ -803,7 +856,8 @@ hji_status hji_engine_create(int ndim, hji_precision prec, const hji_solve_opts*
         hji_engine_destroy(e);
         return efail(nullptr, HJI_E_NOMEM, "engine allocation failed");
     }
-    e->grid = stage_grid(prec == HJI_F32, ndim, o->scheme, 1ll << 40);
+    e->variant = pick_variant(prec, ndim, o, 1ll << 20);
+    e->grid = stage_grid(prec == HJI_F32, ndim, o->scheme, 1ll << 40, e->variant);
     *out = e;
     return HJI_OK;
 }
@@ -919,7 +973,7 @@ hji_status hji_engine_step(hji_engine e, int* active, int* queued) {
             }
         if (slot < 0) break;
         e->queue.pop_front();
-        e->h_desc[slot] = make_desc(req.g, &e->o, e->d_counts);
+        e->h_desc[slot] = make_desc(req.g, &e->o, e->d_counts, e->variant);
         auto& sl = e->slots[slot];
         sl.used = true;
         sl.g = req.g;
@@ -978,7 +1032,7 @@ hji_status hji_engine_step(hji_engine e, int* active, int* queued) {
         if (!e->graph) {
             hji::StageArgs base{e->d_desc, e->d_tiles, e->d_counts + 1, 0, 0, 0.0, 0.0, 0.0f, 0.0f, 0};
             hji_status st = capture_chunk(nullptr, e->cap, f32, e->ndim, e->o.scheme, e->o.rk_order,
-                                          e->chunk, base, e->grid, &e->graph);
+                                          e->chunk, base, e->grid, e->variant, &e->graph);
             if (st != HJI_OK) return efail(e, st, g_create_error);
         }
         ce = cudaGraphLaunch(e->graph, e->s);
@@ -1005,6 +1059,46 @@ hji_status hji_engine_poll(hji_engine e, int64_t* tags, hji_solve_stats* stats, 
         ++n;
     }
     *count = n;
+    return HJI_OK;
+}
+
+hji_status hji_autotune(hji_grid g, const void* l, int ptr_is_device, const hji_solve_opts* o,
+                        int steps, void* cuda_stream, int* chosen, double* ms_per_step) {
+    if (!g) return fail(nullptr, HJI_E_INVALID, "grid is NULL");
+    hji_status st = validate_opts(g, o);
+    if (st != HJI_OK) return st;
+    if (steps < 1) return fail(g, HJI_E_INVALID, "steps must be >= 1");
+    hji_solve_opts t = *o;
+    t.tol = 0.0;
+    t.horizon = 0.0;
+    t.max_steps = steps;
+    t.check_every = steps;
+    t.init = HJI_INIT_STANDARD;
+    const int nvar = g->ndim == 2 ? hji::kTileVariants : 1;
+    double best_ms = 1e300;
+    int best = 0;
+    for (int v = 0; v < hji::kTileVariants; ++v) {
+        if (ms_per_step) ms_per_step[v] = -1.0;
+        if (v >= nvar) continue;
+        g_force_variant = v;
+        hji_solve_stats s1, s2;
+        hji_status r = hji_solve(g, l, nullptr, ptr_is_device, &t, cuda_stream, &s1);  // warm-up
+        if (r == HJI_OK || r == HJI_E_NOT_CONVERGED)
+            r = hji_solve(g, l, nullptr, ptr_is_device, &t, cuda_stream, &s2);
+        g_force_variant = -1;
+        if (r != HJI_OK && r != HJI_E_NOT_CONVERGED) return r;
+        const double ms = s2.wall_ms / (double)(s2.steps > 0 ? s2.steps : 1);
+        if (ms_per_step) ms_per_step[v] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[tune_key(g->prec, g->ndim, o, size_bucket(g->ncells))] = best;
+    }
+    if (chosen) *chosen = best;
     return HJI_OK;
 }
 

@@ -84,14 +84,28 @@ __host__ __device__ inline unsigned long long make_tile(int inst, long long loca
            (static_cast<unsigned long long>(local) & 0xFFFFFFFFFFFFull);
 }
 
-// Tile shape per dimensionality: 1-D tiles are 256 nodes of one row; N-D
-// tiles are 16 x 32 nodes of the two fastest axes at a fixed index of the
-// slower axes (which are read from global memory / L2 directly).
-template <int NDIM>
+// Tile shapes.  1-D tiles are 256 nodes of one row.  N-D tiles cover the
+// two fastest axes at a fixed index of the slower axes (which are read from
+// global memory / L2 directly): variant 0 is 16 x 32 nodes, and 2-D grids
+// also have variant 1 (8 x 32: finer work units, better balance on small
+// grids) and variant 2 (32 x 32: less halo per node on large grids), chosen
+// per problem class by the autotuner.
+constexpr int kTileVariants = 3;
+template <int NDIM, int V = 0>
 struct TileShape {
-    static constexpr int TY = (NDIM == 1) ? 1 : 16;
+    static constexpr int TY = (NDIM == 1) ? 1 : (V == 1 ? 8 : (V == 2 ? 32 : 16));
     static constexpr int TX = (NDIM == 1) ? 256 : 32;
 };
+inline void tile_dims(int ndim, int variant, int& ty, int& tx) {
+    if (ndim == 1) {
+        ty = 1;
+        tx = 256;
+        return;
+    }
+    const int v = ndim == 2 ? variant : 0;
+    ty = v == 1 ? 8 : (v == 2 ? 32 : 16);
+    tx = 32;
+}
 
 inline int ghost_width(int scheme) { return scheme == HJI_ENO1 ? 1 : (scheme == HJI_ENO2 ? 2 : 3); }
 
@@ -118,11 +132,12 @@ struct StageArgs {
 
 using StageLauncher = cudaError_t (*)(const StageArgs&, int grid, cudaStream_t);
 
-// Kernel dispatch tables (one per precision).
-StageLauncher stage_launcher_f64(int ndim, int scheme, bool last);
-StageLauncher stage_launcher_f32(int ndim, int scheme, bool last);
-int stage_max_blocks_f64(int ndim, int scheme, bool last);
-int stage_max_blocks_f32(int ndim, int scheme, bool last);
+// Kernel dispatch tables (one per precision); `variant` selects the tile
+// shape (only 2-D grids have more than variant 0).
+StageLauncher stage_launcher_f64(int ndim, int scheme, bool last, int variant = 0);
+StageLauncher stage_launcher_f32(int ndim, int scheme, bool last, int variant = 0);
+int stage_max_blocks_f64(int ndim, int scheme, bool last, int variant = 0);
+int stage_max_blocks_f32(int ndim, int scheme, bool last, int variant = 0);
 
 // Set-up kernels (hji_setup.cu).
 cudaError_t launch_setup(const InstDesc* d_insts, const InstDesc* h_insts, int count, bool f32,

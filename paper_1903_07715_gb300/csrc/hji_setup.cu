@@ -33,19 +33,41 @@ __global__ void __launch_bounds__(kThreads) table_kernel(const InstDesc* __restr
     }
 }
 
+constexpr int kAlphaTab = 2048;  // term values cached per CTA (FP64)
+
 __global__ void __launch_bounds__(kThreads) alpha_kernel(const InstDesc* __restrict__ d) {
     const InstDesc& D = *d;
     const int nd = D.ndim;
     const Dyn& f = D.dyn;
+    // w_t phi_t(x) depends on one coordinate: tabulate it once per CTA when
+    // the term axes are short enough, instead of once per node.
+    __shared__ double tab[kAlphaTab];
+    __shared__ int tab_off[MAXT];
+    int total = 0;
+    for (int t = 0; t < f.nterms; ++t) total += D.n[f.term_axis[t]];
+    const bool use_tab = total <= kAlphaTab;
+    if (use_tab) {
+        int o = 0;
+        for (int t = 0; t < f.nterms; ++t) {
+            if (threadIdx.x == 0) tab_off[t] = o;
+            const int ax = f.term_axis[t];
+            for (int i = threadIdx.x; i < D.n[ax]; i += blockDim.x)
+                tab[o + i] = f.term_w[t] * apply_fn(f.term_fn[t], D.lo[ax] + (double)i * D.dx[ax]);
+            o += D.n[ax];
+        }
+    }
+    __syncthreads();
     double amax[MAXD] = {0.0, 0.0, 0.0, 0.0};
     double rmax = 0.0;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < D.ncells;
          c += (long long)gridDim.x * blockDim.x) {
         double x[MAXD];
+        int ix[MAXD];
         long long r = c;
         for (int a = nd - 1; a >= 0; --a) {
             const long long i = r % D.n[a];
             r /= D.n[a];
+            ix[a] = (int)i;
             x[a] = D.lo[a] + (double)i * D.dx[a];
         }
         double rate = 0.0;
@@ -55,7 +77,9 @@ __global__ void __launch_bounds__(kThreads) alpha_kernel(const InstDesc* __restr
             double centre = f.c[a], radius = 0.0;
             for (int b = 0; b < nd; ++b) centre += f.A[a * MAXD + b] * x[b];
             for (int t = 0; t < f.nterms; ++t)
-                if (f.term_row[t] == a) centre += f.term_w[t] * apply_fn(f.term_fn[t], x[f.term_axis[t]]);
+                if (f.term_row[t] == a)
+                    centre += use_tab ? tab[tab_off[t] + ix[f.term_axis[t]]]
+                                      : f.term_w[t] * apply_fn(f.term_fn[t], x[f.term_axis[t]]);
             for (int j = 0; j < f.m; ++j) {
                 centre += f.G[a * MAXU + j] * (0.5 * (f.ulo[j] + f.uhi[j]));
                 radius += fabs(f.G[a * MAXU + j]) * (0.5 * (f.uhi[j] - f.ulo[j]));

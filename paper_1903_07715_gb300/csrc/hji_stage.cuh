@@ -295,28 +295,126 @@ __device__ inline void finish_step(const InstDesc& D) {
     __threadfence();
 }
 
-template <typename T, int NDIM, int SCHEME, bool LAST>
-__global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && NDIM <= 2) ? 6 : 1)
+// ---- asynchronous global -> shared copies (cp.async, 4 or 8 bytes) ----
+template <int B>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(B)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Dynamic shared-memory layout of one stage kernel (units of T): two
+// buffers of the staged tile (high words; FP32 also low words and stage
+// increments), two buffers of l (and, FP64, of V^n) for the tile nodes, and
+// the per-tile neighbour differences.
+template <typename T, int NDIM, int SCHEME, bool LAST, int V>
+struct StageSmem {
+    static constexpr int G = Ghost<SCHEME>::G;
+    static constexpr int TY = TileShape<NDIM, V>::TY;
+    static constexpr int TX = TileShape<NDIM, V>::TX;
+    static constexpr int GY = (NDIM >= 2) ? G : 0;
+    static constexpr int SW = TX + 2 * G;
+    static constexpr int SH = TY + 2 * GY;
+    static constexpr int NR = SH * SW;
+    static constexpr int NI = TY * TX;
+    static constexpr int DXW = SW - 1;
+    static constexpr int DYH = SH - 1;
+    static constexpr bool INCR = sizeof(T) == 4;
+    static constexpr int RH = 0;
+    static constexpr int RL = RH + 2 * NR;
+    static constexpr int RD = RL + (INCR ? 2 * NR : 0);
+    static constexpr int LT = RD + (INCR ? 2 * NR : 0);
+    static constexpr int VN = LT + (LAST ? 2 * NI : 0);
+    static constexpr int DX = VN + ((LAST && !INCR) ? 2 * NI : 0);
+    static constexpr int DY = DX + TY * DXW;
+    static constexpr int NT = DY + (NDIM >= 2 ? DYH * TX : 0);
+    static constexpr size_t BYTES = NT * sizeof(T);
+};
+
+// Where tile `local` of an instance sits.  N-D tiles are enumerated with the
+// last slow axis fastest, so consecutive tiles of a CTA's run are neighbours
+// along that axis and share most of their slow-axis stencil lines in L1.
+struct TileGeo {
+    long long base;
+    int sidx[MAXD];
+    int y0, x0;
+};
+
+template <typename T, int NDIM, int TY, int TX>
+__device__ __forceinline__ TileGeo tile_geo(const TileCtx<T>& C, long long local) {
+    TileGeo g;
+    long long tip = local;
+    g.base = 0;
+    if constexpr (NDIM >= 3) {
+        long long r = local;
+        const int ls = NDIM - 3;  // last slow axis
+        g.sidx[ls] = static_cast<int>(r % C.n[ls]);
+        r /= C.n[ls];
+        tip = r % C.tiles_per_plane;
+        r /= C.tiles_per_plane;
+        for (int ax = ls - 1; ax >= 0; --ax) {
+            g.sidx[ax] = static_cast<int>(r % C.n[ax]);
+            r /= C.n[ax];
+        }
+        for (int ax = 0; ax <= ls; ++ax) g.base += (long long)g.sidx[ax] * C.stride[ax];
+    }
+    const int by = static_cast<int>(tip / C.tiles_x);
+    const int bx = static_cast<int>(tip - (long long)by * C.tiles_x);
+    g.y0 = by * TY;
+    g.x0 = bx * TX;
+    return g;
+}
+
+// The CTA's walk over the tile list: runs of R consecutive tiles, run r
+// going to CTA r mod gridDim (R = 1, plain cyclic, for short lists; up to 8
+// for long ones, where consecutive tiles share an instance context).
+struct TileWalk {
+    int R, nruns, ntiles, ti, run, rr;
+    __device__ TileWalk(int n) : ntiles(n) {
+        R = max(1, min(8, n / (static_cast<int>(gridDim.x) * 4)));
+        nruns = (n + R - 1) / R;
+        run = blockIdx.x;
+        ti = run * R;
+        rr = 0;
+    }
+    __device__ int next() {
+        if (run >= nruns) return -1;
+        const int t = ti;
+        if (++rr == R || ti + 1 >= ntiles) {
+            run += gridDim.x;
+            ti = run * R;
+            rr = 0;
+        } else {
+            ++ti;
+        }
+        return t;
+    }
+};
+
+template <typename T, int NDIM, int SCHEME, bool LAST, int V>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 5 : 3) : 3)
     stage_kernel(const StageArgs a) {
-    constexpr int G = Ghost<SCHEME>::G;
-    constexpr int TY = TileShape<NDIM>::TY;
-    constexpr int TX = TileShape<NDIM>::TX;
-    constexpr int GY = (NDIM >= 2) ? G : 0;
-    constexpr int SW = TX + 2 * G;   // shared tile width
-    constexpr int SH = TY + 2 * GY;  // shared tile height
+    using L = StageSmem<T, NDIM, SCHEME, LAST, V>;
+    constexpr int G = L::G, TY = L::TY, TX = L::TX, GY = L::GY, SW = L::SW, SH = L::SH;
+    constexpr int NR = L::NR, NI = L::NI, DXW = L::DXW, DYH = L::DYH;
     constexpr int ROWS_PER_PASS = kThreads / TX;
     constexpr int CELLS = (TY + ROWS_PER_PASS - 1) / ROWS_PER_PASS;
     constexpr int AX = NDIM - 1;  // fastest axis
     constexpr int AY = NDIM >= 2 ? NDIM - 2 : 0;  // second fastest axis (used if NDIM >= 2)
+    constexpr bool INCR = L::INCR;  // FP32: increments + compensated V
 
-    constexpr bool INCR = sizeof(T) == 4;  // FP32: increments + compensated V
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    T* dxs = sm + L::DX;  // dxs[r][c] = W(r, c+1) - W(r, c), tile rows
+    T* dys = sm + L::DY;  // dys[r][c] = W(r+1, c) - W(r, c)
     __shared__ TileCtx<T> C;
-    constexpr int DXW = SW - 1;            // differences along the fastest axis
-    constexpr int DYH = SH - 1;            // differences along the second axis
-    __shared__ T th[SH * SW];              // high words of the stencil input
-    __shared__ T tl[INCR ? SH * SW : 1];   // FP32: low words (+ stage increment)
-    __shared__ T dxs[TY * DXW];            // dxs[r][c] = W(r, c+1) - W(r, c), tile rows
-    __shared__ T dys[NDIM >= 2 ? DYH * TX : 1];  // dys[r][c] = W(r+1, c) - W(r, c)
     __shared__ T red[kThreads / 32];
 
     const int ntiles = *a.ntiles;
@@ -330,11 +428,51 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && NDIM <= 2) ? 6 : 
         cE = a.aE;
     }
     const bool reads_v = a.reads_v != 0;
+    const bool has_d = INCR && a.stage_in != 0;
     const int tx = threadIdx.x % TX;
     const int ty = threadIdx.x / TX;
     int loaded = -1;
 
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    // Issue the asynchronous copies of a tile's stencil input (and l, V^n)
+    // into buffer b.  Nodes outside the grid are filled in afterwards.
+    auto issue = [&](const TileGeo& tg, int b) {
+        const int nx = C.n[AX];
+        const int ny = NDIM >= 2 ? C.n[AY] : 1;
+        const long long sy = NDIM >= 2 ? C.stride[AY] : 0;
+        const T* hp = C.win + tg.base;
+        const T* lp = INCR ? C.vlo + tg.base : nullptr;
+        const T* dp = C.din ? C.din + tg.base : nullptr;
+        for (int s = threadIdx.x; s < NR; s += kThreads) {
+            const int r = s / SW, c = s - r * SW;
+            const int gy = tg.y0 - GY + r, gx = tg.x0 - G + c;
+            if (((NDIM < 2) || (gy >= 0 && gy < ny)) && gx >= 0 && gx < nx) {
+                const long long i = (long long)gy * sy + gx;
+                cp_async<sizeof(T)>(sm + L::RH + b * NR + s, hp + i);
+                if constexpr (INCR) {
+                    cp_async<sizeof(T)>(sm + L::RL + b * NR + s, lp + i);
+                    if (dp) cp_async<sizeof(T)>(sm + L::RD + b * NR + s, dp + i);
+                }
+            }
+        }
+        if constexpr (LAST) {
+            for (int s = threadIdx.x; s < NI; s += kThreads) {
+                const int r = s / TX, c = s - r * TX;
+                const int gy = tg.y0 + r, gx = tg.x0 + c;
+                if (gy < ny && gx < nx) {
+                    const long long i = tg.base + (long long)gy * sy + gx;
+                    cp_async<sizeof(T)>(sm + L::LT + b * NI + s, C.l + i);
+                    if constexpr (!INCR) cp_async<sizeof(T)>(sm + L::VN + b * NI + s, C.vcur + i);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+
+    TileWalk walk(ntiles);
+    int t = walk.next();
+    int buf = 0;
+    bool issued = false;
+    while (t >= 0) {
         const unsigned long long entry = a.tiles[t];
         const int inst = static_cast<int>(entry >> 48);
         const long long local = static_cast<long long>(entry & 0xFFFFFFFFFFFFull);
@@ -344,75 +482,112 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && NDIM <= 2) ? 6 : 
             __syncthreads();
             loaded = inst;
         }
-        if (C.stop) continue;  // uniform across the CTA
-
-        // Tile coordinates: plane index over the slow axes, then (by, bx).
-        const long long plane = local / C.tiles_per_plane;
-        const long long rem = local - plane * C.tiles_per_plane;
-        const int by = static_cast<int>(rem / C.tiles_x);
-        const int bx = static_cast<int>(rem - (long long)by * C.tiles_x);
-        int sidx[MAXD];  // slow-axis indices
-        long long base = 0;
-        {
-            long long p = plane;
-            for (int ax = NDIM - 3; ax >= 0; --ax) {
-                sidx[ax] = static_cast<int>(p % C.n[ax]);
-                p /= C.n[ax];
-                base += (long long)sidx[ax] * C.stride[ax];
+        if (C.stop) {  // uniform across the CTA; nothing was issued for it
+            t = walk.next();
+            issued = false;
+            continue;
+        }
+        const TileGeo tg = tile_geo<T, NDIM, TY, TX>(C, local);
+        if (!issued) issue(tg, buf);
+        // Prefetch the next tile of the walk while this one is computed.
+        const int tn = walk.next();
+        bool pref = false;
+        if (tn >= 0) {
+            const unsigned long long en = a.tiles[tn];
+            if (static_cast<int>(en >> 48) == inst) {
+                issue(tile_geo<T, NDIM, TY, TX>(C, static_cast<long long>(en & 0xFFFFFFFFFFFFull)),
+                      buf ^ 1);
+                pref = true;
             }
         }
+        if (pref) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        __syncthreads();
+
         const int nx = C.n[AX];
         const int ny = NDIM >= 2 ? C.n[AY] : 1;
         const long long sy = NDIM >= 2 ? C.stride[AY] : 0;
-        const int y0 = by * TY, x0 = bx * TX;
-        // Stencil input W = h + l: FP64 h = the stage state, l = 0; FP32
-        // h = high word of V^n, l = low word + the stage increment.
-        const T* __restrict__ hp = C.win + base;
-        const T* __restrict__ lp = INCR ? C.vlo + base : nullptr;
-        const T* __restrict__ dp = C.din ? C.din + base : nullptr;
+        const int y0 = tg.y0, x0 = tg.x0;
+        const T* __restrict__ hp = C.win + tg.base;
+        const T* __restrict__ lp = INCR ? C.vlo + tg.base : nullptr;
+        const T* __restrict__ dp = C.din ? C.din + tg.base : nullptr;
+        T* rh = sm + L::RH + buf * NR;
+        T* rl = sm + L::RL + buf * NR;
+        T* rd = sm + L::RD + buf * NR;
+        auto pair_at = [&](int s) {
+            Pair<T> p;
+            p.h = rh[s];
+            p.l = T(0);
+            if constexpr (INCR) p.l = has_d ? rl[s] + rd[s] : rl[s];
+            return p;
+        };
 
-        // 1. Stage the input tile with its ghost halo.
-        for (int s = threadIdx.x; s < SH * SW; s += kThreads) {
-            const int r = s / SW, cidx = s - r * SW;
-            const int gy = y0 - GY + r, gx = x0 - G + cidx;
-            const bool iny = (NDIM < 2) || (gy >= 0 && gy < ny);
-            const bool inx = gx >= 0 && gx < nx;
-            Pair<T> v;
-            if (iny && inx) {
-                v = load_pair<T>(hp, lp, dp, (long long)gy * sy + gx);
-            } else if (iny) {
-                const long long r0 = (long long)gy * sy;
-                v = line_pair<T>(hp + r0, lp ? lp + r0 : nullptr, dp ? dp + r0 : nullptr, gx, nx,
-                                 1, C.periodic[AX]);
-            } else if (inx) {
-                v = line_pair<T>(hp + gx, lp ? lp + gx : nullptr, dp ? dp + gx : nullptr, gy, ny,
-                                 sy, C.periodic[AY]);
-            } else {
-                v.h = T(0);  // corner of the halo: never used by an axis-aligned stencil
-                v.l = T(0);
+        // 1. Ghost nodes of tiles that reach beyond the grid edge: linear
+        //    extrapolation from the two edge nodes (both inside the staged
+        //    window), or, on a periodic axis, the wrapped node.
+        const bool edge = x0 - G < 0 || x0 + TX + G > nx ||
+                          (NDIM >= 2 && (y0 - GY < 0 || y0 + TY + GY > ny));
+        if (edge) {
+            for (int s = threadIdx.x; s < NR; s += kThreads) {
+                const int r = s / SW, c = s - r * SW;
+                const int gy = y0 - GY + r, gx = x0 - G + c;
+                const bool iny = (NDIM < 2) || (gy >= 0 && gy < ny);
+                const bool inx = gx >= 0 && gx < nx;
+                if (iny && inx) continue;
+                Pair<T> v;
+                if (iny) {
+                    if (C.periodic[AX]) {
+                        const long long r0 = (long long)gy * sy;
+                        v = line_pair<T>(hp + r0, lp ? lp + r0 : nullptr, dp ? dp + r0 : nullptr,
+                                         gx, nx, 1, 1);
+                    } else {
+                        const bool low = gx < 0;
+                        const int ce = (low ? 0 : nx - 1) - (x0 - G);
+                        const int ci = (low ? 1 : nx - 2) - (x0 - G);
+                        v = extrapolate(pair_at(r * SW + ce), pair_at(r * SW + ci),
+                                        low ? -gx : gx - (nx - 1));
+                    }
+                } else if (inx) {
+                    if (C.periodic[AY]) {
+                        v = line_pair<T>(hp + gx, lp ? lp + gx : nullptr, dp ? dp + gx : nullptr,
+                                         gy, ny, sy, 1);
+                    } else {
+                        const bool low = gy < 0;
+                        const int re = (low ? 0 : ny - 1) - (y0 - GY);
+                        const int ri = (low ? 1 : ny - 2) - (y0 - GY);
+                        v = extrapolate(pair_at(re * SW + c), pair_at(ri * SW + c),
+                                        low ? -gy : gy - (ny - 1));
+                    }
+                } else {
+                    v.h = T(0);  // corner of the halo: never used by an axis-aligned stencil
+                    v.l = T(0);
+                }
+                // Written after every read of this pass: ghost nodes only
+                // read in-grid nodes, and no thread writes an in-grid node.
+                rh[s] = v.h;
+                if constexpr (INCR) {
+                    rl[s] = v.l;
+                    if (has_d) rd[s] = T(0);
+                }
             }
-            th[s] = v.h;
-            if constexpr (INCR) tl[s] = v.l;
+            __syncthreads();
         }
-        __syncthreads();
-        // Each neighbour difference once per tile (FP32: on the hi/lo pairs).
+        // 2. Each neighbour difference once per tile (FP32: on the pairs).
         for (int i = threadIdx.x; i < TY * DXW; i += kThreads) {
             const int r = i / DXW, c = i - r * DXW;
             const int s0 = (r + GY) * SW + c;
-            if constexpr (INCR) dxs[i] = (th[s0 + 1] - th[s0]) + (tl[s0 + 1] - tl[s0]);
-            else dxs[i] = th[s0 + 1] - th[s0];
+            dxs[i] = pair_diff(pair_at(s0 + 1), pair_at(s0));
         }
         if constexpr (NDIM >= 2) {
             for (int i = threadIdx.x; i < DYH * TX; i += kThreads) {
                 const int r = i / TX, c = i - r * TX;
                 const int s0 = r * SW + c + G;
-                if constexpr (INCR) dys[i] = (th[s0 + SW] - th[s0]) + (tl[s0 + SW] - tl[s0]);
-                else dys[i] = th[s0 + SW] - th[s0];
+                dys[i] = pair_diff(pair_at(s0 + SW), pair_at(s0));
             }
         }
         __syncthreads();
 
-        // 2-5. Each thread updates CELLS nodes of the tile.
+        // 3-5. Each thread updates CELLS nodes of the tile.
         T dmax = T(0);
 #pragma unroll
         for (int k = 0; k < CELLS; ++k) {
@@ -421,9 +596,8 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && NDIM <= 2) ? 6 : 
             if (ry >= TY || gy >= ny || gx >= nx) continue;
             T pm[NDIM], pp[NDIM];
             T D[2 * G];
-            const int c0 = (ry + GY) * SW + (tx + G);  // this node in the shared tile
-            const T wc = th[c0];
-            // Fastest and second axes: the precomputed differences.
+            const int c0 = (ry + GY) * SW + (tx + G);  // this node in the staged tile
+            const int ci = ry * TX + tx;               // this node among the tile nodes
 #pragma unroll
             for (int o = 0; o < 2 * G; ++o) D[o] = dxs[ry * DXW + tx + o];
             one_sided_diffs<T, SCHEME>(D, C.inv_dx[AX], pm[AX], pp[AX]);
@@ -435,14 +609,23 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && NDIM <= 2) ? 6 : 
             const long long off = (long long)gy * sy + gx;  // within the plane
 #pragma unroll
             for (int ax = 0; ax < NDIM - 2; ++ax) {
-                // Slower axes: the stencil line straight from global memory (L2).
-                const long long l0 = off - (long long)sidx[ax] * C.stride[ax];
+                // Slower axes: the stencil line straight from global memory
+                // (L1/L2).  The slow index is the same for the whole tile, so
+                // a tile away from that axis' edges takes the strided path.
+                const long long st = C.stride[ax];
                 Pair<T> line[2 * G + 1];
+                if (tg.sidx[ax] >= G && tg.sidx[ax] < C.n[ax] - G) {
 #pragma unroll
-                for (int o = -G; o <= G; ++o)
-                    line[o + G] = line_pair<T>(hp + l0, lp ? lp + l0 : nullptr,
-                                               dp ? dp + l0 : nullptr, sidx[ax] + o, C.n[ax],
-                                               C.stride[ax], C.periodic[ax]);
+                    for (int o = -G; o <= G; ++o)
+                        line[o + G] = load_pair<T>(hp, lp, dp, off + o * st);
+                } else {
+                    const long long l0 = off - (long long)tg.sidx[ax] * st;
+#pragma unroll
+                    for (int o = -G; o <= G; ++o)
+                        line[o + G] = line_pair<T>(hp + l0, lp ? lp + l0 : nullptr,
+                                                   dp ? dp + l0 : nullptr, tg.sidx[ax] + o,
+                                                   C.n[ax], st, C.periodic[ax]);
+                }
 #pragma unroll
                 for (int o = 0; o < 2 * G; ++o) D[o] = pair_diff(line[o + 1], line[o]);
                 one_sided_diffs<T, SCHEME>(D, C.inv_dx[ax], pm[ax], pp[ax]);
@@ -450,7 +633,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && NDIM <= 2) ? 6 : 
             // Node coordinates and the drift f0(x) = c + A x + terms.
             int idx[NDIM];
 #pragma unroll
-            for (int ax = 0; ax < NDIM - 2; ++ax) idx[ax] = sidx[ax];
+            for (int ax = 0; ax < NDIM - 2; ++ax) idx[ax] = tg.sidx[ax];
             if constexpr (NDIM >= 2) idx[AY] = gy;
             idx[AX] = gx;
             T x[NDIM], pbar[NDIM];
@@ -485,26 +668,26 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && NDIM <= 2) ? 6 : 
                 h += fmin(r * C.dlo[j], r * C.dhi[j]);
             }
             // Lax-Friedrichs: L = H(pbar) + sum alpha_a (p+ - p-) / 2.
-            T L = h;
+            T Lv = h;
 #pragma unroll
-            for (int ax = 0; ax < NDIM; ++ax) L += C.half_alpha[ax] * (pp[ax] - pm[ax]);
+            for (int ax = 0; ax < NDIM; ++ax) Lv += C.half_alpha[ax] * (pp[ax] - pm[ax]);
             // Runge-Kutta stage combination.
-            const long long gidx = base + off;
+            const long long gidx = tg.base + off;
             if constexpr (INCR) {
-                const T dc = dp ? __ldg(dp + off) : T(0);
-                const T inc = cE * (dc + C.dt * L);
+                const T dc = has_d ? rd[c0] : T(0);
+                const T inc = cE * (dc + C.dt * Lv);
                 if constexpr (!LAST) {
                     C.wout[gidx] = inc;
                 } else {
                     // V^n + inc as an unevaluated float pair (error-free
                     // two-sum), then min(., l) of Eq. (7)-(8).
-                    const T hi = __ldg(C.vcur + gidx);
-                    const T lo = C.vlo[gidx];
+                    const T hi = rh[c0];
+                    const T lo = rl[c0];
                     const T sl = lo + inc;
                     T nh = hi + sl;
                     const T bb = nh - hi;
                     T nl = (hi - (nh - bb)) + (sl - bb);
-                    const T lv = __ldg(C.l + gidx);
+                    const T lv = sm[L::LT + buf * NI + ci];
                     if (nh > lv || (nh == lv && nl > T(0))) {
                         nh = lv;
                         nl = T(0);
@@ -515,17 +698,19 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && NDIM <= 2) ? 6 : 
                     C.vlo[gidx] = nl;
                 }
             } else {
-                const T eul = wc + C.dt * L;
+                const T wc = rh[c0];
+                const T eul = wc + C.dt * Lv;
                 T out;
                 T vn = wc;
                 if (reads_v) {
-                    vn = __ldg(C.vcur + gidx);
+                    if constexpr (LAST) vn = sm[L::VN + buf * NI + ci];
+                    else vn = __ldg(C.vcur + gidx);
                     out = cV * vn + cE * eul;
                 } else {
                     out = eul;
                 }
                 if constexpr (LAST) {
-                    const T lv = __ldg(C.l + gidx);
+                    const T lv = sm[L::LT + buf * NI + ci];
                     out = fmin(out, lv);
                     const T ch = fabs(out - vn);
                     dmax = (ch > dmax || ch != ch) ? ch : dmax;
@@ -555,21 +740,37 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && NDIM <= 2) ? 6 : 
                 if (prev + 1 == static_cast<unsigned int>(C.ntiles)) finish_step(D);
             }
         }
-        __syncthreads();  // tile buffer reuse
+        __syncthreads();  // buffer `buf` is refilled by the prefetch after next
+        buf ^= 1;
+        t = tn;
+        issued = pref;
     }
+    cp_async_wait<0>();
 }
 
-template <typename T, int NDIM, int SCHEME, bool LAST>
+template <typename T, int NDIM, int SCHEME, bool LAST, int V>
 cudaError_t launch_stage(const StageArgs& a, int grid, cudaStream_t s) {
-    stage_kernel<T, NDIM, SCHEME, LAST><<<grid, kThreads, 0, s>>>(a);
+    using L = StageSmem<T, NDIM, SCHEME, LAST, V>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, NDIM, SCHEME, LAST, V>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(L::BYTES));
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    stage_kernel<T, NDIM, SCHEME, LAST, V><<<grid, kThreads, L::BYTES, s>>>(a);
     return cudaGetLastError();
 }
 
-template <typename T, int NDIM, int SCHEME, bool LAST>
+template <typename T, int NDIM, int SCHEME, bool LAST, int V>
 int max_blocks_stage() {
+    using L = StageSmem<T, NDIM, SCHEME, LAST, V>;
+    cudaFuncSetAttribute(stage_kernel<T, NDIM, SCHEME, LAST, V>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L::BYTES));
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stage_kernel<T, NDIM, SCHEME, LAST>,
-                                                      kThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stage_kernel<T, NDIM, SCHEME, LAST, V>,
+                                                      kThreads, L::BYTES) != cudaSuccess)
         return 1;
     return b > 0 ? b : 1;
 }

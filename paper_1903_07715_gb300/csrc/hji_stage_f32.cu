@@ -4,23 +4,29 @@
 
 namespace hji {
 
-#define HJI_STAGE_ENTRY(ND, SC) \
-    if (ndim == ND && scheme == SC) return last ? launch_stage<float, ND, SC, true> : launch_stage<float, ND, SC, false>;
-#define HJI_STAGE_OCC(ND, SC) \
-    if (ndim == ND && scheme == SC) return last ? max_blocks_stage<float, ND, SC, true>() : max_blocks_stage<float, ND, SC, false>();
+#define HJI_ENTRY(ND, SC, V) \
+    if (ndim == ND && scheme == SC && v == V) \
+        return last ? launch_stage<float, ND, SC, true, V> : launch_stage<float, ND, SC, false, V>;
+#define HJI_OCC(ND, SC, V) \
+    if (ndim == ND && scheme == SC && v == V) \
+        return last ? max_blocks_stage<float, ND, SC, true, V>() : max_blocks_stage<float, ND, SC, false, V>();
 #define HJI_ALL(X) \
-    X(1, HJI_ENO1) X(1, HJI_ENO2) X(1, HJI_WENO5) \
-    X(2, HJI_ENO1) X(2, HJI_ENO2) X(2, HJI_WENO5) \
-    X(3, HJI_ENO1) X(3, HJI_ENO2) X(3, HJI_WENO5) \
-    X(4, HJI_ENO1) X(4, HJI_ENO2) X(4, HJI_WENO5)
+    X(1, HJI_ENO1, 0) X(1, HJI_ENO2, 0) X(1, HJI_WENO5, 0) \
+    X(2, HJI_ENO1, 0) X(2, HJI_ENO2, 0) X(2, HJI_WENO5, 0) \
+    X(2, HJI_ENO1, 1) X(2, HJI_ENO2, 1) X(2, HJI_WENO5, 1) \
+    X(2, HJI_ENO1, 2) X(2, HJI_ENO2, 2) X(2, HJI_WENO5, 2) \
+    X(3, HJI_ENO1, 0) X(3, HJI_ENO2, 0) X(3, HJI_WENO5, 0) \
+    X(4, HJI_ENO1, 0) X(4, HJI_ENO2, 0) X(4, HJI_WENO5, 0)
 
-StageLauncher stage_launcher_f32(int ndim, int scheme, bool last) {
-    HJI_ALL(HJI_STAGE_ENTRY)
+StageLauncher stage_launcher_f32(int ndim, int scheme, bool last, int variant) {
+    const int v = ndim == 2 ? variant : 0;
+    HJI_ALL(HJI_ENTRY)
     return nullptr;
 }
 
-int stage_max_blocks_f32(int ndim, int scheme, bool last) {
-    HJI_ALL(HJI_STAGE_OCC)
+int stage_max_blocks_f32(int ndim, int scheme, bool last, int variant) {
+    const int v = ndim == 2 ? variant : 0;
+    HJI_ALL(HJI_OCC)
     return 1;
 }
 

@@ -75,3 +75,30 @@ def test_batch_rejects_mixed_precision(hji_lib):
     assert e.value.status == hji_lib.HJI_E_INVALID
     g1.close()
     g2.close()
+
+
+@pytest.mark.parametrize("prec,scheme,rk", [("f32", "weno5", 3), ("f64", "eno2", 2)])
+def test_tile_shapes_give_identical_results_and_autotune(hji_lib, prec, scheme, rk):
+    """Every tile shape computes the same per-node arithmetic, so forcing each
+    shape gives bit-identical marches; the autotuner times them and its
+    choice is then used by default."""
+    import torch
+    assert torch.cuda.is_available()
+    gd, dyn, l = W.di_config(203, dmax=0.1)
+    l = l.astype(np.float32 if prec == "f32" else np.float64)
+    opts = dict(scheme=scheme, rk=rk, cfl=0.5, tol=1e-6, max_steps=3000)
+    g = hji_lib.Grid(gd, prec)
+    g.set_dynamics(dyn)
+    vals, steps = [], []
+    for v in range(1, hji_lib.HJI_TILE_VARIANTS + 1):
+        st = g.solve(l, tile_variant=v, **opts)
+        vals.append(g.value())
+        steps.append(st["steps"])
+    assert len(set(steps)) == 1
+    for V in vals[1:]:
+        assert np.array_equal(V, vals[0])
+    chosen, ms = g.autotune(l, steps=10, **opts)
+    assert 0 <= chosen < hji_lib.HJI_TILE_VARIANTS and all(m > 0 for m in ms)
+    st = g.solve(l, **opts)
+    assert st["steps"] == steps[0] and np.array_equal(g.value(), vals[0])
+    g.close()
