@@ -43,7 +43,8 @@ struct hji_grid_s {
     void* table = nullptr;
     size_t table_bytes = 0;
     InstState* state = nullptr;      // device
-    InstDesc* d_desc = nullptr;      // device descriptor for single-grid solves
+    InstDesc* d_desc = nullptr;      // descriptors of the solves this grid leads
+    int desc_cap = 0;
     int* d_active = nullptr;         // device counter for single-grid solves
     unsigned long long* d_tiles = nullptr;
     size_t tiles_cap = 0;
@@ -407,13 +408,10 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
     int variant = pick_variant(g0->prec, ndim, o, cells_all / count);
     if (o->tile_variant > 0 && g_force_variant < 0)
         variant = (ndim == 2 && o->tile_variant <= hji::kTileVariants) ? o->tile_variant - 1 : 0;
-    // Batch-wide device scratch: descriptors, tile list, active counter.
+    // Launch-wide device scratch (descriptors, tile list, counters) lives on
+    // the first grid and is reused (grown on demand) by every solve it leads,
+    // together with the captured graph of a chunk.
     std::vector<InstDesc> H(count);
-    InstDesc* d_desc = g0->d_desc;
-    int* d_active = g0->d_active;
-    unsigned long long* d_tiles = nullptr;
-    int* d_ntiles = g0->d_ntiles;
-    bool own_batch = count > 1;
     long long total_tiles = 0;
     for (int i = 0; i < count; ++i) {
         long long tx, ty, planes;
@@ -421,40 +419,31 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
         total_tiles += tx * ty * planes;
     }
     if (total_tiles >= (1ll << 31)) return fail(g0, HJI_E_INVALID, "too many tiles");
-    if (own_batch) {
-        d_desc = (InstDesc*)dev_alloc(g0, sizeof(InstDesc) * count, s);
-        d_active = (int*)dev_alloc(g0, sizeof(int) * 2, s);
-        d_tiles = (unsigned long long*)dev_alloc(g0, sizeof(unsigned long long) * total_tiles, s);
-        if (!d_desc || !d_active || !d_tiles) {
-            dev_free(g0, d_desc, s);
-            dev_free(g0, d_active, s);
-            dev_free(g0, d_tiles, s);
-            return fail(g0, HJI_E_NOMEM, "batch scratch allocation failed");
-        }
-        d_ntiles = d_active + 1;
-    } else {
-        if (g0->tiles_cap < (size_t)total_tiles) {
-            dev_free(g0, g0->d_tiles, s);
-            g0->d_tiles = (unsigned long long*)dev_alloc(g0, sizeof(unsigned long long) * total_tiles, s);
-            if (!g0->d_tiles) {
-                g0->tiles_cap = 0;
-                return fail(g0, HJI_E_NOMEM, "tile list allocation failed");
-            }
-            g0->tiles_cap = (size_t)total_tiles;
-            if (g0->graph) {
-                cudaGraphExecDestroy(g0->graph);
-                g0->graph = nullptr;
-            }
-        }
-        d_tiles = g0->d_tiles;
-    }
-    auto cleanup = [&]() {
-        if (own_batch) {
-            dev_free(g0, d_desc, s);
-            dev_free(g0, d_active, s);
-            dev_free(g0, d_tiles, s);
+    auto drop_graph = [&]() {
+        if (g0->graph) {
+            cudaGraphExecDestroy(g0->graph);
+            g0->graph = nullptr;
         }
     };
+    if (g0->desc_cap < count) {
+        dev_free(g0, g0->d_desc, s);
+        g0->d_desc = (InstDesc*)dev_alloc(g0, sizeof(InstDesc) * count, s);
+        g0->desc_cap = g0->d_desc ? count : 0;
+        drop_graph();
+        if (!g0->d_desc) return fail(g0, HJI_E_NOMEM, "descriptor allocation failed");
+    }
+    if (g0->tiles_cap < (size_t)total_tiles) {
+        dev_free(g0, g0->d_tiles, s);
+        g0->d_tiles = (unsigned long long*)dev_alloc(g0, sizeof(unsigned long long) * total_tiles, s);
+        g0->tiles_cap = g0->d_tiles ? (size_t)total_tiles : 0;
+        drop_graph();
+        if (!g0->d_tiles) return fail(g0, HJI_E_NOMEM, "tile list allocation failed");
+    }
+    InstDesc* d_desc = g0->d_desc;
+    int* d_active = g0->d_active;
+    int* d_ntiles = g0->d_ntiles;
+    unsigned long long* d_tiles = g0->d_tiles;
+    auto cleanup = [&]() {};
 
     std::vector<const void*> kptr(count, nullptr);
     std::vector<int> keep_lo(count, 0);
@@ -532,25 +521,19 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
     const int grid = stage_grid(f32, ndim, o->scheme, total_tiles, variant);
     hji::StageArgs base{d_desc, d_tiles, d_ntiles, 0, 0, 0.0, 0.0, 0.0f, 0.0f, 0};
     cudaGraphExec_t exec = nullptr;
-    const long long key[7] = {(long long)o->scheme, o->rk_order, chunk, grid, (long long)(uintptr_t)d_tiles,
-                              (long long)total_tiles, variant};
-    if (!own_batch && g0->graph && std::memcmp(key, g0->graph_key, sizeof(key)) == 0) {
+    // The graph's kernels read descriptors, tile list and its length from the
+    // leader's scratch, so it stays valid while those buffers and the launch
+    // shape (scheme, RK order, chunk, grid, tile shape) are unchanged.
+    const long long key[7] = {(long long)o->scheme, o->rk_order, chunk, grid, variant, ndim, f32 ? 1 : 0};
+    if (g0->graph && std::memcmp(key, g0->graph_key, sizeof(key)) == 0) {
         exec = g0->graph;
     } else {
-        if (!own_batch && g0->graph) {
-            cudaGraphExecDestroy(g0->graph);
-            g0->graph = nullptr;
-        }
+        drop_graph();
         st = capture_chunk(g0, g0->cap_stream, f32, ndim, o->scheme, o->rk_order, chunk, base, grid,
                            variant, &exec);
-        if (st != HJI_OK) {
-            cleanup();
-            return st;
-        }
-        if (!own_batch) {
-            g0->graph = exec;
-            std::memcpy(g0->graph_key, key, sizeof(key));
-        }
+        if (st != HJI_OK) return st;
+        g0->graph = exec;
+        std::memcpy(g0->graph_key, key, sizeof(key));
     }
     int* h_active = g0->h_active;  // two pinned slots
     cudaEvent_t ev[2];
@@ -573,7 +556,6 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
-    if (own_batch) cudaGraphExecDestroy(exec);
     if (e != cudaSuccess) {
         cleanup();
         return cuda_fail(g0, e, "march");
@@ -680,6 +662,7 @@ hji_status hji_grid_create(int ndim, const int64_t* n, const double* lo, const d
     if (prec == HJI_F32) g->Vlo = dev_alloc(g, bytes, s);
     g->state = (InstState*)dev_alloc(g, sizeof(InstState), s);
     g->d_desc = (InstDesc*)dev_alloc(g, sizeof(InstDesc), s);
+    g->desc_cap = g->d_desc ? 1 : 0;
     g->d_active = (int*)dev_alloc(g, sizeof(int) * 2, s);
     bool ok = g->V[0] && g->V[1] && g->l && g->state && g->d_desc && g->d_active &&
               (prec != HJI_F32 || g->Vlo);

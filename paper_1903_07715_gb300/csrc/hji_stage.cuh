@@ -433,35 +433,64 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 5 : 3)
     const int ty = threadIdx.x / TX;
     int loaded = -1;
 
+    // Staged-window walk of this thread: element s = threadIdx.x + k kThreads
+    // sits at row r, column c; stepping by kThreads adds SR rows and SC
+    // columns (no divisions in the loops).
+    constexpr int SR = kThreads / SW, SC = kThreads % SW;
+    const int r_first = threadIdx.x / SW, c_first = threadIdx.x % SW;
+
     // Issue the asynchronous copies of a tile's stencil input (and l, V^n)
     // into buffer b.  Nodes outside the grid are filled in afterwards.
     auto issue = [&](const TileGeo& tg, int b) {
         const int nx = C.n[AX];
         const int ny = NDIM >= 2 ? C.n[AY] : 1;
-        const long long sy = NDIM >= 2 ? C.stride[AY] : 0;
+        const int sy = NDIM >= 2 ? static_cast<int>(C.stride[AY]) : 0;
         const T* hp = C.win + tg.base;
         const T* lp = INCR ? C.vlo + tg.base : nullptr;
         const T* dp = C.din ? C.din + tg.base : nullptr;
+        const bool inside = tg.x0 - G >= 0 && tg.x0 + TX + G <= nx &&
+                            (NDIM < 2 || (tg.y0 - GY >= 0 && tg.y0 + TY + GY <= ny));
+        T* dh = sm + L::RH + b * NR;
+        T* dl = sm + L::RL + b * NR;
+        T* dd = sm + L::RD + b * NR;
+        int r = r_first, c = c_first;
+        int goff = (tg.y0 - GY + r) * sy + (tg.x0 - G + c);
         for (int s = threadIdx.x; s < NR; s += kThreads) {
-            const int r = s / SW, c = s - r * SW;
-            const int gy = tg.y0 - GY + r, gx = tg.x0 - G + c;
-            if (((NDIM < 2) || (gy >= 0 && gy < ny)) && gx >= 0 && gx < nx) {
-                const long long i = (long long)gy * sy + gx;
-                cp_async<sizeof(T)>(sm + L::RH + b * NR + s, hp + i);
+            bool ok = inside;
+            if (!inside) {
+                const int gy = tg.y0 - GY + r, gx = tg.x0 - G + c;
+                ok = ((NDIM < 2) || (gy >= 0 && gy < ny)) && gx >= 0 && gx < nx;
+            }
+            if (ok) {
+                cp_async<sizeof(T)>(dh + s, hp + goff);
                 if constexpr (INCR) {
-                    cp_async<sizeof(T)>(sm + L::RL + b * NR + s, lp + i);
-                    if (dp) cp_async<sizeof(T)>(sm + L::RD + b * NR + s, dp + i);
+                    cp_async<sizeof(T)>(dl + s, lp + goff);
+                    if (dp) cp_async<sizeof(T)>(dd + s, dp + goff);
                 }
+            }
+            c += SC;
+            r += SR;
+            goff += SR * sy + SC;
+            if (c >= SW) {
+                c -= SW;
+                ++r;
+                goff += sy - SW;
             }
         }
         if constexpr (LAST) {
-            for (int s = threadIdx.x; s < NI; s += kThreads) {
-                const int r = s / TX, c = s - r * TX;
-                const int gy = tg.y0 + r, gx = tg.x0 + c;
-                if (gy < ny && gx < nx) {
-                    const long long i = tg.base + (long long)gy * sy + gx;
-                    cp_async<sizeof(T)>(sm + L::LT + b * NI + s, C.l + i);
-                    if constexpr (!INCR) cp_async<sizeof(T)>(sm + L::VN + b * NI + s, C.vcur + i);
+            // Tile nodes: thread (ty, tx) takes rows ty, ty + ROWS_PER_PASS, ...
+            const T* lg = C.l + tg.base;
+            const T* vg = C.vcur + tg.base;
+            const int gx = tg.x0 + tx;
+#pragma unroll
+            for (int k = 0; k < CELLS; ++k) {
+                const int ry = ty + k * ROWS_PER_PASS;
+                const int gy = tg.y0 + ry;
+                if (ry < TY && gy < ny && gx < nx) {
+                    const int si = ry * TX + tx;
+                    const int gi = gy * sy + gx;
+                    cp_async<sizeof(T)>(sm + L::LT + b * NI + si, lg + gi);
+                    if constexpr (!INCR) cp_async<sizeof(T)>(sm + L::VN + b * NI + si, vg + gi);
                 }
             }
         }
@@ -514,11 +543,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 5 : 3)
         T* rh = sm + L::RH + buf * NR;
         T* rl = sm + L::RL + buf * NR;
         T* rd = sm + L::RD + buf * NR;
+        // FP32 stages 2+: fold the increment into the low word once per node.
+        if constexpr (INCR) {
+            if (has_d) {
+                for (int s = threadIdx.x; s < NR; s += kThreads) rl[s] += rd[s];
+                __syncthreads();
+            }
+        }
         auto pair_at = [&](int s) {
             Pair<T> p;
             p.h = rh[s];
             p.l = T(0);
-            if constexpr (INCR) p.l = has_d ? rl[s] + rd[s] : rl[s];
+            if constexpr (INCR) p.l = rl[s];
             return p;
         };
 
@@ -565,18 +601,24 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 5 : 3)
                 // Written after every read of this pass: ghost nodes only
                 // read in-grid nodes, and no thread writes an in-grid node.
                 rh[s] = v.h;
-                if constexpr (INCR) {
-                    rl[s] = v.l;
-                    if (has_d) rd[s] = T(0);
-                }
+                if constexpr (INCR) rl[s] = v.l;
             }
             __syncthreads();
         }
         // 2. Each neighbour difference once per tile (FP32: on the pairs).
-        for (int i = threadIdx.x; i < TY * DXW; i += kThreads) {
-            const int r = i / DXW, c = i - r * DXW;
-            const int s0 = (r + GY) * SW + c;
-            dxs[i] = pair_diff(pair_at(s0 + 1), pair_at(s0));
+        {
+            constexpr int XR = kThreads / DXW, XC = kThreads % DXW;
+            int r = threadIdx.x / DXW, c = threadIdx.x % DXW;
+            for (int i = threadIdx.x; i < TY * DXW; i += kThreads) {
+                const int s0 = (r + GY) * SW + c;
+                dxs[i] = pair_diff(pair_at(s0 + 1), pair_at(s0));
+                c += XC;
+                r += XR;
+                if (c >= DXW) {
+                    c -= DXW;
+                    ++r;
+                }
+            }
         }
         if constexpr (NDIM >= 2) {
             for (int i = threadIdx.x; i < DYH * TX; i += kThreads) {
@@ -682,7 +724,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 5 : 3)
                     // V^n + inc as an unevaluated float pair (error-free
                     // two-sum), then min(., l) of Eq. (7)-(8).
                     const T hi = rh[c0];
-                    const T lo = rl[c0];
+                    const T lo = has_d ? C.vlo[gidx] : rl[c0];
                     const T sl = lo + inc;
                     T nh = hi + sl;
                     const T bb = nh - hi;
