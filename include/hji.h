@@ -144,6 +144,9 @@ typedef struct {
     hji_init init;
     int tile_variant; /* 0: the autotuned (else default) tile shape;
                          1..HJI_TILE_VARIANTS: force shape tile_variant-1 (2-D) */
+    double tol_rate;  /* >= 0: the test becomes max|dV| < tol + tol_rate * dt, a
+                         bound on the rate of change; tol = 0, tol_rate = 0.1 is
+                         Sec. IV's rule (change < 0.001 per 0.01 of time) */
 } hji_solve_opts;
 
 typedef struct {

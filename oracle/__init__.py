@@ -96,7 +96,8 @@ def _load():
         lib.oracle_init.argtypes = [_P, _D, _D, _D]
         lib.oracle_solve.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int64, _D, _D,
-                                     _D, ctypes.POINTER(_Stats), _D, ctypes.c_int64]
+                                     _D, ctypes.POINTER(_Stats), _D, ctypes.c_int64,
+                                     ctypes.c_double]
         lib.oracle_max_threads.restype = ctypes.c_int
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_ghost_width.argtypes = [ctypes.c_int]
@@ -263,8 +264,9 @@ def step(P, scheme, rk, dt, alpha, l, V):
 
 
 def solve(P, l, k=None, scheme="eno2", rk=2, cfl=0.5, tol=1e-6, horizon=0.0, max_steps=0,
-          history=0):
-    """March to convergence.  Returns (V, stats dict[, history array])."""
+          history=0, tol_rate=0.0):
+    """March to convergence (max|dV| < tol + tol_rate dt).  Returns
+    (V, stats dict[, history array])."""
     l = _f64(l)
     V = np.empty_like(l)
     kk = None if k is None else _f64(k)
@@ -273,7 +275,7 @@ def solve(P, l, k=None, scheme="eno2", rk=2, cfl=0.5, tol=1e-6, horizon=0.0, max
     rc = _load().oracle_solve(ctypes.byref(P), SCHEMES[scheme], int(rk), float(cfl), float(tol),
                               float(horizon), int(max_steps), _ptr(l),
                               None if kk is None else _ptr(kk), _ptr(V), ctypes.byref(st),
-                              _ptr(hist), int(history))
+                              _ptr(hist), int(history), float(tol_rate))
     if rc < 0:
         raise ValueError("oracle_solve rejected its input")
     stats = {"steps": st.steps, "tau": st.tau, "dt": st.dt, "last_delta": st.last_delta,

@@ -420,13 +420,17 @@ void oracle_init(const oracle_problem* P, const double* l, const double* k, doub
     for (int64_t c = 0; c < total; ++c) V[c] = (k && k[c] < l[c]) ? k[c] : l[c];
 }
 
-/* The whole march: initialise, then step until max|dV| < tol (converged),
- * or tau >= horizon (horizon > 0), or max_steps steps (max_steps > 0).
+/* The whole march: initialise, then step until max|dV| < tol + tol_rate dt
+ * (converged), or tau >= horizon (horizon > 0), or max_steps steps
+ * (max_steps > 0).  tol is a bound on the change per step; tol_rate bounds
+ * the change per unit of time, which is how Sec. IV states its rule (a
+ * change below 0.001 over a time step of 0.01: tol_rate = 0.1).
  * If `history` is not NULL it receives max|dV| of the first hist_len steps.
  * Returns 0 converged, 1 stopped without converging, -1 bad input. */
 int oracle_solve(const oracle_problem* P, int scheme, int rk, double cfl, double tol,
                  double horizon, int64_t max_steps, const double* l, const double* k,
-                 double* V, oracle_stats* st, double* history, int64_t hist_len) {
+                 double* V, oracle_stats* st, double* history, int64_t hist_len,
+                 double tol_rate) {
     double alpha[OR_MAXD], dt;
     if (oracle_alpha_dt(P, cfl, alpha, &dt) != 0) return -1;
     int64_t total = oracle_num_cells(P);
@@ -445,7 +449,7 @@ int oracle_solve(const oracle_problem* P, int scheme, int rk, double cfl, double
         if (history && steps < hist_len) history[steps] = delta;
         steps += 1;
         tau += dt;
-        if (delta < tol) {
+        if (delta < tol + tol_rate * dt) {
             converged = 1;
             break;
         }

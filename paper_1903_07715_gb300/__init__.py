@@ -60,7 +60,8 @@ class hji_solve_opts(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int), ("rk_order", ctypes.c_int), ("cfl", ctypes.c_double),
                 ("tol", ctypes.c_double), ("horizon", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("max_steps", ctypes.c_int64),
-                ("init", ctypes.c_int), ("tile_variant", ctypes.c_int)]
+                ("init", ctypes.c_int), ("tile_variant", ctypes.c_int),
+                ("tol_rate", ctypes.c_double)]
 
 
 class hji_solve_stats(ctypes.Structure):
@@ -293,9 +294,9 @@ def _stats_dict(st):
 
 
 def solve_opts(scheme="eno2", rk=2, cfl=0.5, tol=1e-6, horizon=0.0, max_steps=0,
-               check_every=32, init=HJI_INIT_STANDARD, tile_variant=0):
+               check_every=32, init=HJI_INIT_STANDARD, tile_variant=0, tol_rate=0.0):
     return hji_solve_opts(SCHEMES[scheme] if isinstance(scheme, str) else scheme, rk, cfl, tol,
-                          horizon, check_every, max_steps, init, tile_variant)
+                          horizon, check_every, max_steps, init, tile_variant, tol_rate)
 
 
 class Grid:

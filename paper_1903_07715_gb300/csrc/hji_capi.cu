@@ -261,6 +261,8 @@ hji_status validate_opts(hji_grid g, const hji_solve_opts* o) {
         return fail(g, HJI_E_INVALID, "horizon must be finite and >= 0");
     if (o->init != HJI_INIT_STANDARD && o->init != HJI_INIT_USER_K && o->init != HJI_INIT_RESIDENT)
         return fail(g, HJI_E_INVALID, "unknown init mode");
+    if (!(o->tol_rate >= 0.0) || !std::isfinite(o->tol_rate))
+        return fail(g, HJI_E_INVALID, "tol_rate must be finite and >= 0");
     if (o->tile_variant < 0 || o->tile_variant > hji::kTileVariants)
         return fail(g, HJI_E_INVALID, "tile_variant must be 0..HJI_TILE_VARIANTS");
     return HJI_OK;
@@ -307,6 +309,7 @@ InstDesc make_desc(hji_grid g, const hji_solve_opts* o, int* active, int variant
     D.dyn = g->dyn;
     D.cfl = o->cfl;
     D.tol = o->tol;
+    D.tol_rate = o->tol_rate;
     D.horizon = o->horizon;
     D.max_steps = o->max_steps > 0 ? o->max_steps : 1000000;
     D.V[0] = g->V[0];
@@ -473,6 +476,8 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
             keep_lo[i] = 1;
         }
         H[i] = make_desc(g, o, d_active, variant);
+        H[i].kinit = kptr[i];
+        H[i].keep_lo = keep_lo[i];
         for (long long t = 0; t < H[i].ntiles; ++t) tiles.push_back(hji::make_tile(i, t));
         e = cudaMemsetAsync(g->state, 0, sizeof(InstState), s);
         if (e != cudaSuccess) {
@@ -488,7 +493,7 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_active, &counts[0], sizeof(int), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_ntiles, &counts[1], sizeof(int), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = hji::launch_setup(d_desc, H.data(), count, f32, s);
-    if (e == cudaSuccess) e = hji::launch_init(d_desc, H.data(), count, f32, kptr.data(), keep_lo.data(), s);
+    if (e == cudaSuccess) e = hji::launch_init(d_desc, H.data(), count, f32, s);
     if (e != cudaSuccess) {
         cleanup();
         return cuda_fail(g0, e, "set-up");
@@ -1001,13 +1006,12 @@ hji_status hji_engine_step(hji_engine e, int* active, int* queued) {
         hji_grid g = e->slots[slot].g;
         const hji_init init = e->slots[slot].init;
         InstDesc& D = e->h_desc[slot];
-        const void* k = init == HJI_INIT_USER_K ? g->V[1] : (init == HJI_INIT_RESIDENT ? g->V[g->cur] : nullptr);
-        const int keep = init == HJI_INIT_RESIDENT ? 1 : 0;
-        const void* karr[1] = {k};
+        D.kinit = init == HJI_INIT_USER_K ? g->V[1] : (init == HJI_INIT_RESIDENT ? g->V[g->cur] : nullptr);
+        D.keep_lo = init == HJI_INIT_RESIDENT ? 1 : 0;
         ce = cudaMemsetAsync(g->state, 0, sizeof(InstState), e->s);
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(e->d_desc + slot, &D, sizeof(InstDesc), cudaMemcpyHostToDevice, e->s);
         if (ce == cudaSuccess) ce = hji::launch_setup(e->d_desc + slot, &D, 1, f32, e->s);
-        if (ce == cudaSuccess) ce = hji::launch_init(e->d_desc + slot, &D, 1, f32, karr, &keep, e->s);
+        if (ce == cudaSuccess) ce = hji::launch_init(e->d_desc + slot, &D, 1, f32, e->s);
         if (ce != cudaSuccess) return efail(e, HJI_E_CUDA, std::string("admission: ") + cudaGetErrorString(ce));
     }
     e->launched_active = marching;

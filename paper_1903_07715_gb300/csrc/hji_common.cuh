@@ -61,7 +61,7 @@ struct InstDesc {
     long long ncells;
     double lo[MAXD], dx[MAXD];
     Dyn dyn;
-    double cfl, tol, horizon;
+    double cfl, tol, horizon, tol_rate;
     long long max_steps;
     void* V[2];               // ping-pong value buffers: V[cur] = V^n
     void* W1;                 // stage buffers of the Runge-Kutta step: stage
@@ -75,6 +75,8 @@ struct InstDesc {
     long long tiles_x, tiles_y, tiles_per_plane, ntiles;  // tile grid of this instance
     InstState* state;
     int* active;              // batch-wide count of instances still marching (may be null)
+    const void* kinit;        // warm start read by the init pass (null: V0 = l)
+    int keep_lo;              // kinit is the grid's own resident value: keep its FP32 low word
 };
 
 // Tile list entry: instance index in the high 16 bits, tile index within the
@@ -142,9 +144,10 @@ int stage_max_blocks_f32(int ndim, int scheme, bool last, int variant = 0);
 // Set-up kernels (hji_setup.cu).
 cudaError_t launch_setup(const InstDesc* d_insts, const InstDesc* h_insts, int count, bool f32,
                          cudaStream_t s);
-// keep_lo[i] != 0: k[i] is grid i's own resident value; keep its FP32 low word.
+// One launch per pass covers all `count` instances (blockIdx.y picks one);
+// the init pass reads each instance's warm start from its kinit / keep_lo.
 cudaError_t launch_init(const InstDesc* d_insts, const InstDesc* h_insts, int count, bool f32,
-                        const void* const* k, const int* keep_lo, cudaStream_t s);
+                        cudaStream_t s);
 cudaError_t launch_convert(long long n, const void* src_hi, const void* src_lo, bool src_f32,
                            void* dst_hi, void* dst_lo, bool dst_f32, cudaStream_t s);
 

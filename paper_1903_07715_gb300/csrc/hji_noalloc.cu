@@ -198,6 +198,7 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
     D.ncells = cells;
     D.cfl = o->cfl;
     D.tol = o->tol;
+    D.tol_rate = o->tol_rate >= 0.0 && std::isfinite(o->tol_rate) ? o->tol_rate : 0.0;
     D.horizon = o->horizon;
     D.max_steps = o->max_steps > 0 ? o->max_steps : 1000000;
     D.V[0] = v_out;
@@ -214,9 +215,10 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
     D.ntiles = ntiles;
     D.state = d_state;
     D.active = d_ints;
+    D.kinit = o->init == HJI_INIT_USER_K ? k : (o->init == HJI_INIT_RESIDENT ? v_out : nullptr);
+    D.keep_lo = 0;
 
     const int counts[2] = {1, (int)ntiles};
-    const void* kk = o->init == HJI_INIT_USER_K ? k : (o->init == HJI_INIT_RESIDENT ? v_out : nullptr);
     e = cudaMemsetAsync(d_state, 0, sizeof(InstState), s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_desc, &D, sizeof(InstDesc), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_ints, counts, sizeof(counts), cudaMemcpyHostToDevice, s);
@@ -226,9 +228,7 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = hji::launch_setup(d_desc, &D, 1, f32, s);
-    const void* karr[1] = {kk};
-    const int keep[1] = {0};
-    if (e == cudaSuccess) e = hji::launch_init(d_desc, &D, 1, f32, karr, keep, s);
+    if (e == cudaSuccess) e = hji::launch_init(d_desc, &D, 1, f32, s);
     InstState hs;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, d_state, sizeof(hs), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -20,8 +20,8 @@ __device__ __forceinline__ double apply_fn(int fn, double x) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) table_kernel(const InstDesc* __restrict__ d) {
-    const InstDesc& D = *d;
+__global__ void __launch_bounds__(kThreads) table_kernel(const InstDesc* __restrict__ insts) {
+    const InstDesc& D = insts[blockIdx.z];
     T* table = static_cast<T*>(D.table);
     for (int t = blockIdx.y; t < D.dyn.nterms; t += gridDim.y) {
         const int ax = D.dyn.term_axis[t];
@@ -35,8 +35,8 @@ __global__ void __launch_bounds__(kThreads) table_kernel(const InstDesc* __restr
 
 constexpr int kAlphaTab = 2048;  // term values cached per CTA (FP64)
 
-__global__ void __launch_bounds__(kThreads) alpha_kernel(const InstDesc* __restrict__ d) {
-    const InstDesc& D = *d;
+__global__ void __launch_bounds__(kThreads) alpha_kernel(const InstDesc* __restrict__ insts) {
+    const InstDesc& D = insts[blockIdx.y];
     const int nd = D.ndim;
     const Dyn& f = D.dyn;
     // w_t phi_t(x) depends on one coordinate: tabulate it once per CTA when
@@ -129,9 +129,10 @@ __global__ void __launch_bounds__(kThreads) alpha_kernel(const InstDesc* __restr
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
-    init_kernel(const InstDesc* __restrict__ d, const T* __restrict__ k, int keep_lo) {
-    const InstDesc& D = *d;
+__global__ void __launch_bounds__(kThreads) init_kernel(const InstDesc* __restrict__ insts) {
+    const InstDesc& D = insts[blockIdx.y];
+    const T* __restrict__ k = static_cast<const T*>(D.kinit);
+    const int keep_lo = D.keep_lo;
     const T* l = static_cast<const T*>(D.l);
     T* V = static_cast<T*>(D.V[0]);
     // FP32 grids: the low word of V starts at zero, or, when k is the grid's
@@ -200,32 +201,34 @@ static int grid_for(long long work, int cap) {
 
 cudaError_t launch_setup(const InstDesc* d_insts, const InstDesc* h_insts, int count, bool f32,
                          cudaStream_t s) {
+    long long cmax = 0, nmax = 0;
+    int tmax = 0;
     for (int i = 0; i < count; ++i) {
         const InstDesc& H = h_insts[i];
-        if (H.dyn.nterms > 0) {
-            long long nmax = 0;
-            for (int a = 0; a < H.ndim; ++a) nmax = H.n[a] > nmax ? H.n[a] : nmax;
-            dim3 grid(grid_for(nmax, 64), H.dyn.nterms);
-            if (f32)
-                table_kernel<float><<<grid, kThreads, 0, s>>>(d_insts + i);
-            else
-                table_kernel<double><<<grid, kThreads, 0, s>>>(d_insts + i);
-        }
-        alpha_kernel<<<grid_for(H.ncells, 1024), kThreads, 0, s>>>(d_insts + i);
+        cmax = H.ncells > cmax ? H.ncells : cmax;
+        tmax = H.dyn.nterms > tmax ? H.dyn.nterms : tmax;
+        for (int a = 0; a < H.ndim; ++a) nmax = H.n[a] > nmax ? H.n[a] : nmax;
     }
+    if (tmax > 0) {
+        dim3 grid(grid_for(nmax, 64), tmax, count);
+        if (f32)
+            table_kernel<float><<<grid, kThreads, 0, s>>>(d_insts);
+        else
+            table_kernel<double><<<grid, kThreads, 0, s>>>(d_insts);
+    }
+    alpha_kernel<<<dim3(grid_for(cmax, 1024), count), kThreads, 0, s>>>(d_insts);
     return cudaGetLastError();
 }
 
 cudaError_t launch_init(const InstDesc* d_insts, const InstDesc* h_insts, int count, bool f32,
-                        const void* const* k, const int* keep_lo, cudaStream_t s) {
-    for (int i = 0; i < count; ++i) {
-        const int g = grid_for(h_insts[i].ncells, 4096);
-        const int kl = keep_lo ? keep_lo[i] : 0;
-        if (f32)
-            init_kernel<float><<<g, kThreads, 0, s>>>(d_insts + i, static_cast<const float*>(k[i]), kl);
-        else
-            init_kernel<double><<<g, kThreads, 0, s>>>(d_insts + i, static_cast<const double*>(k[i]), kl);
-    }
+                        cudaStream_t s) {
+    long long cmax = 0;
+    for (int i = 0; i < count; ++i) cmax = h_insts[i].ncells > cmax ? h_insts[i].ncells : cmax;
+    const dim3 grid(grid_for(cmax, 4096), count);
+    if (f32)
+        init_kernel<float><<<grid, kThreads, 0, s>>>(d_insts);
+    else
+        init_kernel<double><<<grid, kThreads, 0, s>>>(d_insts);
     return cudaGetLastError();
 }
 

@@ -283,7 +283,7 @@ __device__ inline void finish_step(const InstDesc& D) {
     if (!(d <= DBL_MAX)) {  // NaN or Inf
         st->status = 1;
         st->stop = 1;
-    } else if (d < D.tol) {
+    } else if (d < D.tol + D.tol_rate * st->dt) {
         st->converged = 1;
         st->stop = 1;
     } else if (D.horizon > 0.0 && tau >= D.horizon) {

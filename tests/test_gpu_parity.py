@@ -234,3 +234,19 @@ def test_invalid_inputs_rejected(hji_lib, torch_cuda):
         g2.solve(l, max_steps=5)
     assert e.value.status == hji_lib.HJI_E_STATE
     g2.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_rate_rule_stops_like_the_oracle(orc, hji_lib, torch_cuda, prec):
+    """Sec. IV's convergence rule as a rate (tol_rate = 0.1: change < 0.001
+    per 0.01 of time): same stopping step as the oracle."""
+    gd, dyn, l = W.di_config(101, dmax=0.1)
+    opts = dict(scheme="eno2", rk=2, cfl=0.5, tol=0.0, tol_rate=0.1, max_steps=20000)
+    Vo, so = orc.solve(orc.problem(gd, dyn), l, **opts)
+    g = _grid(hji_lib, gd, dyn, prec)
+    st = g.solve(l.astype(np.float64 if prec == "f64" else np.float32), **opts)
+    V = g.value().astype(np.float64)
+    g.close()
+    assert so["converged"] and st["converged"]
+    assert st["steps"] == so["steps"]
+    assert np.abs(V - Vo).max() <= (1e-9 if prec == "f64" else 1e-4 * np.abs(l).max())

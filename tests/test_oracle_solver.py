@@ -324,3 +324,17 @@ def test_runge_kutta_time_order(orc, rk, order, c):
     measured = np.log2(errs[0] / errs[1])
     assert abs(measured - order) < 0.25, (errs, measured)
     assert errs[1] < {1: 1e-2, 2: 3e-5, 3: 1e-7}[rk]
+
+
+def test_rate_rule_stops_at_first_slow_step(orc):
+    """Sec. IV's rule as a rate: the march stops at the first step whose
+    max|dV| is below tol_rate * dt, which a fixed-length march's history of
+    max|dV| locates independently."""
+    gd, dyn, l = W.di_config(51)
+    P = orc.problem(gd, dyn)
+    _, st_fixed, hist = orc.solve(P, l, tol=0.0, max_steps=600, history=600)
+    dt = st_fixed["dt"]
+    want = int(np.argmax(hist < 0.1 * dt)) + 1
+    assert hist[want - 1] < 0.1 * dt and np.all(hist[: want - 1] >= 0.1 * dt)
+    V, st = orc.solve(P, l, tol=0.0, tol_rate=0.1, max_steps=600)
+    assert st["converged"] and st["steps"] == want
