@@ -320,7 +320,7 @@ def main():
     if rank == 0 and not args.no_variants:
         line["time_to_converge"] = time_to_converge(hji, torch, gd, dyn, l, l_dev, k_dev)
         line["hbm_workloads"] = hbm_workloads(hji, torch)
-        line["serving"] = serving(hji, torch)
+        line["serving"] = serving_both(hji, torch)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(budget_s=12.0)
     g.close()
@@ -415,6 +415,13 @@ def run_hbm_workload(args, hji, torch, dist, rank, world, local_rank):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def serving_both(hji, torch):
+    """The specified stream (50 requests/s, far above one GPU's capacity for
+    these grid sizes) and a stream below capacity (1.5 requests/s)."""
+    return {"rate_50_per_s": serving(hji, torch, duration=6.0, rate=50.0, time_cap=60.0),
+            "rate_1.5_per_s": serving(hji, torch, duration=20.0, rate=1.5, time_cap=60.0)}
 
 
 def serving(hji, torch, duration=6.0, rate=50.0, time_cap=90.0):
