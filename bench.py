@@ -313,7 +313,7 @@ def main():
                        "l2": "flushed (512 MB write) before every timed solve; the 1001^2 "
                              "fields stay L2-resident within a solve",
                        "parallelism": "independent instance per GPU" if world > 1 else "1 GPU",
-                       "tile_shape": ["16x32", "8x32", "32x32"][tuned],
+                       "tile_shape": ["32x32", "16x64", "64x16"][tuned],
                        "autotune_ms_per_step": tune_ms},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk}
 
@@ -514,7 +514,7 @@ def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=N
             launches += max(s["kernel_launches"] for s in sts)
         clk = clocks.stop() if clocks is not None else None
         gbs = upd * bytes_per_update / (ms * 1e-3) / 1e9
-        out[name] = {"nodes": cells, "steps": steps, "ms": ms / repeats, "tile_shape": tuned,
+        out[name] = {"nodes": cells, "steps": steps, "ms": ms / repeats, "tile_shape": ["32x32", "16x64", "64x16"][tuned],
                      "cell_updates_per_s": upd / (ms * 1e-3), "ms_total": ms,
                      "updates_total": upd, "launches": launches, "clocks": clk,
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",

@@ -199,8 +199,9 @@ hji_status hji_value_get(hji_grid g, void* out, int ptr_is_device, void* cuda_st
  * dynamics and options mean what they mean for hji_grid_create,
  * hji_dynamics_set and hji_solve.  Every scratch buffer lives in one static
  * device array of HJI_NOALLOC_SCRATCH_BYTES bytes that each GPU loading the
- * library holds until exit; a grid that needs more (about 3 values per node
- * for FP64 RK3, 4 for FP32 RK3, plus small tables) returns HJI_E_INVALID.
+ * library holds until exit; a grid that needs more (5 values per node for
+ * FP64 RK3, 7 for FP32 RK3, rows padded to a multiple of 8 nodes, plus small
+ * tables) returns HJI_E_INVALID.
  * The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress, once per device); make it before any stream
  * capture.  Calls share the array: calls whose GPU work overlaps race.  No

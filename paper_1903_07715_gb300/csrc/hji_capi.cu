@@ -17,10 +17,77 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "hji_common.cuh"
 
 using hji::InstDesc;
 using hji::InstState;
+
+namespace hji {
+
+// TMA descriptors of an instance's fields.  The encoder comes from the
+// driver through the runtime's entry-point lookup (no link against the
+// driver library).  Dimensions are listed fastest first with the true node
+// counts, so a box reaching past the grid reads zeros there; row strides use
+// the padded pitch.
+bool encode_maps(InstDesc& D, bool f32, int scheme, int variant, const char** why) {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        else
+            cudaGetLastError();
+    });
+    if (!encode) {
+        *why = "cuTensorMapEncodeTiled is not available from the driver";
+        return false;
+    }
+    const int nd = D.ndim;
+    int TY, TX;
+    tile_dims(nd, variant, TY, TX);
+    const int G = ghost_width(scheme);
+    const int GY = nd >= 2 ? G : 0;
+    const size_t es = f32 ? 4 : 8;
+    cuuint64_t dims[MAXD], strides[MAXD];
+    for (int i = 0; i < nd; ++i) dims[i] = (cuuint64_t)D.n[nd - 1 - i];
+    for (int i = 1; i < nd; ++i) strides[i - 1] = (cuuint64_t)D.stride[nd - 1 - i] * es;
+    const cuuint32_t wbox[MAXD] = {(cuuint32_t)(TX + 8), (cuuint32_t)(TY + 2 * GY), 1, 1};
+    const cuuint32_t nbox[MAXD] = {(cuuint32_t)TX, (cuuint32_t)TY, 1, 1};
+    const cuuint32_t estr[MAXD] = {1, 1, 1, 1};
+    const CUtensorMapDataType dt = f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    auto enc = [&](int slot, const void* ptr, const cuuint32_t* box) {
+        if (!ptr) {
+            std::memset(&D.tm[slot], 0, sizeof(CUtensorMap));
+            return true;
+        }
+        const CUresult r = encode(&D.tm[slot], dt, (cuuint32_t)nd, const_cast<void*>(ptr), dims, strides,
+                                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            *why = "cuTensorMapEncodeTiled rejected a field";
+            return false;
+        }
+        return true;
+    };
+    bool ok = enc(TM_WIN_V0, D.V[0], wbox) && enc(TM_WIN_V1, D.V[1], wbox) &&
+              enc(TM_WIN_W1, D.W1, wbox) && enc(TM_WIN_W2, D.W2, wbox) && enc(TM_NODE_L, D.l, nbox);
+    if (f32) {
+        ok = ok && enc(TM_WIN_LO0, D.Vlo[0], wbox) && enc(TM_WIN_LO1, D.Vlo[1], wbox);
+        std::memset(&D.tm[TM_NODE_V0], 0, 2 * sizeof(CUtensorMap));
+    } else {
+        ok = ok && enc(TM_NODE_V0, D.V[0], nbox) && enc(TM_NODE_V1, D.V[1], nbox);
+        std::memset(&D.tm[TM_WIN_LO0], 0, 2 * sizeof(CUtensorMap));
+    }
+    return ok;
+}
+
+}  // namespace hji
 
 struct hji_grid_s {
     int ndim = 0;
@@ -32,13 +99,15 @@ struct hji_grid_s {
     hji_precision prec = HJI_F64;
     size_t esize = 8;
     int64_t ncells = 0;
+    int64_t pitch = 0;               // padded length of the fastest axis (elements)
+    int64_t nalloc = 0;              // elements of one field: pitch x (rows of the other axes)
     int device = 0;
     bool has_alloc = false;
     hji_allocator alloc{};
     void* V[2] = {nullptr, nullptr};
     void* W1 = nullptr;
     void* W2 = nullptr;
-    void* Vlo = nullptr;             // FP32 grids: low word of the compensated value
+    void* Vlo[2] = {nullptr, nullptr};  // FP32 grids: low words of the compensated value (with V[])
     void* l = nullptr;
     void* table = nullptr;
     size_t table_bytes = 0;
@@ -144,6 +213,30 @@ void dev_free(hji_grid g, void* p, cudaStream_t s) {
     if (!p) return;
     if (g->has_alloc) g->alloc.free(p, s, g->alloc.ctx);
     else cudaFreeAsync(p, s);
+}
+
+// Copies between a dense C-order array (rows of n[ndim-1] elements) and a
+// grid field whose rows are padded to the grid's pitch.
+cudaError_t copy_rows(hji_grid g, void* dst, size_t dpitch, const void* src, size_t spitch,
+                      cudaMemcpyKind kind, cudaStream_t s) {
+    const size_t w = (size_t)g->n[g->ndim - 1] * g->esize;
+    const size_t rows = (size_t)(g->nalloc / g->pitch);
+    if (rows == 1 || (dpitch == w && spitch == w)) return cudaMemcpyAsync(dst, src, w * rows, kind, s);
+    if (dpitch < (1ull << 31) && spitch < (1ull << 31))
+        return cudaMemcpy2DAsync(dst, dpitch, src, spitch, w, rows, kind, s);
+    cudaError_t e = cudaSuccess;  // rows too long for a 2-D copy: few of them
+    for (size_t r = 0; r < rows && e == cudaSuccess; ++r)
+        e = cudaMemcpyAsync(static_cast<char*>(dst) + r * dpitch,
+                            static_cast<const char*>(src) + r * spitch, w, kind, s);
+    return e;
+}
+cudaError_t copy_in(hji_grid g, void* field, const void* dense, cudaMemcpyKind kind, cudaStream_t s) {
+    return copy_rows(g, field, (size_t)g->pitch * g->esize, dense,
+                     (size_t)g->n[g->ndim - 1] * g->esize, kind, s);
+}
+cudaError_t copy_out(hji_grid g, void* dense, const void* field, cudaMemcpyKind kind, cudaStream_t s) {
+    return copy_rows(g, dense, (size_t)g->n[g->ndim - 1] * g->esize, field,
+                     (size_t)g->pitch * g->esize, kind, s);
 }
 
 int num_sms() {
@@ -270,7 +363,7 @@ hji_status validate_opts(hji_grid g, const hji_solve_opts* o) {
 
 // Make sure the stage buffers and the term table exist for this solve.
 hji_status ensure_buffers(hji_grid g, int rk, cudaStream_t s) {
-    const size_t bytes = (size_t)g->ncells * g->esize;
+    const size_t bytes = (size_t)g->nalloc * g->esize;
     if (rk >= 2 && !g->W1) {
         g->W1 = dev_alloc(g, bytes, s);
         if (!g->W1) return fail(g, HJI_E_NOMEM, "stage buffer allocation failed");
@@ -290,22 +383,28 @@ hji_status ensure_buffers(hji_grid g, int rk, cudaStream_t s) {
     return HJI_OK;
 }
 
-InstDesc make_desc(hji_grid g, const hji_solve_opts* o, int* active, int variant) {
-    InstDesc D;
+// Element strides of a grid's fields: C order, the fastest axis padded to
+// `pitch`.
+void field_strides(int ndim, const int64_t* n, long long pitch, long long* stride) {
+    long long s = 1;
+    for (int a = ndim - 1; a >= 0; --a) {
+        stride[a] = s;
+        s *= (a == ndim - 1) ? pitch : n[a];
+    }
+}
+
+hji_status make_desc(hji_grid g, const hji_solve_opts* o, int* active, int variant, InstDesc& D) {
     std::memset(&D, 0, sizeof(D));
     D.ndim = g->ndim;
-    long long stride = 1;
     for (int a = HJI_MAX_DIM - 1; a >= 0; --a) {
         D.n[a] = (int)g->n[a];
         D.periodic[a] = g->periodic[a];
         D.lo[a] = g->lo[a];
         D.dx[a] = g->dx[a];
     }
-    for (int a = g->ndim - 1; a >= 0; --a) {
-        D.stride[a] = stride;
-        stride *= g->n[a];
-    }
+    field_strides(g->ndim, g->n, g->pitch, D.stride);
     D.ncells = g->ncells;
+    D.nalloc = g->nalloc;
     D.dyn = g->dyn;
     D.cfl = o->cfl;
     D.tol = o->tol;
@@ -316,7 +415,8 @@ InstDesc make_desc(hji_grid g, const hji_solve_opts* o, int* active, int variant
     D.V[1] = g->V[1];
     D.W1 = g->W1;
     D.W2 = g->W2;
-    D.Vlo = g->Vlo;
+    D.Vlo[0] = g->Vlo[0];
+    D.Vlo[1] = g->Vlo[1];
     D.l = g->l;
     D.table = g->table;
     long long nmax = 0;
@@ -332,7 +432,10 @@ InstDesc make_desc(hji_grid g, const hji_solve_opts* o, int* active, int variant
     D.ntiles = tx * ty * planes;
     D.state = g->state;
     D.active = active;
-    return D;
+    const char* why = nullptr;
+    if (!hji::encode_maps(D, g->prec == HJI_F32, o->scheme, variant, &why))
+        return fail(g, HJI_E_CUDA, std::string("tensor map: ") + why);
+    return HJI_OK;
 }
 
 // Capture `steps` steps of the march (all RK stages) into a graph.
@@ -449,35 +552,31 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
     auto cleanup = [&]() {};
 
     std::vector<const void*> kptr(count, nullptr);
-    std::vector<int> keep_lo(count, 0);
+    std::vector<const void*> kptr_lo(count, nullptr);
     std::vector<unsigned long long> tiles;
     tiles.reserve((size_t)total_tiles);
     for (int i = 0; i < count; ++i) {
         hji_grid g = grids[i];
-        const size_t bytes = (size_t)g->ncells * g->esize;
-        cudaError_t e = cudaMemcpyAsync(g->l, l[i], bytes, kind, s);
+        cudaError_t e = copy_in(g, g->l, l[i], kind, s);
         if (e != cudaSuccess) {
             cleanup();
             return cuda_fail(g, e, "copy of l");
         }
         if (o->init == HJI_INIT_USER_K) {
-            if (ptr_is_device) {
-                kptr[i] = k[i];
-            } else {
-                e = cudaMemcpyAsync(g->V[1], k[i], bytes, cudaMemcpyHostToDevice, s);
-                if (e != cudaSuccess) {
-                    cleanup();
-                    return cuda_fail(g, e, "copy of k");
-                }
-                kptr[i] = g->V[1];
+            e = copy_in(g, g->V[1], k[i], kind, s);
+            if (e != cudaSuccess) {
+                cleanup();
+                return cuda_fail(g, e, "copy of k");
             }
+            kptr[i] = g->V[1];
         } else if (o->init == HJI_INIT_RESIDENT) {
             kptr[i] = g->V[g->cur];
-            keep_lo[i] = 1;
+            kptr_lo[i] = g->Vlo[g->cur];
         }
-        H[i] = make_desc(g, o, d_active, variant);
+        st = make_desc(g, o, d_active, variant, H[i]);
+        if (st != HJI_OK) return st;
         H[i].kinit = kptr[i];
-        H[i].keep_lo = keep_lo[i];
+        H[i].kinit_lo = kptr_lo[i];
         for (long long t = 0; t < H[i].ntiles; ++t) tiles.push_back(hji::make_tile(i, t));
         e = cudaMemsetAsync(g->state, 0, sizeof(InstState), s);
         if (e != cudaSuccess) {
@@ -583,6 +682,8 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
         hji_status si = HJI_OK;
         if (S.status == 1) {
             si = fail(g, HJI_E_NONFINITE, "the march produced NaN or Inf");
+        } else if (S.status == 4) {
+            si = fail(g, HJI_E_TIMEOUT, "a bounded device wait gave up (a tile copy never arrived)");
         } else if (!S.converged) {
             si = fail(g, HJI_E_NOT_CONVERGED, "stopped by the horizon or the step cap");
         }
@@ -654,23 +755,28 @@ hji_status hji_grid_create(int ndim, const int64_t* n, const double* lo, const d
     g->prec = prec;
     g->esize = prec == HJI_F32 ? 4 : 8;
     g->ncells = total;
+    g->pitch = hji::pitch_of(n[ndim - 1]);
+    g->nalloc = total / n[ndim - 1] * g->pitch;
     cudaGetDevice(&g->device);
     if (alloc) {
         g->has_alloc = true;
         g->alloc = *alloc;
     }
     cudaStream_t s = nullptr;
-    const size_t bytes = (size_t)total * g->esize;
+    const size_t bytes = (size_t)g->nalloc * g->esize;
     g->V[0] = dev_alloc(g, bytes, s);
     g->V[1] = dev_alloc(g, bytes, s);
     g->l = dev_alloc(g, bytes, s);
-    if (prec == HJI_F32) g->Vlo = dev_alloc(g, bytes, s);
+    if (prec == HJI_F32) {
+        g->Vlo[0] = dev_alloc(g, bytes, s);
+        g->Vlo[1] = dev_alloc(g, bytes, s);
+    }
     g->state = (InstState*)dev_alloc(g, sizeof(InstState), s);
     g->d_desc = (InstDesc*)dev_alloc(g, sizeof(InstDesc), s);
     g->desc_cap = g->d_desc ? 1 : 0;
     g->d_active = (int*)dev_alloc(g, sizeof(int) * 2, s);
     bool ok = g->V[0] && g->V[1] && g->l && g->state && g->d_desc && g->d_active &&
-              (prec != HJI_F32 || g->Vlo);
+              (prec != HJI_F32 || (g->Vlo[0] && g->Vlo[1]));
     g->d_ntiles = ok ? g->d_active + 1 : nullptr;
     if (ok && cudaMallocHost(&g->h_state, sizeof(InstState) * 2) != cudaSuccess) ok = false;
     if (ok && cudaMallocHost(&g->h_active, sizeof(int) * 2) != cudaSuccess) ok = false;
@@ -690,7 +796,7 @@ hji_status hji_grid_destroy(hji_grid g) {
     cudaStream_t s = nullptr;
     cudaStreamSynchronize(s);
     if (g->graph) cudaGraphExecDestroy(g->graph);
-    void* bufs[] = {g->V[0], g->V[1], g->W1, g->W2, g->Vlo, g->l, g->table, g->state,
+    void* bufs[] = {g->V[0], g->V[1], g->W1, g->W2, g->Vlo[0], g->Vlo[1], g->l, g->table, g->state,
                     g->d_desc, g->d_active, g->d_tiles};
     for (void* p : bufs) dev_free(g, p, s);
     if (g->h_state) cudaFreeHost(g->h_state);
@@ -775,9 +881,8 @@ hji_status hji_value_get(hji_grid g, void* out, int ptr_is_device, void* cuda_st
     if (!out) return fail(g, HJI_E_INVALID, "out is NULL");
     if (!g->has_value) return fail(g, HJI_E_STATE, "no value yet: call hji_solve first");
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    const size_t bytes = (size_t)g->ncells * g->esize;
-    HJI_CUDA(g, cudaMemcpyAsync(out, g->V[g->cur], bytes,
-                                ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    HJI_CUDA(g, copy_out(g, out, g->V[g->cur],
+                         ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     HJI_CUDA(g, cudaStreamSynchronize(s));
     return HJI_OK;
 }
@@ -791,8 +896,8 @@ hji_status hji_value_transfer(hji_grid dst, hji_grid src, void* cuda_stream) {
     if (!src->has_value) return fail(dst, HJI_E_STATE, "source grid has no value yet");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const bool sf = src->prec == HJI_F32, df = dst->prec == HJI_F32;
-    HJI_CUDA(dst, hji::launch_convert(src->ncells, src->V[src->cur], sf ? src->Vlo : nullptr, sf,
-                                      dst->V[0], df ? dst->Vlo : nullptr, df, s));
+    HJI_CUDA(dst, hji::launch_convert(src->nalloc, src->V[src->cur], sf ? src->Vlo[src->cur] : nullptr,
+                                      sf, dst->V[0], df ? dst->Vlo[0] : nullptr, df, s));
     HJI_CUDA(dst, cudaStreamSynchronize(s));
     dst->cur = 0;
     dst->has_value = true;
@@ -806,8 +911,8 @@ static hji_status efail(hji_engine e, hji_status st, const std::string& msg) {
 }
 
 static size_t grid_bytes(hji_grid g, int rk) {
-    const size_t field = (size_t)g->ncells * g->esize;
-    size_t n = 3 + (rk >= 2 ? 1 : 0) + (rk >= 3 ? 1 : 0) + (g->prec == HJI_F32 ? 1 : 0);
+    const size_t field = (size_t)g->nalloc * g->esize;
+    size_t n = 3 + (rk >= 2 ? 1 : 0) + (rk >= 3 ? 1 : 0) + (g->prec == HJI_F32 ? 2 : 0);
     return n * field + g->table_bytes;
 }
 
@@ -887,10 +992,9 @@ hji_status hji_engine_submit(hji_engine e, hji_grid g, const void* l, const void
     if (st != HJI_OK) return efail(e, st, g->err);
     if (e->budget && grid_bytes(g, e->o.rk_order) > e->budget)
         return efail(e, HJI_E_INVALID, "grid larger than the engine's whole budget");
-    const size_t bytes = (size_t)g->ncells * g->esize;
     const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    cudaError_t ce = cudaMemcpyAsync(g->l, l, bytes, kind, e->s);
-    if (ce == cudaSuccess && init == HJI_INIT_USER_K) ce = cudaMemcpyAsync(g->V[1], k, bytes, kind, e->s);
+    cudaError_t ce = copy_in(g, g->l, l, kind, e->s);
+    if (ce == cudaSuccess && init == HJI_INIT_USER_K) ce = copy_in(g, g->V[1], k, kind, e->s);
     if (ce == cudaSuccess && !ptr_is_device) ce = cudaStreamSynchronize(e->s);
     if (ce != cudaSuccess) return efail(e, HJI_E_CUDA, std::string("copy of l/k: ") + cudaGetErrorString(ce));
     e->queue.push_back({g, tag, init, init == HJI_INIT_USER_K});
@@ -923,6 +1027,7 @@ static hji_status engine_retire(hji_engine e) {
         if (S.nonfinite) d.status = HJI_E_INVALID;
         else if (S.status == 2) d.status = HJI_E_INVALID;
         else if (S.status == 1) d.status = HJI_E_NONFINITE;
+        else if (S.status == 4) d.status = HJI_E_TIMEOUT;
         else d.status = S.converged ? HJI_OK : HJI_E_NOT_CONVERGED;
         sl.g->cur = S.cur;
         sl.g->has_value = S.steps > 0 || sl.g->has_value;
@@ -960,8 +1065,9 @@ hji_status hji_engine_step(hji_engine e, int* active, int* queued) {
                 break;
             }
         if (slot < 0) break;
+        if (make_desc(req.g, &e->o, e->d_counts, e->variant, e->h_desc[slot]) != HJI_OK)
+            return efail(e, HJI_E_CUDA, req.g->err);
         e->queue.pop_front();
-        e->h_desc[slot] = make_desc(req.g, &e->o, e->d_counts, e->variant);
         auto& sl = e->slots[slot];
         sl.used = true;
         sl.g = req.g;
@@ -1007,7 +1113,7 @@ hji_status hji_engine_step(hji_engine e, int* active, int* queued) {
         const hji_init init = e->slots[slot].init;
         InstDesc& D = e->h_desc[slot];
         D.kinit = init == HJI_INIT_USER_K ? g->V[1] : (init == HJI_INIT_RESIDENT ? g->V[g->cur] : nullptr);
-        D.keep_lo = init == HJI_INIT_RESIDENT ? 1 : 0;
+        D.kinit_lo = init == HJI_INIT_RESIDENT ? g->Vlo[g->cur] : nullptr;
         ce = cudaMemsetAsync(g->state, 0, sizeof(InstState), e->s);
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(e->d_desc + slot, &D, sizeof(InstDesc), cudaMemcpyHostToDevice, e->s);
         if (ce == cudaSuccess) ce = hji::launch_setup(e->d_desc + slot, &D, 1, f32, e->s);

@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "hji.h"
@@ -52,13 +53,32 @@ struct InstState {
     double alpha[MAXD];
 };
 
+// Tensor maps of one instance (TMA descriptors, encoded on the host):
+// "window" maps copy a tile with its ghost halo (TX + 8 columns starting 4
+// left of the tile, TY + 2G rows), "node" maps copy the tile's own nodes.
+enum TensorMapSlot {
+    TM_WIN_V0, TM_WIN_V1,    // V[0], V[1]: FP64 stage input / FP32 high word
+    TM_WIN_LO0, TM_WIN_LO1,  // FP32 low words Vlo[0], Vlo[1]
+    TM_WIN_W1, TM_WIN_W2,    // stage buffers (FP64 states, FP32 increments)
+    TM_NODE_L,               // l
+    TM_NODE_V0, TM_NODE_V1,  // FP64 V^n for the last stage's combination
+    kNumMaps
+};
+
 // Read-only description of one instance for one solve.
+//
+// Fields are stored in C order with the fastest axis padded to a pitch that
+// is a multiple of 8 elements (stride[ndim-2] = pitch), so that every row
+// starts on a 32-byte boundary: the alignment TMA needs for its row strides
+// and for 16-byte vector accesses of four FP32 (or two FP64) nodes.
 struct InstDesc {
+    alignas(64) CUtensorMap tm[kNumMaps];
     int ndim;
     int periodic[MAXD];
     int n[MAXD];
-    long long stride[MAXD];   // element strides, C order
-    long long ncells;
+    long long stride[MAXD];   // element strides, C order, fastest axis padded
+    long long ncells;         // nodes
+    long long nalloc;         // elements of one field (pitch x rows)
     double lo[MAXD], dx[MAXD];
     Dyn dyn;
     double cfl, tol, horizon, tol_rate;
@@ -66,7 +86,7 @@ struct InstDesc {
     void* V[2];               // ping-pong value buffers: V[cur] = V^n
     void* W1;                 // stage buffers of the Runge-Kutta step: stage
     void* W2;                 // states (FP64) or stage increments (FP32)
-    void* Vlo;                // FP32 only: low word of V = V[cur] + Vlo
+    void* Vlo[2];             // FP32 only: low words, ping-pong with V: V^n = V[cur] + Vlo[cur]
     void* l;                  // target function l(x)
     void* table;              // per-term tables: table[t*n_max + i] = w_t phi_t(x_axis(i))
     long long table_stride;
@@ -76,7 +96,7 @@ struct InstDesc {
     InstState* state;
     int* active;              // batch-wide count of instances still marching (may be null)
     const void* kinit;        // warm start read by the init pass (null: V0 = l)
-    int keep_lo;              // kinit is the grid's own resident value: keep its FP32 low word
+    const void* kinit_lo;     // FP32: low word of kinit when it is a resident value (else null)
 };
 
 // Tile list entry: instance index in the high 16 bits, tile index within the
@@ -86,28 +106,35 @@ __host__ __device__ inline unsigned long long make_tile(int inst, long long loca
            (static_cast<unsigned long long>(local) & 0xFFFFFFFFFFFFull);
 }
 
-// Tile shapes.  1-D tiles are 256 nodes of one row.  N-D tiles cover the
-// two fastest axes at a fixed index of the slower axes (which are read from
-// global memory / L2 directly): variant 0 is 16 x 32 nodes, and 2-D grids
-// also have variant 1 (8 x 32: finer work units, better balance on small
-// grids) and variant 2 (32 x 32: less halo per node on large grids), chosen
-// per problem class by the autotuner.
+// Tile shapes.  A thread updates one run of four consecutive nodes of the
+// fastest axis, so a tile has 4 x 256 nodes.  1-D tiles are 248 nodes (the
+// staged window of 256 is the largest TMA box; threads past the 62nd idle).
+// N-D tiles cover the two fastest axes at a fixed index of the slower axes
+// (which are read from global memory / L2 directly): variant 0 is 32 x 32
+// nodes (rows x columns, the least halo per node), and 2-D grids also have
+// variant 1 (16 x 64) and variant 2 (64 x 16), which fit narrow or short
+// grids with less padding; the autotuner picks per problem class.  Every
+// shape runs the same per-node arithmetic, so results do not depend on it.
 constexpr int kTileVariants = 3;
+constexpr int kPitchAlign = 8;  // elements
 template <int NDIM, int V = 0>
 struct TileShape {
-    static constexpr int TY = (NDIM == 1) ? 1 : (V == 1 ? 8 : (V == 2 ? 32 : 16));
-    static constexpr int TX = (NDIM == 1) ? 256 : 32;
+    static constexpr int TY = (NDIM == 1) ? 1 : (V == 1 ? 16 : (V == 2 ? 64 : 32));
+    static constexpr int TX = (NDIM == 1) ? 248 : (V == 1 ? 64 : (V == 2 ? 16 : 32));
+    static constexpr int GROUPS = TX / 4;  // 4-node runs per row
+    static_assert(NDIM == 1 || TY * GROUPS == kThreads, "one run per thread");
 };
 inline void tile_dims(int ndim, int variant, int& ty, int& tx) {
     if (ndim == 1) {
         ty = 1;
-        tx = 256;
+        tx = 248;
         return;
     }
     const int v = ndim == 2 ? variant : 0;
-    ty = v == 1 ? 8 : (v == 2 ? 32 : 16);
-    tx = 32;
+    ty = v == 1 ? 16 : (v == 2 ? 64 : 32);
+    tx = v == 1 ? 64 : (v == 2 ? 16 : 32);
 }
+inline long long pitch_of(long long nx) { return (nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign; }
 
 inline int ghost_width(int scheme) { return scheme == HJI_ENO1 ? 1 : (scheme == HJI_ENO2 ? 2 : 3); }
 
@@ -148,6 +175,10 @@ cudaError_t launch_setup(const InstDesc* d_insts, const InstDesc* h_insts, int c
 // the init pass reads each instance's warm start from its kinit / keep_lo.
 cudaError_t launch_init(const InstDesc* d_insts, const InstDesc* h_insts, int count, bool f32,
                         cudaStream_t s);
+// Encode the tensor maps of D for the given precision, scheme and tile
+// variant (host; D's field pointers, sizes and strides must be set).
+// Returns false (with a message) if the driver rejects a map.
+bool encode_maps(InstDesc& D, bool f32, int scheme, int variant, const char** why);
 cudaError_t launch_convert(long long n, const void* src_hi, const void* src_lo, bool src_f32,
                            void* dst_hi, void* dst_lo, bool dst_f32, cudaStream_t s);
 

@@ -140,23 +140,29 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
     const bool f32 = prec == HJI_F32;
     const size_t es = f32 ? 4 : 8;
     long long tx, ty, planes = 1;
-    const int TX = ndim == 1 ? hji::TileShape<1>::TX : hji::TileShape<2>::TX;
-    const int TY = ndim == 1 ? hji::TileShape<1>::TY : hji::TileShape<2>::TY;
+    int TX, TY;
+    hji::tile_dims(ndim, 0, TY, TX);
     tx = (n[ndim - 1] + TX - 1) / TX;
     ty = ndim >= 2 ? (n[ndim - 2] + TY - 1) / TY : 1;
     for (int a = 0; a < ndim - 2; ++a) planes *= n[a];
     const long long ntiles = tx * ty * planes;
-    const size_t field = align256((size_t)cells * es);
+    const long long pitch = hji::pitch_of(n[ndim - 1]);
+    const long long rows = cells / n[ndim - 1];
+    const long long nalloc = pitch * rows;
+    const size_t field = align256((size_t)nalloc * es);
     size_t off = 0;
     const size_t o_state = off; off += align256(sizeof(InstState));
     const size_t o_desc = off;  off += align256(sizeof(InstDesc));
     const size_t o_ints = off;  off += 256;
     const size_t o_tiles = off; off += align256((size_t)ntiles * sizeof(unsigned long long));
     const size_t o_table = off; off += align256((size_t)HJI_MAX_TERMS * nmax * es);
+    const size_t o_v0 = off;    off += field;
     const size_t o_v1 = off;    off += field;
+    const size_t o_l = off;     off += field;
     const size_t o_w1 = off;    off += o->rk_order >= 2 ? field : 0;
     const size_t o_w2 = off;    off += o->rk_order >= 3 ? field : 0;
     const size_t o_lo = off;    off += f32 ? field : 0;
+    const size_t o_lo1 = off;   off += f32 ? field : 0;
     if (off > (size_t)HJI_NOALLOC_SCRATCH_BYTES) {
         std::snprintf(g_err, sizeof(g_err),
                       "grid needs %zu bytes of scratch; hji_solve_noalloc holds %u", off,
@@ -182,7 +188,6 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
     unsigned long long* d_tiles = reinterpret_cast<unsigned long long*>(base + o_tiles);
 
     D.ndim = ndim;
-    long long stride = 1;
     for (int a = HJI_MAX_DIM - 1; a >= 0; --a) {
         D.n[a] = a < ndim ? (int)n[a] : 1;
         D.periodic[a] = (a < ndim && periodic) ? (periodic[a] != 0) : 0;
@@ -191,22 +196,27 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
                                             : (hi[a] - lo[a]) / (double)(n[a] - 1))
                            : 1.0;
     }
-    for (int a = ndim - 1; a >= 0; --a) {
-        D.stride[a] = stride;
-        stride *= n[a];
+    {
+        long long stride = 1;  // C order, fastest axis padded to the pitch
+        for (int a = ndim - 1; a >= 0; --a) {
+            D.stride[a] = stride;
+            stride *= (a == ndim - 1) ? pitch : n[a];
+        }
     }
     D.ncells = cells;
+    D.nalloc = nalloc;
     D.cfl = o->cfl;
     D.tol = o->tol;
     D.tol_rate = o->tol_rate >= 0.0 && std::isfinite(o->tol_rate) ? o->tol_rate : 0.0;
     D.horizon = o->horizon;
     D.max_steps = o->max_steps > 0 ? o->max_steps : 1000000;
-    D.V[0] = v_out;
+    D.V[0] = base + o_v0;
     D.V[1] = base + o_v1;
     D.W1 = o->rk_order >= 2 ? base + o_w1 : nullptr;
     D.W2 = o->rk_order >= 3 ? base + o_w2 : nullptr;
-    D.Vlo = f32 ? base + o_lo : nullptr;
-    D.l = const_cast<void*>(l);
+    D.Vlo[0] = f32 ? base + o_lo : nullptr;
+    D.Vlo[1] = f32 ? base + o_lo1 : nullptr;
+    D.l = base + o_l;
     D.table = base + o_table;
     D.table_stride = nmax;
     D.tiles_x = tx;
@@ -215,11 +225,27 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
     D.ntiles = ntiles;
     D.state = d_state;
     D.active = d_ints;
-    D.kinit = o->init == HJI_INIT_USER_K ? k : (o->init == HJI_INIT_RESIDENT ? v_out : nullptr);
-    D.keep_lo = 0;
+    D.kinit = o->init == HJI_INIT_STANDARD ? nullptr : D.V[1];
+    D.kinit_lo = nullptr;
+    {
+        const char* why = nullptr;
+        if (!hji::encode_maps(D, f32, o->scheme, 0, &why)) return nfail(HJI_E_CUDA, why);
+    }
+    // l (and k, or the caller's previous value for HJI_INIT_RESIDENT) into
+    // the padded scratch fields.
+    const size_t wrow = (size_t)n[ndim - 1] * es, prow = (size_t)pitch * es;
+    if (rows > 1 && prow >= (1ull << 31)) return nfail(HJI_E_INVALID, "rows too long for hji_solve_noalloc");
+    auto rows_copy = [&](void* dst, size_t dp, const void* src, size_t sp) {
+        if (rows == 1 || dp == sp)
+            return cudaMemcpyAsync(dst, src, wrow * (size_t)rows, cudaMemcpyDeviceToDevice, s);
+        return cudaMemcpy2DAsync(dst, dp, src, sp, wrow, (size_t)rows, cudaMemcpyDeviceToDevice, s);
+    };
 
     const int counts[2] = {1, (int)ntiles};
-    e = cudaMemsetAsync(d_state, 0, sizeof(InstState), s);
+    e = rows_copy(D.l, prow, l, wrow);
+    if (e == cudaSuccess && o->init != HJI_INIT_STANDARD)
+        e = rows_copy(D.V[1], prow, o->init == HJI_INIT_USER_K ? k : v_out, wrow);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_state, 0, sizeof(InstState), s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_desc, &D, sizeof(InstDesc), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_ints, counts, sizeof(counts), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
@@ -288,8 +314,7 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
     }
     e = cudaMemcpyAsync(&hs, d_state, sizeof(hs), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess && hs.cur == 1)
-        e = cudaMemcpyAsync(v_out, base + o_v1, (size_t)cells * es, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = rows_copy(v_out, wrow, hs.cur == 1 ? D.V[1] : D.V[0], prow);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return ncuda(e, "final state");
     if (stats) {
@@ -303,6 +328,7 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
         stats->kernel_launches = launches;
     }
     if (hs.status == 1) return nfail(HJI_E_NONFINITE, "the march produced NaN or Inf");
+    if (hs.status == 4) return nfail(HJI_E_TIMEOUT, "a bounded device wait gave up");
     if (!hs.converged) return nfail(HJI_E_NOT_CONVERGED, "stopped by the horizon or the step cap");
     g_err[0] = '\0';
     return HJI_OK;

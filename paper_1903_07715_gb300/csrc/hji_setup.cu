@@ -120,8 +120,7 @@ __global__ void __launch_bounds__(kThreads) alpha_kernel(const InstDesc* __restr
             } else {
                 st->dt = 0.0;
                 st->status = 2;
-                st->stop = 1;
-                if (D.active != nullptr) atomicSub(D.active, 1);
+                if (atomicExch(&st->stop, 1) == 0 && D.active != nullptr) atomicSub(D.active, 1);
             }
             __threadfence();
         }
@@ -132,21 +131,26 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) init_kernel(const InstDesc* __restrict__ insts) {
     const InstDesc& D = insts[blockIdx.y];
     const T* __restrict__ k = static_cast<const T*>(D.kinit);
-    const int keep_lo = D.keep_lo;
+    const T* __restrict__ klo_p = static_cast<const T*>(D.kinit_lo);
     const T* l = static_cast<const T*>(D.l);
     T* V = static_cast<T*>(D.V[0]);
     // FP32 grids: the low word of V starts at zero, or, when k is the grid's
     // own resident value, keeps that value's low word.
-    T* Vlo = static_cast<T*>(D.Vlo);
+    T* Vlo = static_cast<T*>(D.Vlo[0]);
+    // Fields are rows of the fastest axis padded to the pitch; pad elements
+    // are left alone.
+    const int nx = D.n[D.ndim - 1];
+    const long long pitch = D.ndim >= 2 ? D.stride[D.ndim - 2] : D.nalloc;
     unsigned int bad = 0u;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < D.ncells;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < D.nalloc;
          c += (long long)gridDim.x * blockDim.x) {
+        if (c % pitch >= nx) continue;
         const T lv = l[c];
         T v = lv, vlo = T(0);
         if (!isfinite(lv)) bad = 1u;
         if (k != nullptr) {
             const T kv = k[c];
-            const T klo = (keep_lo && Vlo != nullptr) ? Vlo[c] : T(0);
+            const T klo = (klo_p != nullptr && Vlo != nullptr) ? klo_p[c] : T(0);
             if (!isfinite(kv)) bad = 1u;
             if (kv < lv || (kv == lv && klo < T(0))) {
                 v = kv;

@@ -1,10 +1,14 @@
 // The fused Runge-Kutta stage kernel: one launch advances one stage of every
 // live instance in the batch.  Per tile of nodes it
-//   1. stages the stencil input W (tile + ghost halo of the two fastest axes)
-//      in shared memory, building ghost nodes beyond the grid edge by linear
-//      extrapolation (or periodic wrap) while loading;
+//   1. copies the stencil input W (tile + ghost halo of the two fastest axes)
+//      into shared memory with TMA (one thread issues the tensor copies of
+//      the next tile while the CTA computes the current one), then builds the
+//      ghost nodes beyond the grid edge by linear extrapolation (or periodic
+//      wrap);
 //   2. forms the one-sided derivatives p-, p+ along every axis (ENO1, ENO2 or
-//      HJ-WENO5; slower axes read their stencil lines from L2 directly);
+//      HJ-WENO5): each thread takes runs of four consecutive nodes of the
+//      fastest axis, whose WENO5 stencils share smoothness indicators, and
+//      slower axes read their stencil lines from L2 directly;
 //   3. evaluates the closed-form control-affine Hamiltonian of Eq. (6) at the
 //      averaged gradient plus the Lax-Friedrichs dissipation;
 //   4. combines the Euler stage W + dt L(W) with V^n (TVD Runge-Kutta);
@@ -14,6 +18,10 @@
 //      counter, tau, stop flag and buffer index.
 // Tiles of instances that have stopped are skipped, so launches queued after
 // convergence do no work and no step past the stop point ever runs.
+//
+// Every wait on a TMA copy is bounded (kWaitNs); a CTA whose copy does not
+// arrive records the failure (HJI_E_TIMEOUT) in the instance's state, stops
+// the instance and returns.
 #pragma once
 
 #include <cfloat>
@@ -45,43 +53,80 @@ __device__ __forceinline__ T smaller_mag(T a, T b) {
 // HJ-WENO5 (Jiang and Peng) on undivided one-sided differences v1..v5, with
 // eps = 1e-6 max(v^2) + tiny as in the textbook form (the relative part is
 // scale free, so undivided differences give the divided-difference weights).
-// FP64 forms the normalised weights d_k / (S_k + eps)^2 as
-// d_k q_k / sum_j d_j q_j with q_1 = (b2 b3)^2, q_2 = (b1 b3)^2,
-// q_3 = (b1 b2)^2, b_k = S_k + eps: one division.  FP32 uses the fast
-// reciprocals r_k = 1/b_k, a_k = d_k r_k^2 and 1/sum a_k; tiny = 1e-18 keeps
-// sum a_k below 2^126 (the range of the fast division) while exceeding
-// 1e-6 max(v^2) only where every |v| < 1e-6 (flat data, where the weights do
-// not matter).
+//
+// The weights split into a part that depends only on the set {v1..v5} and
+// its orientation.  With S_A, S_B, S_C the smoothness indicators of
+// (v1,v2,v3), (v2,v3,v4), (v3,v4,v5) and b = S + eps, the forward derivative
+// weighs d = (0.1, 0.6, 0.3) against (b_A, b_B, b_C); the derivative on the
+// reversed differences (v5..v1) has the same three indicators in reverse
+// order (the indicator formula is symmetric under reversing its triple), so
+// it weighs d against (b_C, b_B, b_A).  Neighbouring nodes of a line use the
+// same five differences for p+ of the left node and p- of the right node,
+// which therefore share one WenoZ.
+//
+// WenoZ holds z1..z3 with forward weights (0.1 z1, 0.6 z2, 0.3 z3) and
+// reversed weights (0.1 z3, 0.6 z2, 0.3 z1), normalised by their sum:
+//   FP64: z = ((b_B b_C)^2, (b_A b_C)^2, (b_A b_B)^2), the weights
+//         d_k / b_k^2 times the common factor (b_A b_B b_C)^2: one division
+//         (tiny = 1e-60 keeps the fourth powers above the FP64 range floor);
+//   FP32: z = (r_A^2, r_B^2, r_C^2), r = 1/b by the fast reciprocal; tiny =
+//         1e-18 keeps the sum below 2^126 (the range of the fast division)
+//         while exceeding 1e-6 max(v^2) only where every |v| < 1e-6 (flat
+//         data, where the weights do not matter).
 template <typename T>
-__device__ __forceinline__ T weno5(T v1, T v2, T v3, T v4, T v5) {
-    const T phi1 = v1 * T(1.0 / 3.0) - v2 * T(7.0 / 6.0) + v3 * T(11.0 / 6.0);
-    const T phi2 = -v2 * T(1.0 / 6.0) + v3 * T(5.0 / 6.0) + v4 * T(1.0 / 3.0);
-    const T phi3 = v3 * T(1.0 / 3.0) + v4 * T(5.0 / 6.0) - v5 * T(1.0 / 6.0);
+struct WenoZ {
+    T z1, z2, z3;
+};
+
+template <typename T>
+__device__ __forceinline__ WenoZ<T> weno_z(T v1, T v2, T v3, T v4, T v5) {
     const T a = v1 - T(2) * v2 + v3, b = v1 - T(4) * v2 + T(3) * v3;
     const T c = v2 - T(2) * v3 + v4, d = v2 - v4;
     const T e = v3 - T(2) * v4 + v5, f = T(3) * v3 - T(4) * v4 + v5;
-    const T s1 = T(13.0 / 12.0) * a * a + T(0.25) * b * b;
-    const T s2 = T(13.0 / 12.0) * c * c + T(0.25) * d * d;
-    const T s3 = T(13.0 / 12.0) * e * e + T(0.25) * f * f;
+    const T sA = T(13.0 / 12.0) * a * a + T(0.25) * b * b;
+    const T sB = T(13.0 / 12.0) * c * c + T(0.25) * d * d;
+    const T sC = T(13.0 / 12.0) * e * e + T(0.25) * f * f;
     const T vm = fmax(fmax(fmax(v1 * v1, v2 * v2), fmax(v3 * v3, v4 * v4)), v5 * v5);
+    WenoZ<T> z;
     if constexpr (sizeof(T) == 4) {
         const float eps = 1e-6f * vm + 1e-18f;
-        const float r1 = __fdividef(1.0f, s1 + eps);
-        const float r2 = __fdividef(1.0f, s2 + eps);
-        const float r3 = __fdividef(1.0f, s3 + eps);
-        const float a1 = 0.1f * (r1 * r1), a2 = 0.6f * (r2 * r2), a3 = 0.3f * (r3 * r3);
-        const float num = a1 * phi1 + a2 * phi2 + a3 * phi3;
-        return __fdividef(num, a1 + a2 + a3);
+        const float rA = __fdividef(1.0f, sA + eps);
+        const float rB = __fdividef(1.0f, sB + eps);
+        const float rC = __fdividef(1.0f, sC + eps);
+        z.z1 = rA * rA;
+        z.z2 = rB * rB;
+        z.z3 = rC * rC;
     } else {
         const T eps = T(1e-6) * vm + Num<T>::weno_tiny();
-        const T b1 = s1 + eps, b2 = s2 + eps, b3 = s3 + eps;
-        const T b12 = b1 * b2, b13 = b1 * b3, b23 = b2 * b3;
-        const T w1 = T(0.1) * (b23 * b23);
-        const T w2 = T(0.6) * (b13 * b13);
-        const T w3 = T(0.3) * (b12 * b12);
-        const T num = w1 * phi1 + w2 * phi2 + w3 * phi3;
-        return num / (w1 + w2 + w3);
+        const T bA = sA + eps, bB = sB + eps, bC = sC + eps;
+        const T pBC = bB * bC, pAC = bA * bC, pAB = bA * bB;
+        z.z1 = pBC * pBC;
+        z.z2 = pAC * pAC;
+        z.z3 = pAB * pAB;
     }
+    return z;
+}
+
+// The WENO5 derivative on v1..v5 with weights (0.1 w1, 0.6 w2, 0.3 w3).
+template <typename T>
+__device__ __forceinline__ T weno_combine(T v1, T v2, T v3, T v4, T v5, T w1, T w2, T w3) {
+    const T phi1 = v1 * T(1.0 / 3.0) - v2 * T(7.0 / 6.0) + v3 * T(11.0 / 6.0);
+    const T phi2 = -v2 * T(1.0 / 6.0) + v3 * T(5.0 / 6.0) + v4 * T(1.0 / 3.0);
+    const T phi3 = v3 * T(1.0 / 3.0) + v4 * T(5.0 / 6.0) - v5 * T(1.0 / 6.0);
+    const T a1 = T(0.1) * w1, a2 = T(0.6) * w2, a3 = T(0.3) * w3;
+    const T num = a1 * phi1 + a2 * phi2 + a3 * phi3;
+    if constexpr (sizeof(T) == 4) return __fdividef(num, a1 + a2 + a3);
+    else return num / (a1 + a2 + a3);
+}
+
+// p- on the forward set v[0..4]; p+ on the reversed set v[4..0].
+template <typename T>
+__device__ __forceinline__ T weno_fwd(const T* v, const WenoZ<T>& z) {
+    return weno_combine(v[0], v[1], v[2], v[3], v[4], z.z1, z.z2, z.z3);
+}
+template <typename T>
+__device__ __forceinline__ T weno_rev(const T* v, const WenoZ<T>& z) {
+    return weno_combine(v[4], v[3], v[2], v[1], v[0], z.z3, z.z2, z.z1);
 }
 
 // (p-, p+) at node c from the 2G undivided differences D[k] = W[k+1] - W[k]
@@ -97,8 +142,8 @@ __device__ __forceinline__ void one_sided_diffs(const T* D, T inv_dx, T& pm, T& 
         pm = (D[1] + T(0.5) * smaller_mag(Sm, S0)) * inv_dx;
         pp = (D[2] - T(0.5) * smaller_mag(S0, Sp)) * inv_dx;
     } else {
-        pm = weno5<T>(D[0], D[1], D[2], D[3], D[4]) * inv_dx;
-        pp = weno5<T>(D[5], D[4], D[3], D[2], D[1]) * inv_dx;
+        pm = weno_fwd(D, weno_z(D[0], D[1], D[2], D[3], D[4])) * inv_dx;
+        pp = weno_rev(D + 1, weno_z(D[1], D[2], D[3], D[4], D[5])) * inv_dx;
     }
 }
 
@@ -176,6 +221,47 @@ __device__ __forceinline__ T pair_diff(const Pair<T>& b, const Pair<T>& a) {
     }
 }
 
+// ---- four consecutive values (16 bytes FP32, 32 bytes FP64) ----
+template <typename T>
+struct Q4 {
+    T v[4];
+};
+template <typename T>
+__device__ __forceinline__ Q4<T> ld4(const T* p) {  // shared or global, 16-byte aligned
+    Q4<T> q;
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        q.v[0] = a.x; q.v[1] = a.y; q.v[2] = a.z; q.v[3] = a.w;
+    } else {
+        const double2 a = reinterpret_cast<const double2*>(p)[0];
+        const double2 b = reinterpret_cast<const double2*>(p)[1];
+        q.v[0] = a.x; q.v[1] = a.y; q.v[2] = b.x; q.v[3] = b.y;
+    }
+    return q;
+}
+template <typename T>
+__device__ __forceinline__ Q4<T> ldg4(const T* p) {  // read-only global, 16-byte aligned
+    Q4<T> q;
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        q.v[0] = a.x; q.v[1] = a.y; q.v[2] = a.z; q.v[3] = a.w;
+    } else {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+        q.v[0] = a.x; q.v[1] = a.y; q.v[2] = b.x; q.v[3] = b.y;
+    }
+    return q;
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T* v) {  // 16-byte aligned
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+    }
+}
+
 // Shared-memory copy of what a tile needs from its instance, in precision T.
 template <typename T>
 struct TileCtx {
@@ -186,20 +272,27 @@ struct TileCtx {
     int n[MAXD];
     int periodic[MAXD];
     long long stride[MAXD];
-    long long tiles_x, tiles_per_plane, ntiles;
+    int tiles_x, tiles_per_plane, ntiles;
     T lo[MAXD], dx[MAXD], inv_dx[MAXD], half_alpha[MAXD];
-    T c[MAXD], A[MAXD * MAXD], G[MAXD * MAXU], E[MAXD * MAXU];
-    T ulo[MAXU], uhi[MAXU], dlo[MAXU], dhi[MAXU];
+    T cmid[MAXD], A[MAXD * MAXD], G[MAXD * MAXU], E[MAXD * MAXU];
+    T urad[MAXU], drad[MAXU];  // half-widths of the control and disturbance boxes
     int term_row[MAXT], term_axis[MAXT];
     T dt;
     const T* win;   // stencil input (FP64: the stage state; FP32: V^n hi word)
     const T* din;   // FP32: stage increment added to win (null for stage 1)
     const T* vcur;
     T* wout;
-    T* vlo;         // FP32: low word of V^n, updated in place by the last stage
+    const T* vlo;   // FP32: low word of V^n
+    T* vlo_out;     // FP32: low word of V^{n+1}, written by the last stage
     const T* l;
     const T* table;
     long long table_stride;
+    // TMA descriptors of the fields this stage copies.
+    const CUtensorMap* tm_win;   // stencil input (high word)
+    const CUtensorMap* tm_lo;    // FP32 low word of V^n
+    const CUtensorMap* tm_d;     // FP32 stage increment
+    const CUtensorMap* tm_l;     // l at the tile nodes
+    const CUtensorMap* tm_vn;    // FP64 V^n at the tile nodes
 };
 
 // Fill the tile context; called by every thread of the CTA (each copies a
@@ -214,11 +307,11 @@ __device__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict__ insts, int 
     if (t < MAXD * MAXD) C.A[t] = T(D.dyn.A[t]);
     else if (t < 32) C.G[t - 16] = T(D.dyn.G[t - 16]);
     else if (t < 48) C.E[t - 32] = T(D.dyn.E[t - 32]);
-    else if (t < 52) C.ulo[t - 48] = T(D.dyn.ulo[t - 48]);
-    else if (t < 56) C.uhi[t - 52] = T(D.dyn.uhi[t - 52]);
-    else if (t < 60) C.dlo[t - 56] = T(D.dyn.dlo[t - 56]);
-    else if (t < 64) C.dhi[t - 60] = T(D.dyn.dhi[t - 60]);
-    else if (t < 72) {
+    else if (t < 52) C.urad[t - 48] = T(0.5 * (D.dyn.uhi[t - 48] - D.dyn.ulo[t - 48]));
+    else if (t < 56) C.drad[t - 52] = T(0.5 * (D.dyn.dhi[t - 52] - D.dyn.dlo[t - 52]));
+    else if (t < 64) {
+        // threads 56..63 have no slice
+    } else if (t < 72) {
         C.term_row[t - 64] = D.dyn.term_row[t - 64];
         C.term_axis[t - 64] = D.dyn.term_axis[t - 64];
     } else if (t < 76) {
@@ -231,7 +324,13 @@ __device__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict__ insts, int 
         C.dx[i] = T(D.dx[i]);
         C.inv_dx[i] = T(1.0 / D.dx[i]);
         C.half_alpha[i] = T(0.5 * st->alpha[i]);
-        C.c[i] = T(D.dyn.c[i]);
+        // c + G umid + E dmid: the box centres' share of the drift.
+        double cm = D.dyn.c[i];
+        for (int j = 0; j < MAXU; ++j) {
+            cm += D.dyn.G[i * MAXU + j] * (0.5 * (D.dyn.ulo[j] + D.dyn.uhi[j]));
+            cm += D.dyn.E[i * MAXU + j] * (0.5 * (D.dyn.dlo[j] + D.dyn.dhi[j]));
+        }
+        C.cmid[i] = T(cm);
     } else if (t == 96) {
         InstState* st = D.state;
         const int cur = *((volatile int*)&st->cur);
@@ -242,27 +341,43 @@ __device__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict__ insts, int 
         C.q = D.dyn.q;
         C.nterms = D.dyn.nterms;
         C.dt = T(*((volatile double*)&st->dt));
-        C.tiles_x = D.tiles_x;
-        C.tiles_per_plane = D.tiles_per_plane;
-        C.ntiles = D.ntiles;
+        C.tiles_x = static_cast<int>(D.tiles_x);
+        C.tiles_per_plane = static_cast<int>(D.tiles_per_plane);
+        C.ntiles = static_cast<int>(D.ntiles);
         const T* vc = static_cast<const T*>(D.V[cur]);
         const T* stage =
             a.stage_in == 0 ? nullptr : static_cast<const T*>(a.stage_in == 1 ? D.W1 : D.W2);
+        const int tm_v = cur ? TM_WIN_V1 : TM_WIN_V0;
+        const int tm_s = a.stage_in == 1 ? TM_WIN_W1 : TM_WIN_W2;
         C.vcur = vc;
         if constexpr (sizeof(T) == 4) {
             C.win = vc;
             C.din = stage;
+            C.tm_win = &D.tm[tm_v];
+            C.tm_d = stage ? &D.tm[tm_s] : nullptr;
         } else {
             C.win = stage ? stage : vc;
             C.din = nullptr;
+            C.tm_win = &D.tm[stage ? tm_s : tm_v];
+            C.tm_d = nullptr;
         }
-        C.vlo = static_cast<T*>(D.Vlo);
+        C.tm_lo = &D.tm[cur ? TM_WIN_LO1 : TM_WIN_LO0];
+        C.tm_l = &D.tm[TM_NODE_L];
+        C.tm_vn = &D.tm[cur ? TM_NODE_V1 : TM_NODE_V0];
+        C.vlo = static_cast<const T*>(D.Vlo[cur]);
+        C.vlo_out = static_cast<T*>(D.Vlo[cur ^ 1]);
         C.wout = a.stage_out == 3 ? static_cast<T*>(D.V[cur ^ 1])
                                   : static_cast<T*>(a.stage_out == 1 ? D.W1 : D.W2);
         C.l = static_cast<const T*>(D.l);
         C.table = static_cast<const T*>(D.table);
         C.table_stride = D.table_stride;
     }
+}
+
+// Stop an instance once: the thread that flips the flag lowers the
+// batch-wide count of marching instances.
+__device__ inline void stop_instance(const InstDesc& D) {
+    if (atomicExch(&D.state->stop, 1) == 0 && D.active != nullptr) atomicSub(D.active, 1);
 }
 
 // Finish one step of an instance: called by the single thread whose tile was
@@ -280,62 +395,131 @@ __device__ inline void finish_step(const InstDesc& D) {
     if (D.history != nullptr && steps - 1 < D.history_len) D.history[steps - 1] = d;
     st->delta_bits = 0ull;
     st->tiles_done = 0u;
+    bool stop = false;
     if (!(d <= DBL_MAX)) {  // NaN or Inf
         st->status = 1;
-        st->stop = 1;
+        stop = true;
     } else if (d < D.tol + D.tol_rate * st->dt) {
         st->converged = 1;
-        st->stop = 1;
+        stop = true;
     } else if (D.horizon > 0.0 && tau >= D.horizon) {
-        st->stop = 1;
+        stop = true;
     } else if (steps >= D.max_steps) {
-        st->stop = 1;
+        stop = true;
     }
-    if (st->stop && D.active != nullptr) atomicSub(D.active, 1);
+    if (stop) stop_instance(D);
     __threadfence();
 }
 
-// ---- asynchronous global -> shared copies (cp.async, 4 or 8 bytes) ----
-template <int B>
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
-    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(B)
+// ---- TMA tensor copies and their mbarriers ----
+constexpr unsigned long long kWaitNs = 4000000000ull;  // a bounded wait gives up after 4 s
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0u;
 }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+// Wait for the phase with the given parity; false if it has not completed
+// within kWaitNs (or 2^26 polls).
+static __device__ __noinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1; it < (1u << 26); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 0u && global_ns() - t0 > kWaitNs) return false;
+    }
+    return false;
+}
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m) : "memory");
+}
+// Tiled tensor copy global -> shared, completing on `bar`; c[] are the
+// element coordinates of the box origin, fastest dimension first.
+template <int R>
+__device__ __forceinline__ void tma_load(unsigned dst, const CUtensorMap* m, const int* c,
+                                         unsigned bar) {
+    const unsigned long long mp = reinterpret_cast<unsigned long long>(m);
+    if constexpr (R == 1) {
+        asm volatile(
+            "cp.async.bulk.tensor.1d.shared::cluster.global.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2}], [%3];" ::"r"(dst), "l"(mp), "r"(c[0]), "r"(bar)
+            : "memory");
+    } else if constexpr (R == 2) {
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst), "l"(mp), "r"(c[0]), "r"(c[1]), "r"(bar)
+            : "memory");
+    } else if constexpr (R == 3) {
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst), "l"(mp), "r"(c[0]), "r"(c[1]),
+            "r"(c[2]), "r"(bar)
+            : "memory");
+    } else {
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst), "l"(mp), "r"(c[0]), "r"(c[1]),
+            "r"(c[2]), "r"(c[3]), "r"(bar)
+            : "memory");
+    }
 }
 
-// Dynamic shared-memory layout of one stage kernel (units of T): two
-// buffers of the staged tile (high words; FP32 also low words and stage
-// increments), two buffers of l (and, FP64, of V^n) for the tile nodes, and
-// the per-tile neighbour differences.
+// Dynamic shared-memory layout of one stage kernel: two buffers, each with
+// the staged window (high words; FP32 also low words and stage increments)
+// and, for the last stage, l (and, FP64, V^n) at the tile nodes; then the
+// y-differences of the current tile.  Window row r, column c holds the node
+// (y0 - GY + r, x0 - 4 + c): columns start 4 left of the tile so that every
+// copy starts on a 16-byte boundary.
+constexpr int round128(int b) { return (b + 127) / 128 * 128; }
+
 template <typename T, int NDIM, int SCHEME, bool LAST, int V>
 struct StageSmem {
+    using S = TileShape<NDIM, V>;
     static constexpr int G = Ghost<SCHEME>::G;
-    static constexpr int TY = TileShape<NDIM, V>::TY;
-    static constexpr int TX = TileShape<NDIM, V>::TX;
+    static constexpr int TY = S::TY, TX = S::TX, GROUPS = S::GROUPS;
     static constexpr int GY = (NDIM >= 2) ? G : 0;
-    static constexpr int SW = TX + 2 * G;
+    static constexpr int SWX = TX + 8;
     static constexpr int SH = TY + 2 * GY;
-    static constexpr int NR = SH * SW;
-    static constexpr int NI = TY * TX;
-    static constexpr int DXW = SW - 1;
-    static constexpr int DYH = SH - 1;
+    static constexpr int WIN = SWX * SH;   // elements of one window field
+    static constexpr int NODES = TY * TX;
     static constexpr bool INCR = sizeof(T) == 4;
-    static constexpr int RH = 0;
-    static constexpr int RL = RH + 2 * NR;
-    static constexpr int RD = RL + (INCR ? 2 * NR : 0);
-    static constexpr int LT = RD + (INCR ? 2 * NR : 0);
-    static constexpr int VN = LT + (LAST ? 2 * NI : 0);
-    static constexpr int DX = VN + ((LAST && !INCR) ? 2 * NI : 0);
-    static constexpr int DY = DX + TY * DXW;
-    static constexpr int NT = DY + (NDIM >= 2 ? DYH * TX : 0);
-    static constexpr size_t BYTES = NT * sizeof(T);
+    static constexpr int WINB = round128(WIN * (int)sizeof(T));
+    static constexpr int NODEB = round128(NODES * (int)sizeof(T));
+    static constexpr int NF = INCR ? 3 : 1;
+    static constexpr int NN = LAST ? (INCR ? 1 : 2) : 0;
+    static constexpr int BUFB = NF * WINB + NN * NODEB;
+    static constexpr int DYS = 2 * BUFB;
+    static constexpr int DYSB = NDIM >= 2 ? round128((SH - 1) * TX * (int)sizeof(T)) : 0;
+    static constexpr int BYTES = DYS + DYSB + 128;  // + alignment slack
+    static __host__ __device__ constexpr int H(int b) { return b * BUFB; }
+    static __host__ __device__ constexpr int LO(int b) { return b * BUFB + WINB; }
+    static __host__ __device__ constexpr int DD(int b) { return b * BUFB + 2 * WINB; }
+    static __host__ __device__ constexpr int LT(int b) { return b * BUFB + NF * WINB; }
+    static __host__ __device__ constexpr int VN(int b) { return b * BUFB + NF * WINB + NODEB; }
 };
 
 // Where tile `local` of an instance sits.  N-D tiles are enumerated with the
@@ -348,25 +532,27 @@ struct TileGeo {
 };
 
 template <typename T, int NDIM, int TY, int TX>
-__device__ __forceinline__ TileGeo tile_geo(const TileCtx<T>& C, long long local) {
+__device__ __forceinline__ TileGeo tile_geo(const TileCtx<T>& C, int local) {
     TileGeo g;
-    long long tip = local;
+    int tip = local;
     g.base = 0;
+#pragma unroll
+    for (int ax = 0; ax < MAXD; ++ax) g.sidx[ax] = 0;
     if constexpr (NDIM >= 3) {
-        long long r = local;
+        int r = local;
         const int ls = NDIM - 3;  // last slow axis
-        g.sidx[ls] = static_cast<int>(r % C.n[ls]);
+        g.sidx[ls] = r % C.n[ls];
         r /= C.n[ls];
         tip = r % C.tiles_per_plane;
         r /= C.tiles_per_plane;
         for (int ax = ls - 1; ax >= 0; --ax) {
-            g.sidx[ax] = static_cast<int>(r % C.n[ax]);
+            g.sidx[ax] = r % C.n[ax];
             r /= C.n[ax];
         }
         for (int ax = 0; ax <= ls; ++ax) g.base += (long long)g.sidx[ax] * C.stride[ax];
     }
-    const int by = static_cast<int>(tip / C.tiles_x);
-    const int bx = static_cast<int>(tip - (long long)by * C.tiles_x);
+    const int by = tip / C.tiles_x;
+    const int bx = tip - by * C.tiles_x;
     g.y0 = by * TY;
     g.x0 = bx * TX;
     return g;
@@ -399,23 +585,22 @@ struct TileWalk {
 };
 
 template <typename T, int NDIM, int SCHEME, bool LAST, int V>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 5 : 3) : 3)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 3) : 2)
     stage_kernel(const StageArgs a) {
     using L = StageSmem<T, NDIM, SCHEME, LAST, V>;
-    constexpr int G = L::G, TY = L::TY, TX = L::TX, GY = L::GY, SW = L::SW, SH = L::SH;
-    constexpr int NR = L::NR, NI = L::NI, DXW = L::DXW, DYH = L::DYH;
-    constexpr int ROWS_PER_PASS = kThreads / TX;
-    constexpr int CELLS = (TY + ROWS_PER_PASS - 1) / ROWS_PER_PASS;
-    constexpr int AX = NDIM - 1;  // fastest axis
+    constexpr int G = L::G, TY = L::TY, TX = L::TX, GROUPS = L::GROUPS;
+    constexpr int GY = L::GY, SWX = L::SWX, SH = L::SH, WIN = L::WIN;
+    constexpr int AX = NDIM - 1;                  // fastest axis
     constexpr int AY = NDIM >= 2 ? NDIM - 2 : 0;  // second fastest axis (used if NDIM >= 2)
-    constexpr bool INCR = L::INCR;  // FP32: increments + compensated V
+    constexpr bool INCR = L::INCR;                // FP32: increments + compensated V
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sm = reinterpret_cast<T*>(smem_raw);
-    T* dxs = sm + L::DX;  // dxs[r][c] = W(r, c+1) - W(r, c), tile rows
-    T* dys = sm + L::DY;  // dys[r][c] = W(r+1, c) - W(r, c)
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sb = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<unsigned long long>(smem_raw) + 127ull) & ~127ull);
     __shared__ TileCtx<T> C;
     __shared__ T red[kThreads / 32];
+    __shared__ __align__(8) unsigned long long bars[2];
+    T* dys = reinterpret_cast<T*>(sb + L::DYS);  // dys[r][c] = W(r+1, c) - W(r, c), tile columns
 
     const int ntiles = *a.ntiles;
     // Stage coefficients in the kernel's precision (no conversion in FP32).
@@ -429,74 +614,50 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 5 : 3)
     }
     const bool reads_v = a.reads_v != 0;
     const bool has_d = INCR && a.stage_in != 0;
-    const int tx = threadIdx.x % TX;
-    const int ty = threadIdx.x / TX;
-    int loaded = -1;
+    // Thread -> (tile row, run of four nodes).
+    const int grp = threadIdx.x % GROUPS;
+    const int ry = threadIdx.x / GROUPS;
+    const bool thread_works = NDIM >= 2 || threadIdx.x < GROUPS;
 
-    // Staged-window walk of this thread: element s = threadIdx.x + k kThreads
-    // sits at row r, column c; stepping by kThreads adds SR rows and SC
-    // columns (no divisions in the loops).
-    constexpr int SR = kThreads / SW, SC = kThreads % SW;
-    const int r_first = threadIdx.x / SW, c_first = threadIdx.x % SW;
+    const unsigned bar0 = smem_addr(&bars[0]);
+    if (threadIdx.x == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    unsigned phase = 0u;  // bit b: parity of the next completion of buffer b
 
-    // Issue the asynchronous copies of a tile's stencil input (and l, V^n)
-    // into buffer b.  Nodes outside the grid are filled in afterwards.
+    // Bytes one tile's copies deliver to its buffer's barrier.
+    const unsigned tile_bytes =
+        static_cast<unsigned>(WIN * sizeof(T)) * (INCR ? (has_d ? 3u : 2u) : 1u) +
+        (LAST ? static_cast<unsigned>(TY * TX * sizeof(T)) * ((!INCR && reads_v) ? 2u : 1u) : 0u);
+
+    // Thread 0: start the tensor copies of a tile into buffer b.
     auto issue = [&](const TileGeo& tg, int b) {
-        const int nx = C.n[AX];
-        const int ny = NDIM >= 2 ? C.n[AY] : 1;
-        const int sy = NDIM >= 2 ? static_cast<int>(C.stride[AY]) : 0;
-        const T* hp = C.win + tg.base;
-        const T* lp = INCR ? C.vlo + tg.base : nullptr;
-        const T* dp = C.din ? C.din + tg.base : nullptr;
-        const bool inside = tg.x0 - G >= 0 && tg.x0 + TX + G <= nx &&
-                            (NDIM < 2 || (tg.y0 - GY >= 0 && tg.y0 + TY + GY <= ny));
-        T* dh = sm + L::RH + b * NR;
-        T* dl = sm + L::RL + b * NR;
-        T* dd = sm + L::RD + b * NR;
-        int r = r_first, c = c_first;
-        int goff = (tg.y0 - GY + r) * sy + (tg.x0 - G + c);
-        for (int s = threadIdx.x; s < NR; s += kThreads) {
-            bool ok = inside;
-            if (!inside) {
-                const int gy = tg.y0 - GY + r, gx = tg.x0 - G + c;
-                ok = ((NDIM < 2) || (gy >= 0 && gy < ny)) && gx >= 0 && gx < nx;
-            }
-            if (ok) {
-                cp_async<sizeof(T)>(dh + s, hp + goff);
-                if constexpr (INCR) {
-                    cp_async<sizeof(T)>(dl + s, lp + goff);
-                    if (dp) cp_async<sizeof(T)>(dd + s, dp + goff);
-                }
-            }
-            c += SC;
-            r += SR;
-            goff += SR * sy + SC;
-            if (c >= SW) {
-                c -= SW;
-                ++r;
-                goff += sy - SW;
-            }
+        const unsigned bar = bar0 + 8u * b;
+        mbar_expect_tx(bar, tile_bytes);
+        int cw[4] = {tg.x0 - 4, tg.y0 - GY, 0, 0};
+        int cn[4] = {tg.x0, tg.y0, 0, 0};
+        if constexpr (NDIM >= 3) {
+            cw[2] = cn[2] = tg.sidx[NDIM - 3];
+            if constexpr (NDIM == 4) cw[3] = cn[3] = tg.sidx[0];
+        }
+        const unsigned base = smem_addr(sb);
+        tma_load<NDIM>(base + L::H(b), C.tm_win, cw, bar);
+        if constexpr (INCR) {
+            tma_load<NDIM>(base + L::LO(b), C.tm_lo, cw, bar);
+            if (has_d) tma_load<NDIM>(base + L::DD(b), C.tm_d, cw, bar);
         }
         if constexpr (LAST) {
-            // Tile nodes: thread (ty, tx) takes rows ty, ty + ROWS_PER_PASS, ...
-            const T* lg = C.l + tg.base;
-            const T* vg = C.vcur + tg.base;
-            const int gx = tg.x0 + tx;
-#pragma unroll
-            for (int k = 0; k < CELLS; ++k) {
-                const int ry = ty + k * ROWS_PER_PASS;
-                const int gy = tg.y0 + ry;
-                if (ry < TY && gy < ny && gx < nx) {
-                    const int si = ry * TX + tx;
-                    const int gi = gy * sy + gx;
-                    cp_async<sizeof(T)>(sm + L::LT + b * NI + si, lg + gi);
-                    if constexpr (!INCR) cp_async<sizeof(T)>(sm + L::VN + b * NI + si, vg + gi);
-                }
+            tma_load<NDIM>(base + L::LT(b), C.tm_l, cn, bar);
+            if constexpr (!INCR) {
+                if (reads_v) tma_load<NDIM>(base + L::VN(b), C.tm_vn, cn, bar);
             }
         }
-        cp_async_commit();
     };
 
+    int loaded = -1;
     TileWalk walk(ntiles);
     int t = walk.next();
     int buf = 0;
@@ -504,11 +665,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 5 : 3)
     while (t >= 0) {
         const unsigned long long entry = a.tiles[t];
         const int inst = static_cast<int>(entry >> 48);
-        const long long local = static_cast<long long>(entry & 0xFFFFFFFFFFFFull);
+        const int local = static_cast<int>(entry & 0xFFFFFFFFFFFFull);
         if (inst != loaded) {
             __syncthreads();  // everyone is done with the previous context
             load_ctx<T>(C, a.insts, inst, a);
             __syncthreads();
+            if (threadIdx.x == 0 && !C.stop) {
+                tensormap_acquire(C.tm_win);
+                if (INCR) tensormap_acquire(C.tm_lo);
+                if (has_d) tensormap_acquire(C.tm_d);
+                if (LAST) tensormap_acquire(C.tm_l);
+                if (LAST && !INCR && reads_v) tensormap_acquire(C.tm_vn);
+            }
             loaded = inst;
         }
         if (C.stop) {  // uniform across the CTA; nothing was issued for it
@@ -517,21 +685,29 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 5 : 3)
             continue;
         }
         const TileGeo tg = tile_geo<T, NDIM, TY, TX>(C, local);
-        if (!issued) issue(tg, buf);
         // Prefetch the next tile of the walk while this one is computed.
         const int tn = walk.next();
-        bool pref = false;
-        if (tn >= 0) {
-            const unsigned long long en = a.tiles[tn];
-            if (static_cast<int>(en >> 48) == inst) {
-                issue(tile_geo<T, NDIM, TY, TX>(C, static_cast<long long>(en & 0xFFFFFFFFFFFFull)),
+        const bool pref = tn >= 0 && static_cast<int>(a.tiles[tn] >> 48) == inst;
+        if (threadIdx.x == 0) {
+            if (!issued) issue(tg, buf);
+            if (pref)
+                issue(tile_geo<T, NDIM, TY, TX>(C, static_cast<int>(a.tiles[tn] & 0xFFFFFFFFFFFFull)),
                       buf ^ 1);
-                pref = true;
-            }
         }
-        if (pref) cp_async_wait<1>();
-        else cp_async_wait<0>();
-        __syncthreads();
+        const bool ok = mbar_wait_bounded(bar0 + 8u * buf, (phase >> buf) & 1u);
+        phase ^= 1u << buf;
+        if (__syncthreads_or(!ok)) {
+            // A copy never arrived: record it, stop the instance, give the
+            // prefetched copy (if any) a bounded wait and leave.
+            if (threadIdx.x == 0) {
+                const InstDesc& D = a.insts[inst];
+                atomicExch(&D.state->status, 4);
+                stop_instance(D);
+                if (pref) mbar_wait_bounded(bar0 + 8u * (buf ^ 1), (phase >> (buf ^ 1)) & 1u);
+            }
+            __syncthreads();
+            return;
+        }
 
         const int nx = C.n[AX];
         const int ny = NDIM >= 2 ? C.n[AY] : 1;
@@ -540,224 +716,413 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 5 : 3)
         const T* __restrict__ hp = C.win + tg.base;
         const T* __restrict__ lp = INCR ? C.vlo + tg.base : nullptr;
         const T* __restrict__ dp = C.din ? C.din + tg.base : nullptr;
-        T* rh = sm + L::RH + buf * NR;
-        T* rl = sm + L::RL + buf * NR;
-        T* rd = sm + L::RD + buf * NR;
+        T* wh = reinterpret_cast<T*>(sb + L::H(buf));
+        T* wl = reinterpret_cast<T*>(sb + L::LO(buf));
+        const T* wd = reinterpret_cast<const T*>(sb + L::DD(buf));
         // FP32 stages 2+: fold the increment into the low word once per node.
         if constexpr (INCR) {
             if (has_d) {
-                for (int s = threadIdx.x; s < NR; s += kThreads) rl[s] += rd[s];
+                for (int i = 4 * threadIdx.x; i < WIN; i += 4 * kThreads) {
+                    const Q4<T> lo = ld4(wl + i), d = ld4(wd + i);
+                    const T s[4] = {lo.v[0] + d.v[0], lo.v[1] + d.v[1], lo.v[2] + d.v[2],
+                                    lo.v[3] + d.v[3]};
+                    st4(wl + i, s);
+                }
                 __syncthreads();
             }
         }
-        auto pair_at = [&](int s) {
+        auto pair_at = [&](int r, int c) {
             Pair<T> p;
-            p.h = rh[s];
+            p.h = wh[r * SWX + c];
             p.l = T(0);
-            if constexpr (INCR) p.l = rl[s];
+            if constexpr (INCR) p.l = wl[r * SWX + c];
             return p;
         };
 
         // 1. Ghost nodes of tiles that reach beyond the grid edge: linear
         //    extrapolation from the two edge nodes (both inside the staged
-        //    window), or, on a periodic axis, the wrapped node.
+        //    window), or, on a periodic axis, the wrapped node.  Only the
+        //    ghosts an axis-aligned stencil of a tile node reaches are built:
+        //    along x for the tile rows, along y for the tile columns.
         const bool edge = x0 - G < 0 || x0 + TX + G > nx ||
                           (NDIM >= 2 && (y0 - GY < 0 || y0 + TY + GY > ny));
         if (edge) {
-            for (int s = threadIdx.x; s < NR; s += kThreads) {
-                const int r = s / SW, c = s - r * SW;
-                const int gy = y0 - GY + r, gx = x0 - G + c;
-                const bool iny = (NDIM < 2) || (gy >= 0 && gy < ny);
-                const bool inx = gx >= 0 && gx < nx;
-                if (iny && inx) continue;
+            constexpr int NXG = 2 * G * TY;
+            constexpr int NYG = NDIM >= 2 ? 2 * G * TX : 0;
+            for (int s = threadIdx.x; s < NXG + NYG; s += kThreads) {
                 Pair<T> v;
-                if (iny) {
+                int r, c;
+                if (s < NXG) {
+                    const int ry = s / (2 * G), j = s - ry * (2 * G);
+                    r = GY + ry;
+                    const int gy = y0 + ry;
+                    const int gx = j < G ? j - G : nx + (j - G);
+                    c = gx - x0 + 4;
+                    if ((NDIM >= 2 && gy >= ny) || c < 4 - G || c >= 4 + TX + G) continue;
                     if (C.periodic[AX]) {
                         const long long r0 = (long long)gy * sy;
                         v = line_pair<T>(hp + r0, lp ? lp + r0 : nullptr, dp ? dp + r0 : nullptr,
                                          gx, nx, 1, 1);
                     } else {
                         const bool low = gx < 0;
-                        const int ce = (low ? 0 : nx - 1) - (x0 - G);
-                        const int ci = (low ? 1 : nx - 2) - (x0 - G);
-                        v = extrapolate(pair_at(r * SW + ce), pair_at(r * SW + ci),
-                                        low ? -gx : gx - (nx - 1));
+                        const int ce = (low ? 0 : nx - 1) - x0 + 4;
+                        const int ci = (low ? 1 : nx - 2) - x0 + 4;
+                        v = extrapolate(pair_at(r, ce), pair_at(r, ci), low ? -gx : gx - (nx - 1));
                     }
-                } else if (inx) {
+                } else {
+                    const int s2 = s - NXG;
+                    const int j = s2 / TX, cx = s2 - j * TX;
+                    c = 4 + cx;
+                    const int gx = x0 + cx;
+                    const int gy = j < G ? j - G : ny + (j - G);
+                    r = gy - y0 + GY;
+                    if (gx >= nx || r < 0 || r >= SH) continue;
                     if (C.periodic[AY]) {
                         v = line_pair<T>(hp + gx, lp ? lp + gx : nullptr, dp ? dp + gx : nullptr,
                                          gy, ny, sy, 1);
                     } else {
                         const bool low = gy < 0;
-                        const int re = (low ? 0 : ny - 1) - (y0 - GY);
-                        const int ri = (low ? 1 : ny - 2) - (y0 - GY);
-                        v = extrapolate(pair_at(re * SW + c), pair_at(ri * SW + c),
-                                        low ? -gy : gy - (ny - 1));
+                        const int re = (low ? 0 : ny - 1) - y0 + GY;
+                        const int ri = (low ? 1 : ny - 2) - y0 + GY;
+                        v = extrapolate(pair_at(re, c), pair_at(ri, c), low ? -gy : gy - (ny - 1));
                     }
-                } else {
-                    v.h = T(0);  // corner of the halo: never used by an axis-aligned stencil
-                    v.l = T(0);
                 }
                 // Written after every read of this pass: ghost nodes only
                 // read in-grid nodes, and no thread writes an in-grid node.
-                rh[s] = v.h;
-                if constexpr (INCR) rl[s] = v.l;
+                wh[r * SWX + c] = v.h;
+                if constexpr (INCR) wl[r * SWX + c] = v.l;
             }
             __syncthreads();
         }
-        // 2. Each neighbour difference once per tile (FP32: on the pairs).
-        {
-            constexpr int XR = kThreads / DXW, XC = kThreads % DXW;
-            int r = threadIdx.x / DXW, c = threadIdx.x % DXW;
-            for (int i = threadIdx.x; i < TY * DXW; i += kThreads) {
-                const int s0 = (r + GY) * SW + c;
-                dxs[i] = pair_diff(pair_at(s0 + 1), pair_at(s0));
-                c += XC;
-                r += XR;
-                if (c >= DXW) {
-                    c -= DXW;
-                    ++r;
+        // 2. y-differences of the tile columns, once per tile (FP32: on the pairs).
+        if constexpr (NDIM >= 2) {
+            for (int i = threadIdx.x; i < (SH - 1) * GROUPS; i += kThreads) {
+                const int r = i / GROUPS, g4 = i - r * GROUPS;
+                const int s0 = r * SWX + 4 + 4 * g4;
+                const Q4<T> h0 = ld4(wh + s0), h1 = ld4(wh + s0 + SWX);
+                T dv[4];
+                if constexpr (INCR) {
+                    const Q4<T> l0 = ld4(wl + s0), l1 = ld4(wl + s0 + SWX);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) dv[q] = (h1.v[q] - h0.v[q]) + (l1.v[q] - l0.v[q]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) dv[q] = h1.v[q] - h0.v[q];
+                }
+                st4(dys + r * TX + 4 * g4, dv);
+            }
+            __syncthreads();
+        }
+
+        // 3-5. Each thread updates a run of 4 nodes of the tile.  The
+        // derivatives of each axis are folded at once into the
+        // Lax-Friedrichs sum Lv = sum_a alpha_a (p+ - p-) / 2 and the
+        // averaged gradient pbar, so they never need to be kept for all axes.
+        T dmax = T(0);
+        const int gx0 = x0 + 4 * grp;
+        const int gy = y0 + ry;
+        if (thread_works && gx0 < nx && (NDIM < 2 || gy < ny)) {
+            T Lv[4] = {T(0), T(0), T(0), T(0)};
+            T pb[4][NDIM];
+            auto fold = [&](int ax, int i, T pm_, T pp_) {
+                Lv[i] += C.half_alpha[ax] * (pp_ - pm_);
+                pb[i][ax] = T(0.5) * (pp_ + pm_);
+            };
+            // x: the window row of this run, columns 4 grp .. 4 grp + 11.
+            const int s0 = (ry + GY) * SWX + 4 * grp;
+            T wc[4], lc[4];  // the run's own stencil input (high, low)
+            {
+                T d[11];
+                const Q4<T> h0 = ld4(wh + s0), h1 = ld4(wh + s0 + 4), h2 = ld4(wh + s0 + 8);
+                const T hv[12] = {h0.v[0], h0.v[1], h0.v[2], h0.v[3], h1.v[0], h1.v[1],
+                                  h1.v[2], h1.v[3], h2.v[0], h2.v[1], h2.v[2], h2.v[3]};
+                if constexpr (INCR) {
+                    const Q4<T> l0 = ld4(wl + s0), l1 = ld4(wl + s0 + 4), l2 = ld4(wl + s0 + 8);
+                    const T lv[12] = {l0.v[0], l0.v[1], l0.v[2], l0.v[3], l1.v[0], l1.v[1],
+                                      l1.v[2], l1.v[3], l2.v[0], l2.v[1], l2.v[2], l2.v[3]};
+#pragma unroll
+                    for (int j = 4 - G; j < 7 + G; ++j)
+                        d[j] = (hv[j + 1] - hv[j]) + (lv[j + 1] - lv[j]);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) lc[i] = lv[4 + i];
+                } else {
+#pragma unroll
+                    for (int j = 4 - G; j < 7 + G; ++j) d[j] = hv[j + 1] - hv[j];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) lc[i] = T(0);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) wc[i] = hv[4 + i];
+                const T ix = C.inv_dx[AX];
+                if constexpr (SCHEME == HJI_WENO5) {
+                    // Node i: p- on d[i+1..i+5], p+ on d[i+2..i+6] reversed;
+                    // the set d[j..j+4] serves p+ of node j-2 and p- of node j-1.
+                    WenoZ<T> zl = weno_z(d[1], d[2], d[3], d[4], d[5]);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const WenoZ<T> zr = weno_z(d[i + 2], d[i + 3], d[i + 4], d[i + 5], d[i + 6]);
+                        fold(AX, i, weno_fwd(d + i + 1, zl) * ix, weno_rev(d + i + 2, zr) * ix);
+                        zl = zr;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        T pm_, pp_;
+                        one_sided_diffs<T, SCHEME>(d + 4 + i - G, ix, pm_, pp_);
+                        fold(AX, i, pm_, pp_);
+                    }
                 }
             }
-        }
-        if constexpr (NDIM >= 2) {
-            for (int i = threadIdx.x; i < DYH * TX; i += kThreads) {
-                const int r = i / TX, c = i - r * TX;
-                const int s0 = r * SW + c + G;
-                dys[i] = pair_diff(pair_at(s0 + SW), pair_at(s0));
-            }
-        }
-        __syncthreads();
-
-        // 3-5. Each thread updates CELLS nodes of the tile.
-        T dmax = T(0);
-#pragma unroll
-        for (int k = 0; k < CELLS; ++k) {
-            const int ry = ty + k * ROWS_PER_PASS;
-            const int gy = y0 + ry, gx = x0 + tx;
-            if (ry >= TY || gy >= ny || gx >= nx) continue;
-            T pm[NDIM], pp[NDIM];
-            T D[2 * G];
-            const int c0 = (ry + GY) * SW + (tx + G);  // this node in the staged tile
-            const int ci = ry * TX + tx;               // this node among the tile nodes
-#pragma unroll
-            for (int o = 0; o < 2 * G; ++o) D[o] = dxs[ry * DXW + tx + o];
-            one_sided_diffs<T, SCHEME>(D, C.inv_dx[AX], pm[AX], pp[AX]);
+            // y: rows ry .. ry + 2G - 1 of the difference array.
             if constexpr (NDIM >= 2) {
+                T dy[2 * G][4];
 #pragma unroll
-                for (int o = 0; o < 2 * G; ++o) D[o] = dys[(ry + o) * TX + tx];
-                one_sided_diffs<T, SCHEME>(D, C.inv_dx[AY], pm[AY], pp[AY]);
+                for (int o = 0; o < 2 * G; ++o) {
+                    const Q4<T> q = ld4(dys + (ry + o) * TX + 4 * grp);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) dy[o][i] = q.v[i];
+                }
+                const T iy = C.inv_dx[AY];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    T D[2 * G];
+#pragma unroll
+                    for (int o = 0; o < 2 * G; ++o) D[o] = dy[o][i];
+                    T pm_, pp_;
+                    one_sided_diffs<T, SCHEME>(D, iy, pm_, pp_);
+                    fold(AY, i, pm_, pp_);
+                }
             }
-            const long long off = (long long)gy * sy + gx;  // within the plane
+            const long long gidx = tg.base + (long long)gy * sy + gx0;
+            // Slower axes: the stencil lines straight from global memory
+            // (L1/L2), four nodes per load, differenced plane by plane.  The
+            // slow index is the same for the whole tile, so a tile away from
+            // that axis' edges takes the direct path.
 #pragma unroll
             for (int ax = 0; ax < NDIM - 2; ++ax) {
-                // Slower axes: the stencil line straight from global memory
-                // (L1/L2).  The slow index is the same for the whole tile, so
-                // a tile away from that axis' edges takes the strided path.
                 const long long st = C.stride[ax];
-                Pair<T> line[2 * G + 1];
-                if (tg.sidx[ax] >= G && tg.sidx[ax] < C.n[ax] - G) {
+                const int si = tg.sidx[ax], ns = C.n[ax];
+                const long long l0 = gidx - (long long)si * st;  // node 0 of these lines
+                auto plane = [&](int j, Pair<T>* out) {
+                    const long long o = l0 + (long long)j * st;
+                    const Q4<T> h = ldg4(C.win + o);
+                    Q4<T> lo, dd;
+                    if constexpr (INCR) {
+                        lo = ldg4(C.vlo + o);
+                        if (C.din) dd = ldg4(C.din + o);
+                    }
 #pragma unroll
-                    for (int o = -G; o <= G; ++o)
-                        line[o + G] = load_pair<T>(hp, lp, dp, off + o * st);
-                } else {
-                    const long long l0 = off - (long long)tg.sidx[ax] * st;
+                    for (int i = 0; i < 4; ++i) {
+                        out[i].h = h.v[i];
+                        out[i].l = T(0);
+                        if constexpr (INCR) {
+                            out[i].l = lo.v[i];
+                            if (C.din) out[i].l += dd.v[i];
+                        }
+                    }
+                };
+                auto plane_any = [&](int j, Pair<T>* out) {
+                    if (j >= 0 && j < ns) {
+                        plane(j, out);
+                    } else if (C.periodic[ax]) {
+                        j %= ns;
+                        if (j < 0) j += ns;
+                        plane(j, out);
+                    } else {
+                        const bool low = j < 0;
+                        Pair<T> e[4], i1[4];
+                        plane(low ? 0 : ns - 1, e);
+                        plane(low ? 1 : ns - 2, i1);
 #pragma unroll
-                    for (int o = -G; o <= G; ++o)
-                        line[o + G] = line_pair<T>(hp + l0, lp ? lp + l0 : nullptr,
-                                                   dp ? dp + l0 : nullptr, tg.sidx[ax] + o,
-                                                   C.n[ax], st, C.periodic[ax]);
+                        for (int i = 0; i < 4; ++i)
+                            out[i] = extrapolate(e[i], i1[i], low ? -j : j - (ns - 1));
+                    }
+                };
+                const bool inner = si >= G && si < ns - G;
+                T D[2 * G][4];
+                Pair<T> prev[4], cur[4];
+                if (inner) plane(si - G, prev);
+                else plane_any(si - G, prev);
+#pragma unroll
+                for (int o = 1 - G; o <= G; ++o) {
+                    if (inner) plane(si + o, cur);
+                    else plane_any(si + o, cur);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        D[o + G - 1][i] = pair_diff(cur[i], prev[i]);
+                        prev[i] = cur[i];
+                    }
                 }
+                const T is = C.inv_dx[ax];
 #pragma unroll
-                for (int o = 0; o < 2 * G; ++o) D[o] = pair_diff(line[o + 1], line[o]);
-                one_sided_diffs<T, SCHEME>(D, C.inv_dx[ax], pm[ax], pp[ax]);
+                for (int i = 0; i < 4; ++i) {
+                    T Di[2 * G];
+#pragma unroll
+                    for (int o = 0; o < 2 * G; ++o) Di[o] = D[o][i];
+                    T pm_, pp_;
+                    one_sided_diffs<T, SCHEME>(Di, is, pm_, pp_);
+                    fold(ax, i, pm_, pp_);
+                }
             }
-            // Node coordinates and the drift f0(x) = c + A x + terms.
-            int idx[NDIM];
+            // Hamiltonian (Eq. (6)) at pbar.  With the boxes written as
+            // mid +- rad, max_u <G^T p, u> = <G^T p, umid> + sum_j urad_j |(G^T p)_j|
+            // and min_d <E^T p, d> = <E^T p, dmid> - sum_k drad_k |(E^T p)_k|;
+            // the mid parts are folded into the constant drift (cmid), so
+            // H = <p, cmid + A x + terms> + sum_j urad_j |.| - sum_k drad_k |.|.
+            // Along the run only x[AX] changes, by dx per node.
+            {
+                int idx[NDIM];
 #pragma unroll
-            for (int ax = 0; ax < NDIM - 2; ++ax) idx[ax] = tg.sidx[ax];
-            if constexpr (NDIM >= 2) idx[AY] = gy;
-            idx[AX] = gx;
-            T x[NDIM], pbar[NDIM];
+                for (int ax = 0; ax < NDIM - 2; ++ax) idx[ax] = tg.sidx[ax];
+                if constexpr (NDIM >= 2) idx[AY] = gy;
+                idx[AX] = gx0;
+                T x[NDIM];
 #pragma unroll
-            for (int ax = 0; ax < NDIM; ++ax) {
-                x[ax] = C.lo[ax] + T(idx[ax]) * C.dx[ax];
-                pbar[ax] = T(0.5) * (pp[ax] + pm[ax]);
+                for (int ax = 0; ax < NDIM; ++ax) x[ax] = C.lo[ax] + T(idx[ax]) * C.dx[ax];
+#pragma unroll
+                for (int r = 0; r < NDIM; ++r) {
+                    T f0 = C.cmid[r];
+#pragma unroll
+                    for (int j = 0; j < NDIM; ++j) f0 += C.A[r * MAXD + j] * x[j];
+                    const T step = C.A[r * MAXD + AX] * C.dx[AX];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) Lv[i] += pb[i][r] * (f0 + T(i) * step);
+                }
+                for (int tt = 0; tt < C.nterms; ++tt) {
+                    const int ax = C.term_axis[tt], row = C.term_row[tt];
+                    const T* tab = C.table + tt * C.table_stride;
+                    if (ax == AX) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)  // runs may reach past the edge
+                            Lv[i] += pb[i][row] * __ldg(tab + min(gx0 + i, nx - 1));
+                    } else {
+                        const T w = __ldg(tab + idx[ax]);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) Lv[i] += pb[i][row] * w;
+                    }
+                }
+                for (int j = 0; j < C.m; ++j) {
+                    T g[NDIM];
+#pragma unroll
+                    for (int r = 0; r < NDIM; ++r) g[r] = C.G[r * MAXU + j];
+                    const T rad = C.urad[j];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        T s = T(0);
+#pragma unroll
+                        for (int r = 0; r < NDIM; ++r) s += g[r] * pb[i][r];
+                        Lv[i] += rad * fabs(s);
+                    }
+                }
+                for (int j = 0; j < C.q; ++j) {
+                    T e[NDIM];
+#pragma unroll
+                    for (int r = 0; r < NDIM; ++r) e[r] = C.E[r * MAXU + j];
+                    const T rad = C.drad[j];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        T s = T(0);
+#pragma unroll
+                        for (int r = 0; r < NDIM; ++r) s += e[r] * pb[i][r];
+                        Lv[i] -= rad * fabs(s);
+                    }
+                }
             }
-            T h = T(0);
-#pragma unroll
-            for (int i = 0; i < NDIM; ++i) {
-                T fi = C.c[i];
-#pragma unroll
-                for (int j = 0; j < NDIM; ++j) fi += C.A[i * MAXD + j] * x[j];
-                h += pbar[i] * fi;
-            }
-            for (int tt = 0; tt < C.nterms; ++tt) {
-                const int ax = C.term_axis[tt];
-                h += pbar[C.term_row[tt]] * __ldg(C.table + tt * C.table_stride + idx[ax]);
-            }
-            // max_u <G^T p, u> and min_d <E^T p, d> over the boxes (Eq. (6)).
-            for (int j = 0; j < C.m; ++j) {
-                T s = T(0);
-#pragma unroll
-                for (int i = 0; i < NDIM; ++i) s += C.G[i * MAXU + j] * pbar[i];
-                h += fmax(s * C.ulo[j], s * C.uhi[j]);
-            }
-            for (int j = 0; j < C.q; ++j) {
-                T r = T(0);
-#pragma unroll
-                for (int i = 0; i < NDIM; ++i) r += C.E[i * MAXU + j] * pbar[i];
-                h += fmin(r * C.dlo[j], r * C.dhi[j]);
-            }
-            // Lax-Friedrichs: L = H(pbar) + sum alpha_a (p+ - p-) / 2.
-            T Lv = h;
-#pragma unroll
-            for (int ax = 0; ax < NDIM; ++ax) Lv += C.half_alpha[ax] * (pp[ax] - pm[ax]);
-            // Runge-Kutta stage combination.
-            const long long gidx = tg.base + off;
+            // Runge-Kutta stage combination and stores (four nodes at once
+            // when the whole run lies inside the grid).
+            const int nvalid = min(4, nx - gx0);
+            const T dt = C.dt;
             if constexpr (INCR) {
-                const T dc = has_d ? rd[c0] : T(0);
-                const T inc = cE * (dc + C.dt * Lv);
+                T dc[4] = {T(0), T(0), T(0), T(0)};
+                if (has_d) {
+                    const Q4<T> q = ld4(wd + s0 + 4);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) dc[i] = q.v[i];
+                }
+                T inc[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) inc[i] = cE * (dc[i] + dt * Lv[i]);
                 if constexpr (!LAST) {
-                    C.wout[gidx] = inc;
+                    if (nvalid == 4) st4(C.wout + gidx, inc);
+                    else
+                        for (int i = 0; i < nvalid; ++i) C.wout[gidx + i] = inc[i];
                 } else {
                     // V^n + inc as an unevaluated float pair (error-free
                     // two-sum), then min(., l) of Eq. (7)-(8).
-                    const T hi = rh[c0];
-                    const T lo = has_d ? C.vlo[gidx] : rl[c0];
-                    const T sl = lo + inc;
-                    T nh = hi + sl;
-                    const T bb = nh - hi;
-                    T nl = (hi - (nh - bb)) + (sl - bb);
-                    const T lv = sm[L::LT + buf * NI + ci];
-                    if (nh > lv || (nh == lv && nl > T(0))) {
-                        nh = lv;
-                        nl = T(0);
+                    T lo[4];
+                    if (has_d) {
+                        const Q4<T> q = ldg4(C.vlo + gidx);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) lo[i] = q.v[i];
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) lo[i] = lc[i];
                     }
-                    const T ch = fabs((nh - hi) + (nl - lo));
-                    dmax = (ch > dmax || ch != ch) ? ch : dmax;
-                    C.wout[gidx] = nh;
-                    C.vlo[gidx] = nl;
+                    const Q4<T> lt =
+                        ld4(reinterpret_cast<const T*>(sb + L::LT(buf)) + ry * TX + 4 * grp);
+                    T nh[4], nl[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const T hi = wc[i];
+                        const T sl = lo[i] + inc[i];
+                        T vh = hi + sl;
+                        const T bb = vh - hi;
+                        T vl = (hi - (vh - bb)) + (sl - bb);
+                        const T lv = lt.v[i];
+                        if (vh > lv || (vh == lv && vl > T(0))) {
+                            vh = lv;
+                            vl = T(0);
+                        }
+                        nh[i] = vh;
+                        nl[i] = vl;
+                        if (i < nvalid) {
+                            const T ch = fabs((vh - hi) + (vl - lo[i]));
+                            dmax = (ch > dmax || ch != ch) ? ch : dmax;
+                        }
+                    }
+                    if (nvalid == 4) {
+                        st4(C.wout + gidx, nh);
+                        st4(C.vlo_out + gidx, nl);
+                    } else {
+                        for (int i = 0; i < nvalid; ++i) {
+                            C.wout[gidx + i] = nh[i];
+                            C.vlo_out[gidx + i] = nl[i];
+                        }
+                    }
                 }
             } else {
-                const T wc = rh[c0];
-                const T eul = wc + C.dt * Lv;
-                T out;
-                T vn = wc;
+                T vn[4], out[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) vn[i] = wc[i];
                 if (reads_v) {
-                    if constexpr (LAST) vn = sm[L::VN + buf * NI + ci];
-                    else vn = __ldg(C.vcur + gidx);
-                    out = cV * vn + cE * eul;
-                } else {
-                    out = eul;
+                    Q4<T> q;
+                    if constexpr (LAST)
+                        q = ld4(reinterpret_cast<const T*>(sb + L::VN(buf)) + ry * TX + 4 * grp);
+                    else
+                        q = ldg4(C.vcur + gidx);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) vn[i] = q.v[i];
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const T eul = wc[i] + dt * Lv[i];
+                    out[i] = reads_v ? cV * vn[i] + cE * eul : eul;
                 }
                 if constexpr (LAST) {
-                    const T lv = sm[L::LT + buf * NI + ci];
-                    out = fmin(out, lv);
-                    const T ch = fabs(out - vn);
-                    dmax = (ch > dmax || ch != ch) ? ch : dmax;
+                    const Q4<T> lt =
+                        ld4(reinterpret_cast<const T*>(sb + L::LT(buf)) + ry * TX + 4 * grp);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        out[i] = fmin(out[i], lt.v[i]);
+                        if (i < nvalid) {
+                            const T ch = fabs(out[i] - vn[i]);
+                            dmax = (ch > dmax || ch != ch) ? ch : dmax;
+                        }
+                    }
                 }
-                C.wout[gidx] = out;
+                if (nvalid == 4) st4(C.wout + gidx, out);
+                else
+                    for (int i = 0; i < nvalid; ++i) C.wout[gidx + i] = out[i];
             }
         }
 
@@ -772,7 +1137,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 5 : 3)
             __syncthreads();
             if (threadIdx.x == 0) {
                 T mt = red[0];
-                for (int w = 1; w < kThreads / 32; ++w) mt = (red[w] > mt || red[w] != red[w]) ? red[w] : mt;
+                for (int w = 1; w < kThreads / 32; ++w)
+                    mt = (red[w] > mt || red[w] != red[w]) ? red[w] : mt;
                 const double m = static_cast<double>(mt);
                 const InstDesc& D = a.insts[inst];
                 InstState* st = D.state;
@@ -787,7 +1153,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 5 : 3)
         t = tn;
         issued = pref;
     }
-    cp_async_wait<0>();
 }
 
 template <typename T, int NDIM, int SCHEME, bool LAST, int V>

@@ -102,3 +102,25 @@ def test_tile_shapes_give_identical_results_and_autotune(hji_lib, prec, scheme, 
     st = g.solve(l, **opts)
     assert st["steps"] == steps[0] and np.array_equal(g.value(), vals[0])
     g.close()
+
+
+def test_f32_last_stage_has_no_read_write_overlap(hji_lib):
+    """On a grid with several waves of tiles per stage (1001^2: about 2000
+    tiles for 760 resident CTAs), a tile's last stage must not see the low
+    words its neighbours already wrote for V^{n+1}: the march is then
+    independent of the order in which tiles run, so every tile shape gives
+    the same bits."""
+    import torch
+    assert torch.cuda.is_available()
+    gd, dyn, l = W.di_config(1001, dmax=0.2)
+    l = l.astype(np.float32)
+    g = hji_lib.Grid(gd, "f32")
+    g.set_dynamics(dyn)
+    vals = []
+    for v in range(1, hji_lib.HJI_TILE_VARIANTS + 1):
+        st = g.solve(l, scheme="weno5", rk=3, cfl=0.5, tol=0.0, max_steps=60, tile_variant=v)
+        assert st["steps"] == 60
+        vals.append(g.value())
+    for V in vals[1:]:
+        assert np.array_equal(V, vals[0])
+    g.close()

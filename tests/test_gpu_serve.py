@@ -69,7 +69,8 @@ def test_budget_admission_and_resident_warm_start(hji_lib):
     insts = W.batch_instances(count=4, seed=5, side=(41, 41))
     grids = _grids(hji, insts, "f64")
     ls = [W.instance_target(i) for i in insts]
-    per_grid = 41 * 41 * 8 * 5 + 8 * 41 * 8  # V x2, l, W1, W2 + term table
+    # V x2, l, W1, W2 (rows padded to a multiple of 8 nodes: 41 -> 48) + term table
+    per_grid = 41 * 48 * 8 * 5 + 8 * 41 * 8
     eng = hji.Engine(2, "f64", max_slots=8, budget_bytes=2 * per_grid + 100, **OPTS)
     for i, (g, l) in enumerate(zip(grids, ls)):
         eng.submit(g, l, tag=i)
