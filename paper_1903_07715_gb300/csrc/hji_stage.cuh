@@ -585,7 +585,7 @@ struct TileWalk {
 };
 
 template <typename T, int NDIM, int SCHEME, bool LAST, int V>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 3) : 2)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2) : 2)
     stage_kernel(const StageArgs a) {
     using L = StageSmem<T, NDIM, SCHEME, LAST, V>;
     constexpr int G = L::G, TY = L::TY, TX = L::TX, GROUPS = L::GROUPS;
@@ -685,29 +685,28 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 3)
             continue;
         }
         const TileGeo tg = tile_geo<T, NDIM, TY, TX>(C, local);
-        // Prefetch the next tile of the walk while this one is computed.
         const int tn = walk.next();
         const bool pref = tn >= 0 && static_cast<int>(a.tiles[tn] >> 48) == inst;
-        if (threadIdx.x == 0) {
-            if (!issued) issue(tg, buf);
-            if (pref)
-                issue(tile_geo<T, NDIM, TY, TX>(C, static_cast<int>(a.tiles[tn] & 0xFFFFFFFFFFFFull)),
-                      buf ^ 1);
-        }
+        // Buffer `buf` was last read two tiles ago, which every thread
+        // finished before the barrier below of the previous tile.
+        if (threadIdx.x == 0 && !issued) issue(tg, buf);
         const bool ok = mbar_wait_bounded(bar0 + 8u * buf, (phase >> buf) & 1u);
         phase ^= 1u << buf;
+        // After this barrier every thread is done with the previous tile, so
+        // its buffer (buf ^ 1) and the y-differences may be overwritten.
         if (__syncthreads_or(!ok)) {
-            // A copy never arrived: record it, stop the instance, give the
-            // prefetched copy (if any) a bounded wait and leave.
+            // A copy never arrived: record it, stop the instance and leave.
             if (threadIdx.x == 0) {
                 const InstDesc& D = a.insts[inst];
                 atomicExch(&D.state->status, 4);
                 stop_instance(D);
-                if (pref) mbar_wait_bounded(bar0 + 8u * (buf ^ 1), (phase >> (buf ^ 1)) & 1u);
             }
-            __syncthreads();
             return;
         }
+        // Prefetch the next tile of the walk while this one is computed.
+        if (threadIdx.x == 0 && pref)
+            issue(tile_geo<T, NDIM, TY, TX>(C, static_cast<int>(a.tiles[tn] & 0xFFFFFFFFFFFFull)),
+                  buf ^ 1);
 
         const int nx = C.n[AX];
         const int ny = NDIM >= 2 ? C.n[AY] : 1;
@@ -830,7 +829,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 3)
             };
             // x: the window row of this run, columns 4 grp .. 4 grp + 11.
             const int s0 = (ry + GY) * SWX + 4 * grp;
-            T wc[4], lc[4];  // the run's own stencil input (high, low)
             {
                 T d[11];
                 const Q4<T> h0 = ld4(wh + s0), h1 = ld4(wh + s0 + 4), h2 = ld4(wh + s0 + 8);
@@ -843,16 +841,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 3)
 #pragma unroll
                     for (int j = 4 - G; j < 7 + G; ++j)
                         d[j] = (hv[j + 1] - hv[j]) + (lv[j + 1] - lv[j]);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) lc[i] = lv[4 + i];
                 } else {
 #pragma unroll
                     for (int j = 4 - G; j < 7 + G; ++j) d[j] = hv[j + 1] - hv[j];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) lc[i] = T(0);
                 }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) wc[i] = hv[4 + i];
                 const T ix = C.inv_dx[AX];
                 if constexpr (SCHEME == HJI_WENO5) {
                     // Node i: p- on d[i+1..i+5], p+ on d[i+2..i+6] reversed;
@@ -991,14 +983,25 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 3)
                 for (int tt = 0; tt < C.nterms; ++tt) {
                     const int ax = C.term_axis[tt], row = C.term_row[tt];
                     const T* tab = C.table + tt * C.table_stride;
+                    // pb[i][row] by selects: a runtime index would put pb in local memory.
+                    T pr[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        pr[i] = pb[i][0];
+#pragma unroll
+                        for (int r = 1; r < NDIM; ++r) pr[i] = row == r ? pb[i][r] : pr[i];
+                    }
+                    int ia = idx[0];
+#pragma unroll
+                    for (int r = 1; r < NDIM; ++r) ia = ax == r ? idx[r] : ia;
                     if (ax == AX) {
 #pragma unroll
                         for (int i = 0; i < 4; ++i)  // runs may reach past the edge
-                            Lv[i] += pb[i][row] * __ldg(tab + min(gx0 + i, nx - 1));
+                            Lv[i] += pr[i] * __ldg(tab + min(gx0 + i, nx - 1));
                     } else {
-                        const T w = __ldg(tab + idx[ax]);
+                        const T w = __ldg(tab + ia);
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) Lv[i] += pb[i][row] * w;
+                        for (int i = 0; i < 4; ++i) Lv[i] += pr[i] * w;
                     }
                 }
                 for (int j = 0; j < C.m; ++j) {
@@ -1032,6 +1035,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 3)
             // when the whole run lies inside the grid).
             const int nvalid = min(4, nx - gx0);
             const T dt = C.dt;
+            // The run's own stencil input (high word), read again here rather
+            // than kept in registers through the derivatives.
+            T wc[4];
+            {
+                const Q4<T> q = ld4(wh + s0 + 4);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) wc[i] = q.v[i];
+            }
             if constexpr (INCR) {
                 T dc[4] = {T(0), T(0), T(0), T(0)};
                 if (has_d) {
@@ -1049,14 +1060,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 3)
                 } else {
                     // V^n + inc as an unevaluated float pair (error-free
                     // two-sum), then min(., l) of Eq. (7)-(8).
+                    // The low word of V^n: the window's low words hold it
+                    // unless the stage increment was folded into them.
                     T lo[4];
-                    if (has_d) {
-                        const Q4<T> q = ldg4(C.vlo + gidx);
+                    {
+                        const Q4<T> q = has_d ? ldg4(C.vlo + gidx) : ld4(wl + s0 + 4);
 #pragma unroll
                         for (int i = 0; i < 4; ++i) lo[i] = q.v[i];
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) lo[i] = lc[i];
                     }
                     const Q4<T> lt =
                         ld4(reinterpret_cast<const T*>(sb + L::LT(buf)) + ry * TX + 4 * grp);
@@ -1148,7 +1158,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 3)
                 if (prev + 1 == static_cast<unsigned int>(C.ntiles)) finish_step(D);
             }
         }
-        __syncthreads();  // buffer `buf` is refilled by the prefetch after next
         buf ^= 1;
         t = tn;
         issued = pref;
