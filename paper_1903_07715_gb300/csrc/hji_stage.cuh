@@ -54,23 +54,30 @@ __device__ __forceinline__ T smaller_mag(T a, T b) {
 // eps = 1e-6 max(v^2) + tiny as in the textbook form (the relative part is
 // scale free, so undivided differences give the divided-difference weights).
 //
-// The weights split into a part that depends only on the set {v1..v5} and
-// its orientation.  With S_A, S_B, S_C the smoothness indicators of
-// (v1,v2,v3), (v2,v3,v4), (v3,v4,v5) and b = S + eps, the forward derivative
-// weighs d = (0.1, 0.6, 0.3) against (b_A, b_B, b_C); the derivative on the
-// reversed differences (v5..v1) has the same three indicators in reverse
-// order (the indicator formula is symmetric under reversing its triple), so
-// it weighs d against (b_C, b_B, b_A).  Neighbouring nodes of a line use the
-// same five differences for p+ of the left node and p- of the right node,
-// which therefore share one WenoZ.
+// The textbook evaluation is rewritten on differences of the v's, which
+// neighbouring stencils share.  With e_k = v_k - v_{k+1} (k = 1..4):
+//   smoothness indicators S_A = 13/12 (e1 - e2)^2 + 1/4 (e1 - 3 e2)^2,
+//                         S_B = 13/12 (e2 - e3)^2 + 1/4 (e2 + e3)^2,
+//                         S_C = 13/12 (e3 - e4)^2 + 1/4 (3 e3 - e4)^2
+//   (the usual (v1 - 2v2 + v3), (v1 - 4v2 + 3v3), ... written in e's);
+//   candidate polynomials: phi_1 - phi_2 = t1 / 3 and phi_3 - phi_2 = t3 / 6
+//   with the third differences t1 = e1 - 2e2 + e3, t3 = e2 - 2e3 + e4, so
+//   sum_k w_k phi_k = phi_2 + (alpha_1 t1 / 3 + alpha_3 t3 / 6) / sum alpha
+//   (alpha_k = d_k / (S_k + eps)^2, d = (0.1, 0.6, 0.3)); and
+//   max v^2 = (max |v|)^2.
+// The derivative on the reversed differences (v5..v1) has the same three
+// indicators in reverse order (the indicator formula is symmetric under
+// reversing its triple) and third differences (-t3, -t1), so one set of
+// five differences serves p+ of one node and p- of its neighbour.
 //
 // WenoZ holds z1..z3 with forward weights (0.1 z1, 0.6 z2, 0.3 z3) and
 // reversed weights (0.1 z3, 0.6 z2, 0.3 z1), normalised by their sum:
-//   FP64: z = ((b_B b_C)^2, (b_A b_C)^2, (b_A b_B)^2), the weights
-//         d_k / b_k^2 times the common factor (b_A b_B b_C)^2: one division
-//         (tiny = 1e-60 keeps the fourth powers above the FP64 range floor);
+//   FP64: z = ((b_B b_C)^2, (b_A b_C)^2, (b_A b_B)^2), b = S + eps: the
+//         weights d_k / b_k^2 times the common factor (b_A b_B b_C)^2, one
+//         division (tiny = 1e-60 keeps the fourth powers above the FP64
+//         range floor);
 //   FP32: z = (r_A^2, r_B^2, r_C^2), r = 1/b by the fast reciprocal; tiny =
-//         1e-18 keeps the sum below 2^126 (the range of the fast division)
+//         1e-18 keeps the sums below 2^126 (the range of the fast division)
 //         while exceeding 1e-6 max(v^2) only where every |v| < 1e-6 (flat
 //         data, where the weights do not matter).
 template <typename T>
@@ -78,18 +85,18 @@ struct WenoZ {
     T z1, z2, z3;
 };
 
+// Weights of a set from its first differences e1..e4 and m = max |v_k|.
 template <typename T>
-__device__ __forceinline__ WenoZ<T> weno_z(T v1, T v2, T v3, T v4, T v5) {
-    const T a = v1 - T(2) * v2 + v3, b = v1 - T(4) * v2 + T(3) * v3;
-    const T c = v2 - T(2) * v3 + v4, d = v2 - v4;
-    const T e = v3 - T(2) * v4 + v5, f = T(3) * v3 - T(4) * v4 + v5;
-    const T sA = T(13.0 / 12.0) * a * a + T(0.25) * b * b;
-    const T sB = T(13.0 / 12.0) * c * c + T(0.25) * d * d;
-    const T sC = T(13.0 / 12.0) * e * e + T(0.25) * f * f;
-    const T vm = fmax(fmax(fmax(v1 * v1, v2 * v2), fmax(v3 * v3, v4 * v4)), v5 * v5);
+__device__ __forceinline__ WenoZ<T> weno_z(T e1, T e2, T e3, T e4, T m) {
+    const T pA = e1 - e2, qA = e1 - T(3) * e2;
+    const T pB = e2 - e3, qB = e2 + e3;
+    const T pC = e3 - e4, qC = T(3) * e3 - e4;
+    const T sA = T(13.0 / 12.0) * pA * pA + T(0.25) * qA * qA;
+    const T sB = T(13.0 / 12.0) * pB * pB + T(0.25) * qB * qB;
+    const T sC = T(13.0 / 12.0) * pC * pC + T(0.25) * qC * qC;
     WenoZ<T> z;
     if constexpr (sizeof(T) == 4) {
-        const float eps = 1e-6f * vm + 1e-18f;
+        const float eps = 1e-6f * (m * m) + 1e-18f;
         const float rA = __fdividef(1.0f, sA + eps);
         const float rB = __fdividef(1.0f, sB + eps);
         const float rC = __fdividef(1.0f, sC + eps);
@@ -97,7 +104,7 @@ __device__ __forceinline__ WenoZ<T> weno_z(T v1, T v2, T v3, T v4, T v5) {
         z.z2 = rB * rB;
         z.z3 = rC * rC;
     } else {
-        const T eps = T(1e-6) * vm + Num<T>::weno_tiny();
+        const T eps = T(1e-6) * (m * m) + Num<T>::weno_tiny();
         const T bA = sA + eps, bB = sB + eps, bC = sC + eps;
         const T pBC = bB * bC, pAC = bA * bC, pAB = bA * bB;
         z.z1 = pBC * pBC;
@@ -107,26 +114,42 @@ __device__ __forceinline__ WenoZ<T> weno_z(T v1, T v2, T v3, T v4, T v5) {
     return z;
 }
 
-// The WENO5 derivative on v1..v5 with weights (0.1 w1, 0.6 w2, 0.3 w3).
 template <typename T>
-__device__ __forceinline__ T weno_combine(T v1, T v2, T v3, T v4, T v5, T w1, T w2, T w3) {
-    const T phi1 = v1 * T(1.0 / 3.0) - v2 * T(7.0 / 6.0) + v3 * T(11.0 / 6.0);
-    const T phi2 = -v2 * T(1.0 / 6.0) + v3 * T(5.0 / 6.0) + v4 * T(1.0 / 3.0);
-    const T phi3 = v3 * T(1.0 / 3.0) + v4 * T(5.0 / 6.0) - v5 * T(1.0 / 6.0);
-    const T a1 = T(0.1) * w1, a2 = T(0.6) * w2, a3 = T(0.3) * w3;
-    const T num = a1 * phi1 + a2 * phi2 + a3 * phi3;
-    if constexpr (sizeof(T) == 4) return __fdividef(num, a1 + a2 + a3);
-    else return num / (a1 + a2 + a3);
+__device__ __forceinline__ T ratio(T num, T den) {
+    if constexpr (sizeof(T) == 4) return __fdividef(num, den);
+    else return num / den;
 }
 
-// p- on the forward set v[0..4]; p+ on the reversed set v[4..0].
+// p- on the forward set v1..v5 (phi_2 = -v2/6 + 5 v3/6 + v4/3).
 template <typename T>
-__device__ __forceinline__ T weno_fwd(const T* v, const WenoZ<T>& z) {
-    return weno_combine(v[0], v[1], v[2], v[3], v[4], z.z1, z.z2, z.z3);
+__device__ __forceinline__ T weno_fwd(T v2, T v3, T v4, T t1, T t3, const WenoZ<T>& z) {
+    const T phi2 = v3 * T(5.0 / 6.0) - v2 * T(1.0 / 6.0) + v4 * T(1.0 / 3.0);
+    const T num = z.z1 * T(0.1 / 3.0) * t1 + z.z3 * T(0.3 / 6.0) * t3;
+    const T den = T(0.1) * z.z1 + T(0.6) * z.z2 + T(0.3) * z.z3;
+    return phi2 + ratio(num, den);
 }
+// p+ on the same set read in reverse (v5..v1).
 template <typename T>
-__device__ __forceinline__ T weno_rev(const T* v, const WenoZ<T>& z) {
-    return weno_combine(v[4], v[3], v[2], v[1], v[0], z.z3, z.z2, z.z1);
+__device__ __forceinline__ T weno_rev(T v2, T v3, T v4, T t1, T t3, const WenoZ<T>& z) {
+    const T phi2 = v3 * T(5.0 / 6.0) - v4 * T(1.0 / 6.0) + v2 * T(1.0 / 3.0);
+    const T num = z.z3 * T(0.1 / 3.0) * t3 + z.z1 * T(0.3 / 6.0) * t1;
+    const T den = T(0.1) * z.z3 + T(0.6) * z.z2 + T(0.3) * z.z1;
+    return phi2 - ratio(num, den);
+}
+
+// WENO5 (p-, p+) from the six differences D[0..5] of one node.
+template <typename T>
+__device__ __forceinline__ void weno5_pair(const T* D, T inv_dx, T& pm, T& pp) {
+    T E[5], Tt[3];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) E[k] = D[k] - D[k + 1];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Tt[k] = E[k] - T(2) * E[k + 1] + E[k + 2];
+    const T m14 = fmax(fmax(fabs(D[1]), fabs(D[2])), fmax(fabs(D[3]), fabs(D[4])));
+    const WenoZ<T> za = weno_z(E[0], E[1], E[2], E[3], fmax(m14, fabs(D[0])));
+    const WenoZ<T> zb = weno_z(E[1], E[2], E[3], E[4], fmax(m14, fabs(D[5])));
+    pm = weno_fwd(D[1], D[2], D[3], Tt[0], Tt[1], za) * inv_dx;
+    pp = weno_rev(D[2], D[3], D[4], Tt[1], Tt[2], zb) * inv_dx;
 }
 
 // (p-, p+) at node c from the 2G undivided differences D[k] = W[k+1] - W[k]
@@ -142,8 +165,7 @@ __device__ __forceinline__ void one_sided_diffs(const T* D, T inv_dx, T& pm, T& 
         pm = (D[1] + T(0.5) * smaller_mag(Sm, S0)) * inv_dx;
         pp = (D[2] - T(0.5) * smaller_mag(S0, Sp)) * inv_dx;
     } else {
-        pm = weno_fwd(D, weno_z(D[0], D[1], D[2], D[3], D[4])) * inv_dx;
-        pp = weno_rev(D + 1, weno_z(D[1], D[2], D[3], D[4], D[5])) * inv_dx;
+        weno5_pair(D, inv_dx, pm, pp);
     }
 }
 
@@ -847,13 +869,27 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
                 }
                 const T ix = C.inv_dx[AX];
                 if constexpr (SCHEME == HJI_WENO5) {
-                    // Node i: p- on d[i+1..i+5], p+ on d[i+2..i+6] reversed;
-                    // the set d[j..j+4] serves p+ of node j-2 and p- of node j-1.
-                    WenoZ<T> zl = weno_z(d[1], d[2], d[3], d[4], d[5]);
+                    // Node i: p- on the set d[i+1..i+5], p+ on d[i+2..i+6]
+                    // reversed; the set d[j..j+4] serves p+ of node j-2 and
+                    // p- of node j-1, with first differences E[j..j+3] and
+                    // third differences Tt[j], Tt[j+1] for both.
+                    T E[9], Tt[8], a[10];
+#pragma unroll
+                    for (int j = 1; j <= 8; ++j) E[j] = d[j] - d[j + 1];
+#pragma unroll
+                    for (int j = 1; j <= 7; ++j) Tt[j] = E[j] - T(2) * E[j + 1] + E[j + 2];
+#pragma unroll
+                    for (int j = 1; j <= 9; ++j) a[j] = fabs(d[j]);
+                    auto set_z = [&](int j) {
+                        const T m = fmax(fmax(fmax(a[j], a[j + 1]), fmax(a[j + 2], a[j + 3])), a[j + 4]);
+                        return weno_z(E[j], E[j + 1], E[j + 2], E[j + 3], m);
+                    };
+                    WenoZ<T> zl = set_z(1);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const WenoZ<T> zr = weno_z(d[i + 2], d[i + 3], d[i + 4], d[i + 5], d[i + 6]);
-                        fold(AX, i, weno_fwd(d + i + 1, zl) * ix, weno_rev(d + i + 2, zr) * ix);
+                        const WenoZ<T> zr = set_z(i + 2);
+                        fold(AX, i, weno_fwd(d[i + 2], d[i + 3], d[i + 4], Tt[i + 1], Tt[i + 2], zl) * ix,
+                             weno_rev(d[i + 3], d[i + 4], d[i + 5], Tt[i + 2], Tt[i + 3], zr) * ix);
                         zl = zr;
                     }
                 } else {
