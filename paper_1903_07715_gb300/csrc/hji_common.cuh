@@ -107,22 +107,25 @@ __host__ __device__ inline unsigned long long make_tile(int inst, long long loca
 }
 
 // Tile shapes.  A thread updates one run of four consecutive nodes of the
-// fastest axis, so a tile has 4 x 256 nodes.  1-D tiles are 248 nodes (the
-// staged window of 256 is the largest TMA box; threads past the 62nd idle).
-// N-D tiles cover the two fastest axes at a fixed index of the slower axes
-// (which are read from global memory / L2 directly): variant 0 is 32 x 32
-// nodes (rows x columns, the least halo per node), and 2-D grids also have
-// variant 1 (16 x 64) and variant 2 (64 x 16), which fit narrow or short
-// grids with less padding; the autotuner picks per problem class.  Every
-// shape runs the same per-node arithmetic, so results do not depend on it.
+// fastest axis.  1-D tiles are 248 nodes (the staged window of 256 is the
+// largest TMA box; threads past the 62nd idle).  N-D tiles cover the two
+// fastest axes at a fixed index of the slower axes (which are read from
+// global memory / L2 directly): TY rows x TX columns with (TY + 1) x TX / 4
+// = 256, so that the TY + 1 sets of five y-differences a WENO5 tile column
+// needs are one per thread (the TY x TX / 4 runs of the tile use all but
+// one row of threads).  Variant 0 is 31 x 32 nodes (the least halo per
+// node), and 2-D grids also have variant 1 (15 x 64) and variant 2
+// (63 x 16), which fit narrow or short grids with less padding; the
+// autotuner picks per problem class.  Every shape runs the same per-node
+// arithmetic, so results do not depend on it.
 constexpr int kTileVariants = 3;
 constexpr int kPitchAlign = 8;  // elements
 template <int NDIM, int V = 0>
 struct TileShape {
-    static constexpr int TY = (NDIM == 1) ? 1 : (V == 1 ? 16 : (V == 2 ? 64 : 32));
+    static constexpr int TY = (NDIM == 1) ? 1 : (V == 1 ? 15 : (V == 2 ? 63 : 31));
     static constexpr int TX = (NDIM == 1) ? 248 : (V == 1 ? 64 : (V == 2 ? 16 : 32));
     static constexpr int GROUPS = TX / 4;  // 4-node runs per row
-    static_assert(NDIM == 1 || TY * GROUPS == kThreads, "one run per thread");
+    static_assert(NDIM == 1 || (TY + 1) * GROUPS == kThreads, "one y-set per thread");
 };
 inline void tile_dims(int ndim, int variant, int& ty, int& tx) {
     if (ndim == 1) {
@@ -131,7 +134,7 @@ inline void tile_dims(int ndim, int variant, int& ty, int& tx) {
         return;
     }
     const int v = ndim == 2 ? variant : 0;
-    ty = v == 1 ? 16 : (v == 2 ? 64 : 32);
+    ty = v == 1 ? 15 : (v == 2 ? 63 : 31);
     tx = v == 1 ? 64 : (v == 2 ? 16 : 32);
 }
 inline long long pitch_of(long long nx) { return (nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign; }

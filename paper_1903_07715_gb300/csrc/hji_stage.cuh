@@ -513,7 +513,7 @@ __device__ __forceinline__ void tma_load(unsigned dst, const CUtensorMap* m, con
 // Dynamic shared-memory layout of one stage kernel: two buffers, each with
 // the staged window (high words; FP32 also low words and stage increments)
 // and, for the last stage, l (and, FP64, V^n) at the tile nodes; then the
-// y-differences of the current tile.  Window row r, column c holds the node
+// y-differences of the current tile and, for WENO5, its y-derivatives.  Window row r, column c holds the node
 // (y0 - GY + r, x0 - 4 + c): columns start 4 left of the tile so that every
 // copy starts on a 16-byte boundary.
 constexpr int round128(int b) { return (b + 127) / 128 * 128; }
@@ -536,7 +536,12 @@ struct StageSmem {
     static constexpr int BUFB = NF * WINB + NN * NODEB;
     static constexpr int DYS = 2 * BUFB;
     static constexpr int DYSB = NDIM >= 2 ? round128((SH - 1) * TX * (int)sizeof(T)) : 0;
-    static constexpr int BYTES = DYS + DYSB + 128;  // + alignment slack
+    // WENO5 y-derivatives p-, p+ of the tile nodes, from the set pass.
+    static constexpr bool YSETS = NDIM >= 2 && SCHEME == HJI_WENO5;
+    static constexpr int PMY = DYS + DYSB;
+    static constexpr int PYB = YSETS ? round128(NODES * (int)sizeof(T)) : 0;
+    static constexpr int PPY = PMY + PYB;
+    static constexpr int BYTES = PPY + PYB + 128;  // + alignment slack
     static __host__ __device__ constexpr int H(int b) { return b * BUFB; }
     static __host__ __device__ constexpr int LO(int b) { return b * BUFB + WINB; }
     static __host__ __device__ constexpr int DD(int b) { return b * BUFB + 2 * WINB; }
@@ -636,10 +641,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
     }
     const bool reads_v = a.reads_v != 0;
     const bool has_d = INCR && a.stage_in != 0;
-    // Thread -> (tile row, run of four nodes).
+    // Thread -> (tile row, run of four nodes); for NDIM >= 2 the last row of
+    // threads has no run (it takes a y-set in the WENO5 set pass).
     const int grp = threadIdx.x % GROUPS;
     const int ry = threadIdx.x / GROUPS;
-    const bool thread_works = NDIM >= 2 || threadIdx.x < GROUPS;
+    const bool thread_works = NDIM >= 2 ? ry < TY : threadIdx.x < GROUPS;
 
     const unsigned bar0 = smem_addr(&bars[0]);
     if (threadIdx.x == 0) {
@@ -834,6 +840,37 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
             }
             __syncthreads();
         }
+        // 2b. WENO5 along y by sets: set j of a column is its differences
+        //     j .. j+4, which give p- of tile row j (forward) and p+ of tile
+        //     row j-1 (reversed), so each set is evaluated once.  Thread
+        //     (j, g4) takes set j of columns 4 g4 .. 4 g4 + 3.
+        if constexpr (L::YSETS) {
+            const int j = threadIdx.x / GROUPS, g4 = threadIdx.x - j * GROUPS;
+            T q[5][4];
+#pragma unroll
+            for (int o = 0; o < 5; ++o) {
+                const Q4<T> v = ld4(dys + (j + o) * TX + 4 * g4);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) q[o][c] = v.v[c];
+            }
+            const T iy = C.inv_dx[AY];
+            T pmv[4], ppv[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                T e[4];
+#pragma unroll
+                for (int o = 0; o < 4; ++o) e[o] = q[o][c] - q[o + 1][c];
+                const T t1 = e[0] - T(2) * e[1] + e[2], t3 = e[1] - T(2) * e[2] + e[3];
+                const T m = fmax(fmax(fmax(fabs(q[0][c]), fabs(q[1][c])), fmax(fabs(q[2][c]), fabs(q[3][c]))),
+                                 fabs(q[4][c]));
+                const WenoZ<T> z = weno_z(e[0], e[1], e[2], e[3], m);
+                pmv[c] = weno_fwd(q[1][c], q[2][c], q[3][c], t1, t3, z) * iy;
+                ppv[c] = weno_rev(q[1][c], q[2][c], q[3][c], t1, t3, z) * iy;
+            }
+            if (j < TY) st4(reinterpret_cast<T*>(sb + L::PMY) + j * TX + 4 * g4, pmv);
+            if (j > 0) st4(reinterpret_cast<T*>(sb + L::PPY) + (j - 1) * TX + 4 * g4, ppv);
+            __syncthreads();
+        }
 
         // 3-5. Each thread updates a run of 4 nodes of the tile.  The
         // derivatives of each axis are folded at once into the
@@ -901,8 +938,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
                     }
                 }
             }
-            // y: rows ry .. ry + 2G - 1 of the difference array.
-            if constexpr (NDIM >= 2) {
+            // y: WENO5 from the set pass; ENO from rows ry .. ry + 2G - 1 of
+            // the difference array.
+            if constexpr (L::YSETS) {
+                const Q4<T> m4 = ld4(reinterpret_cast<const T*>(sb + L::PMY) + ry * TX + 4 * grp);
+                const Q4<T> p4 = ld4(reinterpret_cast<const T*>(sb + L::PPY) + ry * TX + 4 * grp);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) fold(AY, i, m4.v[i], p4.v[i]);
+            } else if constexpr (NDIM >= 2) {
                 T dy[2 * G][4];
 #pragma unroll
                 for (int o = 0; o < 2 * G; ++o) {

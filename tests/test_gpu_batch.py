@@ -105,8 +105,8 @@ def test_tile_shapes_give_identical_results_and_autotune(hji_lib, prec, scheme, 
 
 
 def test_f32_last_stage_has_no_read_write_overlap(hji_lib):
-    """On a grid with several waves of tiles per stage (1001^2: about 2000
-    tiles for 760 resident CTAs), a tile's last stage must not see the low
+    """On a grid with several waves of tiles per stage (1001^2: about 1000
+    tiles for about 600 resident CTAs), a tile's last stage must not see the low
     words its neighbours already wrote for V^{n+1}: the march is then
     independent of the order in which tiles run, so every tile shape gives
     the same bits."""
