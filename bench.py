@@ -293,8 +293,13 @@ def main():
         peak = 152 * 128 * 2 * 2070e6 / 1e12
     else:
         peak = 1.25
+    # DRAM bytes per stage launch of this kernel from one ncu capture
+    # (dram__bytes_read.sum + dram__bytes_write.sum, mean of the three RK3
+    # stage launches: 8.1, 12.2 and 16.2 MB, the first touch of each field;
+    # everything else is served by L2).  FP64 was not captured.
+    traffic = 12.16e6 if prec == "f32" else None
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved_tflops / peak, "traffic": None,
+                "frac": achieved_tflops / peak, "traffic": traffic,
                 "kernel": "stage_kernel<%s,2,WENO5> (per-stage, 3 per RK3 step)" % prec,
                 "flops_per_node_stage": FLOPS_PER_NODE_STAGE,
                 "mem_words_per_node_step": WORDS_PER_NODE_STEP[prec],
