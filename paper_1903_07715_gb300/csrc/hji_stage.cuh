@@ -746,23 +746,17 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
         T* wh = reinterpret_cast<T*>(sb + L::H(buf));
         T* wl = reinterpret_cast<T*>(sb + L::LO(buf));
         const T* wd = reinterpret_cast<const T*>(sb + L::DD(buf));
-        // FP32 stages 2+: fold the increment into the low word once per node.
-        if constexpr (INCR) {
-            if (has_d) {
-                for (int i = 4 * threadIdx.x; i < WIN; i += 4 * kThreads) {
-                    const Q4<T> lo = ld4(wl + i), d = ld4(wd + i);
-                    const T s[4] = {lo.v[0] + d.v[0], lo.v[1] + d.v[1], lo.v[2] + d.v[2],
-                                    lo.v[3] + d.v[3]};
-                    st4(wl + i, s);
-                }
-                __syncthreads();
-            }
-        }
+        // FP32 stages 2+: the stencil input is hi + (lo + d); every reader
+        // adds the stage increment to the low word itself.  Ghost slots lie
+        // outside the tensor, so their increments read as zero.
         auto pair_at = [&](int r, int c) {
             Pair<T> p;
             p.h = wh[r * SWX + c];
             p.l = T(0);
-            if constexpr (INCR) p.l = wl[r * SWX + c];
+            if constexpr (INCR) {
+                p.l = wl[r * SWX + c];
+                if (has_d) p.l += wd[r * SWX + c];
+            }
             return p;
         };
 
@@ -829,7 +823,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
                 const Q4<T> h0 = ld4(wh + s0), h1 = ld4(wh + s0 + SWX);
                 T dv[4];
                 if constexpr (INCR) {
-                    const Q4<T> l0 = ld4(wl + s0), l1 = ld4(wl + s0 + SWX);
+                    Q4<T> l0 = ld4(wl + s0), l1 = ld4(wl + s0 + SWX);
+                    if (has_d) {
+                        const Q4<T> d0 = ld4(wd + s0), d1 = ld4(wd + s0 + SWX);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            l0.v[q] += d0.v[q];
+                            l1.v[q] += d1.v[q];
+                        }
+                    }
 #pragma unroll
                     for (int q = 0; q < 4; ++q) dv[q] = (h1.v[q] - h0.v[q]) + (l1.v[q] - l0.v[q]);
                 } else {
@@ -895,8 +897,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
                                   h1.v[2], h1.v[3], h2.v[0], h2.v[1], h2.v[2], h2.v[3]};
                 if constexpr (INCR) {
                     const Q4<T> l0 = ld4(wl + s0), l1 = ld4(wl + s0 + 4), l2 = ld4(wl + s0 + 8);
-                    const T lv[12] = {l0.v[0], l0.v[1], l0.v[2], l0.v[3], l1.v[0], l1.v[1],
-                                      l1.v[2], l1.v[3], l2.v[0], l2.v[1], l2.v[2], l2.v[3]};
+                    T lv[12] = {l0.v[0], l0.v[1], l0.v[2], l0.v[3], l1.v[0], l1.v[1],
+                                l1.v[2], l1.v[3], l2.v[0], l2.v[1], l2.v[2], l2.v[3]};
+                    if (has_d) {
+                        const Q4<T> d0 = ld4(wd + s0), d1 = ld4(wd + s0 + 4), d2 = ld4(wd + s0 + 8);
+                        const T dd[12] = {d0.v[0], d0.v[1], d0.v[2], d0.v[3], d1.v[0], d1.v[1],
+                                          d1.v[2], d1.v[3], d2.v[0], d2.v[1], d2.v[2], d2.v[3]};
+#pragma unroll
+                        for (int j = 0; j < 12; ++j) lv[j] += dd[j];
+                    }
 #pragma unroll
                     for (int j = 4 - G; j < 7 + G; ++j)
                         d[j] = (hv[j + 1] - hv[j]) + (lv[j + 1] - lv[j]);
@@ -1139,11 +1148,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
                 } else {
                     // V^n + inc as an unevaluated float pair (error-free
                     // two-sum), then min(., l) of Eq. (7)-(8).
-                    // The low word of V^n: the window's low words hold it
-                    // unless the stage increment was folded into them.
+                    // The low word of V^n, from the window.
                     T lo[4];
                     {
-                        const Q4<T> q = has_d ? ldg4(C.vlo + gidx) : ld4(wl + s0 + 4);
+                        const Q4<T> q = ld4(wl + s0 + 4);
 #pragma unroll
                         for (int i = 0; i < 4; ++i) lo[i] = q.v[i];
                     }
