@@ -192,10 +192,12 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--workload", default="di1001", choices=["di1001", "quad61", "batch256"],
+    ap.add_argument("--workload", default="di1001",
+                    choices=["di1001", "quad61", "batch256", "di8192"],
                     help="di1001: whole warm-started solves of the 1001^2 double integrator "
-                         "(default); quad61 / batch256: 50-step FP32 marches of the HBM-bound "
-                         "61^4 quadrotor subsystem / 256 uneven double integrators")
+                         "(default); quad61 / batch256 / di8192: 50-step FP32 marches of the "
+                         "HBM-bound 61^4 quadrotor subsystem / 256 uneven double integrators / "
+                         "8192^2 double integrator")
     args = ap.parse_args()
 
     rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
@@ -318,7 +320,7 @@ def main():
                        "l2": "flushed (512 MB write) before every timed solve; the 1001^2 "
                              "fields stay L2-resident within a solve",
                        "parallelism": "independent instance per GPU" if world > 1 else "1 GPU",
-                       "tile_shape": ["32x32", "16x64", "64x16"][tuned],
+                       "tile_shape": ["31x32", "15x64", "63x16"][tuned],
                        "autotune_ms_per_step": tune_ms},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk}
 
@@ -399,7 +401,8 @@ def time_to_converge(hji, torch, gd, dyn, l, l_dev, k_dev):
 def run_hbm_workload(args, hji, torch, dist, rank, world, local_rank):
     """Main line for the HBM-bound workloads: each bench step is one 50-step
     FP32 ENO2/RK2 march (set-up, init from V0 = l, 100 stage launches)."""
-    name = "quad4d_61^4" if args.workload == "quad61" else "batch256_di_101..501"
+    name = {"quad61": "quad4d_61^4", "batch256": "batch256_di_101..501",
+            "di8192": "di_8192^2"}[args.workload]
     clocks = ClockSampler(local_rank)
     res = hbm_workloads(hji, torch, steps=50, only=name, repeats=args.steps, warmup=args.warmup,
                         clocks=clocks)[name]
@@ -484,6 +487,11 @@ def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=N
         insts = W.batch_instances(count=256, seed=1903)
         cases.append(("batch256_di_101..501", [i["grid"] for i in insts],
                       [i["dyn"] for i in insts], [W.instance_target(i) for i in insts]))
+    if only in (None, "di_8192^2"):
+        # 2-D stress grid with the 101^2 workload's dynamics (|u| <= 1, no
+        # disturbance, l = 1 - |x1|): 67 M nodes, 268 MB per FP32 field.
+        gd, dyn, l = W.di_config(8192)
+        cases.append(("di_8192^2", [gd], [dyn], [l]))
     opts = dict(scheme="eno2", rk=2, cfl=0.5, tol=0.0, max_steps=steps, check_every=steps)
     stream = torch.cuda.current_stream()
     for name, gds, dyns, ls in cases:
@@ -519,7 +527,7 @@ def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=N
             launches += max(s["kernel_launches"] for s in sts)
         clk = clocks.stop() if clocks is not None else None
         gbs = upd * bytes_per_update / (ms * 1e-3) / 1e9
-        out[name] = {"nodes": cells, "steps": steps, "ms": ms / repeats, "tile_shape": ["32x32", "16x64", "64x16"][tuned],
+        out[name] = {"nodes": cells, "steps": steps, "ms": ms / repeats, "tile_shape": ["31x32", "15x64", "63x16"][tuned],
                      "cell_updates_per_s": upd / (ms * 1e-3), "ms_total": ms,
                      "updates_total": upd, "launches": launches, "clocks": clk,
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",

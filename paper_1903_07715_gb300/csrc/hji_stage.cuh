@@ -690,6 +690,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
     int t = walk.next();
     int buf = 0;
     bool issued = false;
+    // Last stage: each thread's running max|dV| over the CTA's tiles of the
+    // current instance, published (with the tile count) when the CTA moves
+    // on to another instance or runs out of tiles.
+    T dmax = T(0);
+    int run_tiles = 0;
     while (t >= 0) {
         const unsigned long long entry = a.tiles[t];
         const int inst = static_cast<int>(entry >> 48);
@@ -878,7 +883,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
         // derivatives of each axis are folded at once into the
         // Lax-Friedrichs sum Lv = sum_a alpha_a (p+ - p-) / 2 and the
         // averaged gradient pbar, so they never need to be kept for all axes.
-        T dmax = T(0);
         const int gx0 = x0 + 4 * grp;
         const int gy = y0 + ry;
         if (thread_works && gx0 < nx && (NDIM < 2 || gy < ny)) {
@@ -1224,25 +1228,33 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
         }
 
         if constexpr (LAST) {
-            // CTA max of |dV| (NaN wins), then the instance-wide reduction.
+            ++run_tiles;
+            if (!pref) {  // uniform: the next tile is another instance's, or none
+                // CTA max of |dV| (NaN wins), then the instance-wide reduction;
+                // the CTA that completes the instance's tile count finishes
+                // the step.
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const T other = __shfl_xor_sync(0xffffffffu, dmax, o);
-                dmax = (other > dmax || other != other) ? other : dmax;
-            }
-            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dmax;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                T mt = red[0];
-                for (int w = 1; w < kThreads / 32; ++w)
-                    mt = (red[w] > mt || red[w] != red[w]) ? red[w] : mt;
-                const double m = static_cast<double>(mt);
-                const InstDesc& D = a.insts[inst];
-                InstState* st = D.state;
-                atomicMax(&st->delta_bits, static_cast<unsigned long long>(__double_as_longlong(m)));
-                __threadfence();
-                const unsigned int prev = atomicAdd(&st->tiles_done, 1u);
-                if (prev + 1 == static_cast<unsigned int>(C.ntiles)) finish_step(D);
+                for (int o = 16; o > 0; o >>= 1) {
+                    const T other = __shfl_xor_sync(0xffffffffu, dmax, o);
+                    dmax = (other > dmax || other != other) ? other : dmax;
+                }
+                if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dmax;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    T mt = red[0];
+                    for (int w = 1; w < kThreads / 32; ++w)
+                        mt = (red[w] > mt || red[w] != red[w]) ? red[w] : mt;
+                    const double m = static_cast<double>(mt);
+                    const InstDesc& D = a.insts[inst];
+                    InstState* st = D.state;
+                    atomicMax(&st->delta_bits, static_cast<unsigned long long>(__double_as_longlong(m)));
+                    __threadfence();
+                    const unsigned int prev = atomicAdd(&st->tiles_done, static_cast<unsigned int>(run_tiles));
+                    if (prev + static_cast<unsigned int>(run_tiles) == static_cast<unsigned int>(C.ntiles))
+                        finish_step(D);
+                }
+                dmax = T(0);
+                run_tiles = 0;
             }
         }
         buf ^= 1;
