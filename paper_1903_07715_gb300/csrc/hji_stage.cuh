@@ -627,6 +627,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
     __shared__ TileCtx<T> C;
     __shared__ T red[kThreads / 32];
     __shared__ __align__(8) unsigned long long bars[2];
+    __shared__ TileGeo geo_s[2];  // where the tile in each buffer sits (written by thread 0)
     T* dys = reinterpret_cast<T*>(sb + L::DYS);  // dys[r][c] = W(r+1, c) - W(r, c), tile columns
 
     const int ntiles = *a.ntiles;
@@ -717,12 +718,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
             issued = false;
             continue;
         }
-        const TileGeo tg = tile_geo<T, NDIM, TY, TX>(C, local);
         const int tn = walk.next();
         const bool pref = tn >= 0 && static_cast<int>(a.tiles[tn] >> 48) == inst;
         // Buffer `buf` was last read two tiles ago, which every thread
-        // finished before the barrier below of the previous tile.
-        if (threadIdx.x == 0 && !issued) issue(tg, buf);
+        // finished before the barrier below of the previous tile.  Thread 0
+        // places the tiles (one integer division each) for everyone.
+        if (threadIdx.x == 0 && !issued) {
+            geo_s[buf] = tile_geo<T, NDIM, TY, TX>(C, local);
+            issue(geo_s[buf], buf);
+        }
         const bool ok = mbar_wait_bounded(bar0 + 8u * buf, (phase >> buf) & 1u);
         phase ^= 1u << buf;
         // After this barrier every thread is done with the previous tile, so
@@ -736,10 +740,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
             }
             return;
         }
+        const TileGeo& tg = geo_s[buf];  // read from shared memory where used
         // Prefetch the next tile of the walk while this one is computed.
-        if (threadIdx.x == 0 && pref)
-            issue(tile_geo<T, NDIM, TY, TX>(C, static_cast<int>(a.tiles[tn] & 0xFFFFFFFFFFFFull)),
-                  buf ^ 1);
+        if (threadIdx.x == 0 && pref) {
+            geo_s[buf ^ 1] = tile_geo<T, NDIM, TY, TX>(C, static_cast<int>(a.tiles[tn] & 0xFFFFFFFFFFFFull));
+            issue(geo_s[buf ^ 1], buf ^ 1);
+        }
 
         const int nx = C.n[AX];
         const int ny = NDIM >= 2 ? C.n[AY] : 1;
@@ -942,6 +948,19 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
                              weno_rev(d[i + 3], d[i + 4], d[i + 5], Tt[i + 2], Tt[i + 3], zr) * ix);
                         zl = zr;
                     }
+                } else if constexpr (SCHEME == HJI_ENO2) {
+                    // Node i: second differences S[i+2..i+4]; the choice
+                    // between S[j] and S[j+1] serves p+ of node j-3 and p- of
+                    // node j-2, so it is made once.
+                    T S[8], M[7];
+#pragma unroll
+                    for (int j = 2; j <= 7; ++j) S[j] = d[j + 1] - d[j];
+#pragma unroll
+                    for (int j = 2; j <= 6; ++j) M[j] = smaller_mag(S[j], S[j + 1]);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        fold(AX, i, (d[i + 3] + T(0.5) * M[i + 2]) * ix,
+                             (d[i + 4] - T(0.5) * M[i + 3]) * ix);
                 } else {
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
