@@ -898,6 +898,78 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
                 Lv[i] += C.half_alpha[ax] * (pp_ - pm_);
                 pb[i][ax] = T(0.5) * (pp_ + pm_);
             };
+            const long long gidx = tg.base + (long long)gy * sy + gx0;
+            // Slower axes first (their stencil lines are the largest live
+            // set): the lines straight from global memory
+            // (L1/L2), four nodes per load, differenced plane by plane.  The
+            // slow index is the same for the whole tile, so a tile away from
+            // that axis' edges takes the direct path.
+#pragma unroll
+            for (int ax = 0; ax < NDIM - 2; ++ax) {
+                const long long st = C.stride[ax];
+                const int si = tg.sidx[ax], ns = C.n[ax];
+                const long long l0 = gidx - (long long)si * st;  // node 0 of these lines
+                auto plane = [&](int j, Pair<T>* out) {
+                    const long long o = l0 + (long long)j * st;
+                    const Q4<T> h = ldg4(C.win + o);
+                    Q4<T> lo, dd;
+                    if constexpr (INCR) {
+                        lo = ldg4(C.vlo + o);
+                        if (C.din) dd = ldg4(C.din + o);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        out[i].h = h.v[i];
+                        out[i].l = T(0);
+                        if constexpr (INCR) {
+                            out[i].l = lo.v[i];
+                            if (C.din) out[i].l += dd.v[i];
+                        }
+                    }
+                };
+                auto plane_any = [&](int j, Pair<T>* out) {
+                    if (j >= 0 && j < ns) {
+                        plane(j, out);
+                    } else if (C.periodic[ax]) {
+                        j %= ns;
+                        if (j < 0) j += ns;
+                        plane(j, out);
+                    } else {
+                        const bool low = j < 0;
+                        Pair<T> e[4], i1[4];
+                        plane(low ? 0 : ns - 1, e);
+                        plane(low ? 1 : ns - 2, i1);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            out[i] = extrapolate(e[i], i1[i], low ? -j : j - (ns - 1));
+                    }
+                };
+                const bool inner = si >= G && si < ns - G;
+                T D[2 * G][4];
+                Pair<T> prev[4], cur[4];
+                if (inner) plane(si - G, prev);
+                else plane_any(si - G, prev);
+#pragma unroll
+                for (int o = 1 - G; o <= G; ++o) {
+                    if (inner) plane(si + o, cur);
+                    else plane_any(si + o, cur);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        D[o + G - 1][i] = pair_diff(cur[i], prev[i]);
+                        prev[i] = cur[i];
+                    }
+                }
+                const T is = C.inv_dx[ax];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    T Di[2 * G];
+#pragma unroll
+                    for (int o = 0; o < 2 * G; ++o) Di[o] = D[o][i];
+                    T pm_, pp_;
+                    one_sided_diffs<T, SCHEME>(Di, is, pm_, pp_);
+                    fold(ax, i, pm_, pp_);
+                }
+            }
             // x: the window row of this run, columns 4 grp .. 4 grp + 11.
             const int s0 = (ry + GY) * SWX + 4 * grp;
             {
@@ -994,77 +1066,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
                     T pm_, pp_;
                     one_sided_diffs<T, SCHEME>(D, iy, pm_, pp_);
                     fold(AY, i, pm_, pp_);
-                }
-            }
-            const long long gidx = tg.base + (long long)gy * sy + gx0;
-            // Slower axes: the stencil lines straight from global memory
-            // (L1/L2), four nodes per load, differenced plane by plane.  The
-            // slow index is the same for the whole tile, so a tile away from
-            // that axis' edges takes the direct path.
-#pragma unroll
-            for (int ax = 0; ax < NDIM - 2; ++ax) {
-                const long long st = C.stride[ax];
-                const int si = tg.sidx[ax], ns = C.n[ax];
-                const long long l0 = gidx - (long long)si * st;  // node 0 of these lines
-                auto plane = [&](int j, Pair<T>* out) {
-                    const long long o = l0 + (long long)j * st;
-                    const Q4<T> h = ldg4(C.win + o);
-                    Q4<T> lo, dd;
-                    if constexpr (INCR) {
-                        lo = ldg4(C.vlo + o);
-                        if (C.din) dd = ldg4(C.din + o);
-                    }
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        out[i].h = h.v[i];
-                        out[i].l = T(0);
-                        if constexpr (INCR) {
-                            out[i].l = lo.v[i];
-                            if (C.din) out[i].l += dd.v[i];
-                        }
-                    }
-                };
-                auto plane_any = [&](int j, Pair<T>* out) {
-                    if (j >= 0 && j < ns) {
-                        plane(j, out);
-                    } else if (C.periodic[ax]) {
-                        j %= ns;
-                        if (j < 0) j += ns;
-                        plane(j, out);
-                    } else {
-                        const bool low = j < 0;
-                        Pair<T> e[4], i1[4];
-                        plane(low ? 0 : ns - 1, e);
-                        plane(low ? 1 : ns - 2, i1);
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            out[i] = extrapolate(e[i], i1[i], low ? -j : j - (ns - 1));
-                    }
-                };
-                const bool inner = si >= G && si < ns - G;
-                T D[2 * G][4];
-                Pair<T> prev[4], cur[4];
-                if (inner) plane(si - G, prev);
-                else plane_any(si - G, prev);
-#pragma unroll
-                for (int o = 1 - G; o <= G; ++o) {
-                    if (inner) plane(si + o, cur);
-                    else plane_any(si + o, cur);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        D[o + G - 1][i] = pair_diff(cur[i], prev[i]);
-                        prev[i] = cur[i];
-                    }
-                }
-                const T is = C.inv_dx[ax];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    T Di[2 * G];
-#pragma unroll
-                    for (int o = 0; o < 2 * G; ++o) Di[o] = D[o][i];
-                    T pm_, pp_;
-                    one_sided_diffs<T, SCHEME>(Di, is, pm_, pp_);
-                    fold(ax, i, pm_, pp_);
                 }
             }
             // Hamiltonian (Eq. (6)) at pbar.  With the boxes written as
