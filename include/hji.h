@@ -286,6 +286,17 @@ const char* hji_engine_last_error(hji_engine e);
 hji_status hji_autotune(hji_grid g, const void* l, int ptr_is_device, const hji_solve_opts* o,
                         int steps, void* cuda_stream, int* chosen, double* ms_per_step);
 
+/* Self-test of the bounded waits inside the stage kernels (the paper has no
+ * counterpart).  Every wait of a stage kernel on a TMA copy gives up after a
+ * time limit and the kernel records HJI_E_TIMEOUT for the instance, instead
+ * of hanging the GPU.  This call runs the same wait routine on one CTA whose
+ * mbarrier is armed for bytes that no copy delivers, with limit_ns
+ * (1e6 .. 4e9 nanoseconds), and returns HJI_E_TIMEOUT when the wait gave up
+ * (the expected result), HJI_E_STATE if the barrier completed, HJI_E_INVALID
+ * for a limit out of range, HJI_E_NOMEM / HJI_E_CUDA on runtime failures.
+ * Synchronous on cuda_stream; the message is in hji_last_error(NULL). */
+hji_status hji_selftest_bounded_wait(int64_t limit_ns, void* cuda_stream);
+
 /* Grid facts: ndim, n[], and the number of nodes (may be NULL each). */
 hji_status hji_grid_info(hji_grid g, int* ndim, int64_t* n, int64_t* num_nodes);
 

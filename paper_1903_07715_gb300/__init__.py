@@ -34,7 +34,8 @@ EXPORTS = ["hji_grid_create", "hji_grid_destroy", "hji_dynamics_set", "hji_solve
            "hji_batch_solve", "hji_value_get", "hji_value_transfer", "hji_grid_info",
            "hji_status_string", "hji_last_error", "hji_solve_noalloc", "hji_noalloc_last_error",
            "hji_engine_create", "hji_engine_submit", "hji_engine_step", "hji_engine_poll",
-           "hji_engine_destroy", "hji_engine_last_error", "hji_autotune"]
+           "hji_engine_destroy", "hji_engine_last_error", "hji_autotune",
+           "hji_selftest_bounded_wait"]
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -129,6 +130,7 @@ def load(build_if_missing=False):
                                  ctypes.POINTER(ctypes.c_double)]
     lib.hji_engine_last_error.argtypes = [vp]
     lib.hji_engine_last_error.restype = ctypes.c_char_p
+    lib.hji_selftest_bounded_wait.argtypes = [ctypes.c_int64, vp]
     for name in EXPORTS:
         if name not in ("hji_status_string", "hji_last_error", "hji_noalloc_last_error",
                         "hji_engine_last_error"):
@@ -169,6 +171,10 @@ def hji_value_transfer(dst, src, stream):
 
 def hji_grid_info(g, ndim, n, num_nodes):
     return load().hji_grid_info(g, ndim, n, num_nodes)
+
+
+def hji_selftest_bounded_wait(limit_ns, stream):
+    return load().hji_selftest_bounded_wait(limit_ns, stream)
 
 
 def hji_solve_noalloc(ndim, n, lo, hi, periodic, prec, dyn, l, k, v_out, opts, stream, stats):

@@ -1195,6 +1195,27 @@ hji_status hji_autotune(hji_grid g, const void* l, int ptr_is_device, const hji_
     return HJI_OK;
 }
 
+hji_status hji_selftest_bounded_wait(int64_t limit_ns, void* cuda_stream) {
+    if (limit_ns < 1000000 || limit_ns > 4000000000ll)
+        return fail(nullptr, HJI_E_INVALID, "limit_ns must be 1e6..4e9");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int* d = nullptr;
+    if (cudaMallocAsync(&d, sizeof(int), s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, HJI_E_NOMEM, "device allocation failed");
+    }
+    int h = -1;
+    cudaError_t e = cudaMemsetAsync(d, 0xFF, sizeof(int), s);
+    if (e == cudaSuccess) e = hji::launch_wait_selftest((unsigned long long)limit_ns, d, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(nullptr, HJI_E_CUDA, std::string("self-test: ") + cudaGetErrorString(e));
+    if (h == 4) return fail(nullptr, HJI_E_TIMEOUT, "the bounded wait gave up, as it should");
+    if (h == 0) return fail(nullptr, HJI_E_STATE, "a barrier that nothing completes completed");
+    return fail(nullptr, HJI_E_CUDA, "self-test kernel wrote no result");
+}
+
 hji_status hji_grid_info(hji_grid g, int* ndim, int64_t* n, int64_t* num_nodes) {
     if (!g) return fail(nullptr, HJI_E_INVALID, "grid is NULL");
     if (ndim) *ndim = g->ndim;

@@ -182,6 +182,8 @@ cudaError_t launch_init(const InstDesc* d_insts, const InstDesc* h_insts, int co
 // variant (host; D's field pointers, sizes and strides must be set).
 // Returns false (with a message) if the driver rejects a map.
 bool encode_maps(InstDesc& D, bool f32, int scheme, int variant, const char** why);
+// Bounded-wait self-test (hji_setup.cu): *d_result = 4 when the wait gave up.
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, int* d_result, cudaStream_t s);
 cudaError_t launch_convert(long long n, const void* src_hi, const void* src_lo, bool src_f32,
                            void* dst_hi, void* dst_lo, bool dst_f32, cudaStream_t s);
 

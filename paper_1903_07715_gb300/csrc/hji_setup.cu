@@ -10,6 +10,7 @@
 #include <cfloat>
 
 #include "hji_common.cuh"
+#include "hji_stage.cuh"
 
 namespace hji {
 
@@ -185,6 +186,31 @@ __global__ void __launch_bounds__(kThreads)
             static_cast<double*>(dst_hi)[c] = v;
         }
     }
+}
+
+// Self-test of the bounded TMA wait: one CTA arms an mbarrier for 16 bytes
+// that no copy delivers, so its phase never completes, and waits on it with
+// the stage kernel's bounded routine.  result = 4 (the status a stage kernel
+// records) when the wait gave up, 0 if the phase completed.  Nothing is in
+// flight on the barrier when the CTA leaves.
+__global__ void wait_selftest_kernel(unsigned long long limit_ns, int* result) {
+    __shared__ __align__(8) unsigned long long bar;
+    const unsigned b = smem_addr(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(b, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_expect_tx(b, 16u);
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(b, 0u, limit_ns);
+    const int gave_up = __syncthreads_or(!ok);
+    if (threadIdx.x == 0) *result = gave_up ? 4 : 0;
+}
+
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, int* d_result, cudaStream_t s) {
+    wait_selftest_kernel<<<1, 64, 0, s>>>(limit_ns, d_result);
+    return cudaGetLastError();
 }
 
 static int grid_for(long long work, int cap);

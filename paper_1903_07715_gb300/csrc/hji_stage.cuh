@@ -466,13 +466,14 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
     return ok != 0u;
 }
 // Wait for the phase with the given parity; false if it has not completed
-// within kWaitNs (or 2^26 polls).
-static __device__ __noinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+// within limit_ns (or 2^26 polls).
+static __device__ __noinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity,
+                                                      unsigned long long limit_ns = kWaitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (unsigned it = 1; it < (1u << 26); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63u) == 0u && global_ns() - t0 > kWaitNs) return false;
+        if ((it & 63u) == 0u && global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }
@@ -532,7 +533,10 @@ struct StageSmem {
     static constexpr int WINB = round128(WIN * (int)sizeof(T));
     static constexpr int NODEB = round128(NODES * (int)sizeof(T));
     static constexpr int NF = INCR ? 3 : 1;
-    static constexpr int NN = LAST ? (INCR ? 1 : 2) : 0;
+    // FP64 last stage: l and V^n at the tile nodes.  (The FP32 last stage
+    // reads l from L2 where it uses it: staging it would take the 8 KB that
+    // keep four CTAs per SM.)
+    static constexpr int NN = (LAST && !INCR) ? 2 : 0;
     static constexpr int BUFB = NF * WINB + NN * NODEB;
     static constexpr int DYS = 2 * BUFB;
     static constexpr int DYSB = NDIM >= 2 ? round128((SH - 1) * TX * (int)sizeof(T)) : 0;
@@ -660,7 +664,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
     // Bytes one tile's copies deliver to its buffer's barrier.
     const unsigned tile_bytes =
         static_cast<unsigned>(WIN * sizeof(T)) * (INCR ? (has_d ? 3u : 2u) : 1u) +
-        (LAST ? static_cast<unsigned>(TY * TX * sizeof(T)) * ((!INCR && reads_v) ? 2u : 1u) : 0u);
+        ((LAST && !INCR) ? static_cast<unsigned>(TY * TX * sizeof(T)) * (reads_v ? 2u : 1u) : 0u);
 
     // Thread 0: start the tensor copies of a tile into buffer b.
     auto issue = [&](const TileGeo& tg, int b) {
@@ -678,11 +682,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
             tma_load<NDIM>(base + L::LO(b), C.tm_lo, cw, bar);
             if (has_d) tma_load<NDIM>(base + L::DD(b), C.tm_d, cw, bar);
         }
-        if constexpr (LAST) {
+        if constexpr (LAST && !INCR) {
             tma_load<NDIM>(base + L::LT(b), C.tm_l, cn, bar);
-            if constexpr (!INCR) {
-                if (reads_v) tma_load<NDIM>(base + L::VN(b), C.tm_vn, cn, bar);
-            }
+            if (reads_v) tma_load<NDIM>(base + L::VN(b), C.tm_vn, cn, bar);
         }
     };
 
@@ -708,7 +710,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
                 tensormap_acquire(C.tm_win);
                 if (INCR) tensormap_acquire(C.tm_lo);
                 if (has_d) tensormap_acquire(C.tm_d);
-                if (LAST) tensormap_acquire(C.tm_l);
+                if (LAST && !INCR) tensormap_acquire(C.tm_l);
                 if (LAST && !INCR && reads_v) tensormap_acquire(C.tm_vn);
             }
             loaded = inst;
@@ -1179,8 +1181,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
 #pragma unroll
                         for (int i = 0; i < 4; ++i) lo[i] = q.v[i];
                     }
-                    const Q4<T> lt =
-                        ld4(reinterpret_cast<const T*>(sb + L::LT(buf)) + ry * TX + 4 * grp);
+                    const Q4<T> lt = ldg4(C.l + gidx);  // l (its pad columns are never used)
                     T nh[4], nl[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {

@@ -73,3 +73,8 @@ def test_product_has_no_oracle_dependency():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "hji_oracle" not in text, f
+
+
+def test_selftest_limit_is_validated_before_device_work(hji_lib):
+    assert hji_lib.hji_selftest_bounded_wait(10, None) == hji_lib.HJI_E_INVALID
+    assert hji_lib.hji_selftest_bounded_wait(10 ** 10, None) == hji_lib.HJI_E_INVALID
