@@ -72,7 +72,7 @@ enum TensorMapSlot {
 // starts on a 32-byte boundary: the alignment TMA needs for its row strides
 // and for 16-byte vector accesses of four FP32 (or two FP64) nodes.
 struct InstDesc {
-    alignas(64) CUtensorMap tm[kNumMaps];
+    CUtensorMap tm[kNumMaps];  // 128-byte aligned (the type says so)
     int ndim;
     int periodic[MAXD];
     int n[MAXD];

@@ -35,10 +35,13 @@ __global__ void __launch_bounds__(kThreads) table_kernel(const InstDesc* __restr
 }
 
 constexpr int kAlphaTab = 2048;  // term values cached per CTA (FP64)
+constexpr int kAlphaChunk = 16;  // consecutive nodes per alpha thread
 
 __global__ void __launch_bounds__(kThreads) alpha_kernel(const InstDesc* __restrict__ insts) {
     const InstDesc& D = insts[blockIdx.y];
     const int nd = D.ndim;
+    const int fa = nd - 1;  // fastest axis
+    const int nx = D.n[fa];
     const Dyn& f = D.dyn;
     // w_t phi_t(x) depends on one coordinate: tabulate it once per CTA when
     // the term axes are short enough, instead of once per node.
@@ -58,44 +61,108 @@ __global__ void __launch_bounds__(kThreads) alpha_kernel(const InstDesc* __restr
         }
     }
     __syncthreads();
+    auto term = [&](int t, int i) {
+        const int ax = f.term_axis[t];
+        return use_tab ? tab[tab_off[t] + i]
+                       : f.term_w[t] * apply_fn(f.term_fn[t], D.lo[ax] + (double)i * D.dx[ax]);
+    };
+    // f_a is affine in (u, d): its range over the boxes is centre +- radius,
+    // so max |f_a| = |centre| + radius, with the radius the same at every
+    // node and the centre c_a + G umid + E dmid + sum_b A_ab x_b + terms.
+    // (Loops over axes run to MAXD with a guard, so the per-axis arrays stay
+    // in registers.)
+    double radius[MAXD], cconst[MAXD], inv_dx[MAXD];
+#pragma unroll
+    for (int a = 0; a < MAXD; ++a) {
+        if (a >= nd) {
+            radius[a] = cconst[a] = inv_dx[a] = 0.0;
+            continue;
+        }
+        double c = f.c[a], r = 0.0;
+        for (int j = 0; j < f.m; ++j) {
+            c += f.G[a * MAXU + j] * (0.5 * (f.ulo[j] + f.uhi[j]));
+            r += fabs(f.G[a * MAXU + j]) * (0.5 * (f.uhi[j] - f.ulo[j]));
+        }
+        for (int k = 0; k < f.q; ++k) {
+            c += f.E[a * MAXU + k] * (0.5 * (f.dlo[k] + f.dhi[k]));
+            r += fabs(f.E[a * MAXU + k]) * (0.5 * (f.dhi[k] - f.dlo[k]));
+        }
+        cconst[a] = c;
+        radius[a] = r;
+        inv_dx[a] = 1.0 / D.dx[a];
+    }
+    // Each thread takes chunks of consecutive nodes; along a row of the
+    // fastest axis only x_fa changes, so the rest of each centre (rowc) is
+    // formed once per row the chunk touches.
+    constexpr int kChunk = kAlphaChunk;
+    const int ncells = static_cast<int>(D.ncells);
     double amax[MAXD] = {0.0, 0.0, 0.0, 0.0};
     double rmax = 0.0;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < D.ncells;
-         c += (long long)gridDim.x * blockDim.x) {
-        double x[MAXD];
-        int ix[MAXD];
-        long long r = c;
-        for (int a = nd - 1; a >= 0; --a) {
-            const long long i = r % D.n[a];
-            r /= D.n[a];
-            ix[a] = (int)i;
-            x[a] = D.lo[a] + (double)i * D.dx[a];
-        }
-        double rate = 0.0;
-        for (int a = 0; a < nd; ++a) {
-            // f_a is affine in (u, d): its range over the boxes is
-            // centre +- radius, so max |f_a| = |centre| + radius.
-            double centre = f.c[a], radius = 0.0;
-            for (int b = 0; b < nd; ++b) centre += f.A[a * MAXD + b] * x[b];
-            for (int t = 0; t < f.nterms; ++t)
-                if (f.term_row[t] == a)
-                    centre += use_tab ? tab[tab_off[t] + ix[f.term_axis[t]]]
-                                      : f.term_w[t] * apply_fn(f.term_fn[t], x[f.term_axis[t]]);
-            for (int j = 0; j < f.m; ++j) {
-                centre += f.G[a * MAXU + j] * (0.5 * (f.ulo[j] + f.uhi[j]));
-                radius += fabs(f.G[a * MAXU + j]) * (0.5 * (f.uhi[j] - f.ulo[j]));
+    double rowc[MAXD];
+    const long long nchunks = (static_cast<long long>(ncells) + kChunk - 1) / kChunk;
+    for (long long ch = blockIdx.x * (long long)blockDim.x + threadIdx.x; ch < nchunks;
+         ch += (long long)gridDim.x * blockDim.x) {
+        int c = static_cast<int>(ch * kChunk);
+        const int cend = min(c + kChunk, ncells);
+        int row = c / nx;
+        int i = c - row * nx;
+        bool fresh = true;
+        for (; c < cend; ++c, ++i) {
+            if (i == nx) {
+                i = 0;
+                ++row;
+                fresh = true;
             }
-            for (int k = 0; k < f.q; ++k) {
-                centre += f.E[a * MAXU + k] * (0.5 * (f.dlo[k] + f.dhi[k]));
-                radius += fabs(f.E[a * MAXU + k]) * (0.5 * (f.dhi[k] - f.dlo[k]));
+            if (fresh) {  // the row's constant part of every centre
+                fresh = false;
+                double xs[MAXD];  // coordinates of the slower axes
+                int idx[MAXD];
+                int r = row;
+#pragma unroll
+                for (int a = MAXD - 1; a >= 0; --a) {
+                    idx[a] = 0;
+                    xs[a] = 0.0;
+                    if (a < nd - 1) {
+                        idx[a] = r % D.n[a];
+                        r /= D.n[a];
+                        xs[a] = D.lo[a] + (double)idx[a] * D.dx[a];
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < MAXD; ++a) {
+                    double cc = cconst[a];
+#pragma unroll
+                    for (int b = 0; b < MAXD; ++b)
+                        if (b < nd - 1) cc += f.A[a * MAXD + b] * xs[b];
+                    for (int t = 0; t < f.nterms; ++t) {
+                        const int ax = f.term_axis[t];
+                        if (f.term_row[t] == a && ax != fa) {
+                            int ia = idx[0];
+#pragma unroll
+                            for (int b = 1; b < MAXD; ++b) ia = ax == b ? idx[b] : ia;
+                            cc += term(t, ia);
+                        }
+                    }
+                    rowc[a] = cc;
+                }
             }
-            const double al = fabs(centre) + radius;
-            amax[a] = fmax(amax[a], al);
-            rate += al / D.dx[a];
+            const double xf = D.lo[fa] + (double)i * D.dx[fa];
+            double rate = 0.0;
+#pragma unroll
+            for (int a = 0; a < MAXD; ++a) {
+                if (a >= nd) break;
+                double centre = rowc[a] + f.A[a * MAXD + fa] * xf;
+                for (int t = 0; t < f.nterms; ++t)
+                    if (f.term_row[t] == a && f.term_axis[t] == fa) centre += term(t, i);
+                const double al = fabs(centre) + radius[a];
+                amax[a] = fmax(amax[a], al);
+                rate += al * inv_dx[a];
+            }
+            rmax = fmax(rmax, rate);
         }
-        rmax = fmax(rmax, rate);
     }
     __shared__ double red[kThreads / 32][MAXD + 1];
+#pragma unroll
     for (int a = 0; a <= MAXD; ++a) {
         double v = a < MAXD ? amax[a] : rmax;
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -143,9 +210,13 @@ __global__ void __launch_bounds__(kThreads) init_kernel(const InstDesc* __restri
     const int nx = D.n[D.ndim - 1];
     const long long pitch = D.ndim >= 2 ? D.stride[D.ndim - 2] : D.nalloc;
     unsigned int bad = 0u;
+    const bool small = D.nalloc < (1ll << 32);  // 32-bit column arithmetic suffices
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < D.nalloc;
          c += (long long)gridDim.x * blockDim.x) {
-        if (c % pitch >= nx) continue;
+        const long long col = small ? static_cast<long long>(static_cast<unsigned>(c) %
+                                                             static_cast<unsigned>(pitch))
+                                    : c % pitch;
+        if (col >= nx) continue;
         const T lv = l[c];
         T v = lv, vlo = T(0);
         if (!isfinite(lv)) bad = 1u;
@@ -246,7 +317,9 @@ cudaError_t launch_setup(const InstDesc* d_insts, const InstDesc* h_insts, int c
         else
             table_kernel<double><<<grid, kThreads, 0, s>>>(d_insts);
     }
-    alpha_kernel<<<dim3(grid_for(cmax, 1024), count), kThreads, 0, s>>>(d_insts);
+    // Each alpha thread takes chunks of kAlphaChunk nodes.
+    alpha_kernel<<<dim3(grid_for((cmax + kAlphaChunk - 1) / kAlphaChunk, 1024), count), kThreads, 0,
+                   s>>>(d_insts);
     return cudaGetLastError();
 }
 
