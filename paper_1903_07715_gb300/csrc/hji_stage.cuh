@@ -533,17 +533,20 @@ struct StageSmem {
     static constexpr int WINB = round128(WIN * (int)sizeof(T));
     static constexpr int NODEB = round128(NODES * (int)sizeof(T));
     static constexpr int NF = INCR ? 3 : 1;
-    // FP64 last stage: l and V^n at the tile nodes.  (The FP32 last stage
-    // reads l from L2 where it uses it: staging it would take the 8 KB that
-    // keep four CTAs per SM.)
-    static constexpr int NN = (LAST && !INCR) ? 2 : 0;
-    static constexpr int BUFB = NF * WINB + NN * NODEB;
-    static constexpr int DYS = 2 * BUFB;
     static constexpr int DYSB = NDIM >= 2 ? round128((SH - 1) * TX * (int)sizeof(T)) : 0;
     // WENO5 y-derivatives p-, p+ of the tile nodes, from the set pass.
     static constexpr bool YSETS = NDIM >= 2 && SCHEME == HJI_WENO5;
-    static constexpr int PMY = DYS + DYSB;
     static constexpr int PYB = YSETS ? round128(NODES * (int)sizeof(T)) : 0;
+    // The last stage stages l (and, FP64, V^n) at the tile nodes with the
+    // window, unless (FP32 WENO5) the two l buffers would cost the fourth CTA
+    // per SM (233472 B of shared memory, about 2.4 KB of it static and
+    // reserved per CTA); it then reads l from L2 where it uses it.
+    static constexpr int BASEB = 2 * NF * WINB + DYSB + 2 * PYB + 128;
+    static constexpr bool STAGE_L = LAST && (!INCR || 4 * (BASEB + 2 * NODEB + 2400) <= 233472);
+    static constexpr int NN = STAGE_L ? (INCR ? 1 : 2) : 0;
+    static constexpr int BUFB = NF * WINB + NN * NODEB;
+    static constexpr int DYS = 2 * BUFB;
+    static constexpr int PMY = DYS + DYSB;
     static constexpr int PPY = PMY + PYB;
     static constexpr int BYTES = PPY + PYB + 128;  // + alignment slack
     static __host__ __device__ constexpr int H(int b) { return b * BUFB; }
@@ -664,7 +667,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
     // Bytes one tile's copies deliver to its buffer's barrier.
     const unsigned tile_bytes =
         static_cast<unsigned>(WIN * sizeof(T)) * (INCR ? (has_d ? 3u : 2u) : 1u) +
-        ((LAST && !INCR) ? static_cast<unsigned>(TY * TX * sizeof(T)) * (reads_v ? 2u : 1u) : 0u);
+        (L::STAGE_L ? static_cast<unsigned>(TY * TX * sizeof(T)) * ((!INCR && reads_v) ? 2u : 1u) : 0u);
 
     // Thread 0: start the tensor copies of a tile into buffer b.
     auto issue = [&](const TileGeo& tg, int b) {
@@ -682,9 +685,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
             tma_load<NDIM>(base + L::LO(b), C.tm_lo, cw, bar);
             if (has_d) tma_load<NDIM>(base + L::DD(b), C.tm_d, cw, bar);
         }
-        if constexpr (LAST && !INCR) {
+        if constexpr (L::STAGE_L) {
             tma_load<NDIM>(base + L::LT(b), C.tm_l, cn, bar);
-            if (reads_v) tma_load<NDIM>(base + L::VN(b), C.tm_vn, cn, bar);
+            if constexpr (!INCR) {
+                if (reads_v) tma_load<NDIM>(base + L::VN(b), C.tm_vn, cn, bar);
+            }
         }
     };
 
@@ -710,7 +715,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
                 tensormap_acquire(C.tm_win);
                 if (INCR) tensormap_acquire(C.tm_lo);
                 if (has_d) tensormap_acquire(C.tm_d);
-                if (LAST && !INCR) tensormap_acquire(C.tm_l);
+                if (L::STAGE_L) tensormap_acquire(C.tm_l);
                 if (LAST && !INCR && reads_v) tensormap_acquire(C.tm_vn);
             }
             loaded = inst;
@@ -1181,7 +1186,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2)
 #pragma unroll
                         for (int i = 0; i < 4; ++i) lo[i] = q.v[i];
                     }
-                    const Q4<T> lt = ldg4(C.l + gidx);  // l (its pad columns are never used)
+                    Q4<T> lt;  // l at the run's nodes
+                    if constexpr (L::STAGE_L)
+                        lt = ld4(reinterpret_cast<const T*>(sb + L::LT(buf)) + ry * TX + 4 * grp);
+                    else
+                        lt = ldg4(C.l + gidx);  // (its pad columns are never used)
                     T nh[4], nl[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
