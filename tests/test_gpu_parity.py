@@ -53,10 +53,19 @@ def oracle_traj(orc, gd, dyn, l, scheme, rk, steps, cfl=0.5, k=None):
     return P, alpha, dt, out
 
 
+def _di_rect(ny, nx, dmax=0.1):
+    gd = W.grid([ny, nx], [-2.0, -2.0], [2.0, 2.0])
+    return gd, W.double_integrator(dmax=dmax), W.target_strip(gd, 0, 1.0)
+
+
 CASES = [
     # (name, grid dict, dyn, l)
     ("di101", *W.di_config(101)),
     ("di_dist_ragged", *W.di_config(37, dmax=0.2)),
+    # 2 x 2 whole 31 x 32 tiles, rows exactly 8-aligned (no padding)
+    ("exact_tiles_62x64", *_di_rect(62, 64)),
+    # one node row / column into a second tile, rows padded 33 -> 40
+    ("one_past_32x33", *_di_rect(32, 33)),
 ]
 
 
