@@ -308,6 +308,18 @@ def main():
                 "peak_source": "derived from unit counts at 2070 MHz max SM clock"
                                if prec == "f32" else "GB300 datasheet FP64 rate"}
 
+    # Each stage kernel alone between two CUDA events on this stream
+    # (hji_stage_times: 300 steps from V0 = l, after the timed region): the
+    # kernel durations without the gaps between graph launches and the
+    # host's convergence checks that the timed-region average includes.
+    st_ms = g.stage_times(l_dev, steps=300, **{k: v for k, v in SOLVE.items()
+                                                if k in ("scheme", "rk", "cfl")})
+    ev_ms = statistics.mean(st_ms)
+    ev_tflops = flops / (ev_ms * 1e-3) / 1e12
+    roofline["event_timed"] = {"stage_ms": st_ms, "achieved": ev_tflops, "frac": ev_tflops / peak,
+                               "note": "mean of the three stage kernels, each timed alone "
+                                       "between two CUDA events (300 steps)"}
+
     line = {"metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -418,6 +430,8 @@ def run_hbm_workload(args, hji, torch, dist, rank, world, local_rank):
                        "l2": "inputs larger than L2"},
             "e2e": None, "gpu_launches": res["launches"], "roofline": res["roofline"],
             "clocks": res["clocks"]}
+    if res.get("stage_kernels"):
+        line["stage_kernels"] = res["stage_kernels"]
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -460,6 +474,17 @@ def serving(hji, torch, duration=6.0, rate=50.0, time_cap=90.0):
                 "mix": "50% quad4d (31..61^4), 50% double integrator (201..1001^2); mass x "
                        "U[1,1.5] or |d| ~ U[0,0.3]"})
     return out
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# each ENO2 stage kernel in an ncu capture of the HBM-bound marches (the
+# kernels as they are now).
+DRAM_BYTES_PER_LAUNCH = {
+    ("di_8192^2", "first_stage"): 0.546188e9 + 0.241354e9,
+    ("di_8192^2", "fused_last_stage"): 1.202314e9 + 0.509869e9,
+    ("quad4d_61^4", "first_stage"): 121.153e6 + 39.843e6,
+    ("quad4d_61^4", "fused_last_stage"): 256.508e6 + 97.690e6,
+}
 
 
 def _measured_hbm():
@@ -526,6 +551,17 @@ def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=N
             upd += sum(int(np.prod(gd["n"])) * s["steps"] for gd, s in zip(gds, sts))
             launches += max(s["kernel_launches"] for s in sts)
         clk = clocks.stop() if clocks is not None else None
+        stage = None
+        if len(grids) == 1:
+            # Each of the two stage kernels alone between two CUDA events
+            # (20 steps from V0 = l): stage 1 moves 12 B per node, the fused
+            # last stage (min(l), max|dV|) 24 B.
+            sms = grids[0].stage_times(ldev[0], steps=20, scheme="eno2", rk=2, cfl=0.5)
+            stage = {}
+            for key, t, b in (("first_stage", sms[0], 12), ("fused_last_stage", sms[1], 24)):
+                a = b * cells / (t * 1e-3) / 1e9
+                stage[key] = {"ms": t, "bytes_per_node": b, "achieved": a, "frac": a / peak,
+                              "traffic": DRAM_BYTES_PER_LAUNCH.get((name, key))}
         gbs = upd * bytes_per_update / (ms * 1e-3) / 1e9
         out[name] = {"nodes": cells, "steps": steps, "ms": ms / repeats, "tile_shape": ["31x32", "15x64", "63x16"][tuned],
                      "cell_updates_per_s": upd / (ms * 1e-3), "ms_total": ms,
@@ -534,7 +570,8 @@ def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=N
                                   "frac": gbs / peak, "peak_source": src,
                                   "bytes_per_node_step": bytes_per_update, "traffic": None,
                                   "note": "whole-march time (set-up, init and 50 steps of "
-                                          "2 stage launches) in the denominator"}}
+                                          "2 stage launches) in the denominator"},
+                     "stage_kernels": stage}
         for g in grids:
             g.close()
     return out

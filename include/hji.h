@@ -286,6 +286,21 @@ const char* hji_engine_last_error(hji_engine e);
 hji_status hji_autotune(hji_grid g, const void* l, int ptr_is_device, const hji_solve_opts* o,
                         int steps, void* cuda_stream, int* chosen, double* ms_per_step);
 
+/* Per-stage kernel durations (the paper has no counterpart; a measurement aid
+ * for the stage kernels of the time march of Sec. II-B).  Runs `steps` (1..4096)
+ * steps of the march from V0 = l with o's scheme, RK order, CFL and tile
+ * shape (o's tol, horizon, max_steps, check_every and init are ignored),
+ * launching each RK stage kernel on its own between two CUDA events on
+ * cuda_stream instead of inside a graph, and writes the mean duration in
+ * milliseconds of RK stage i's kernel to ms_per_stage[i] (rk_order entries,
+ * caller-owned; entry rk_order-1 is the last stage, fused with min(., l) of
+ * Eq. (7)-(8) and the max|dV| reduction).  The kernels are those of
+ * hji_solve, so the grid's value afterwards equals that of hji_solve with
+ * tol = 0 and max_steps = steps.  Synchronous.  Errors: as hji_solve, and
+ * HJI_E_INVALID for steps out of range or ms_per_stage NULL. */
+hji_status hji_stage_times(hji_grid g, const void* l, int ptr_is_device, const hji_solve_opts* o,
+                           int steps, void* cuda_stream, double* ms_per_stage);
+
 /* Self-test of the bounded waits inside the stage kernels (the paper has no
  * counterpart).  Every wait of a stage kernel on a TMA copy gives up after a
  * time limit and the kernel records HJI_E_TIMEOUT for the instance, instead

@@ -35,7 +35,7 @@ EXPORTS = ["hji_grid_create", "hji_grid_destroy", "hji_dynamics_set", "hji_solve
            "hji_status_string", "hji_last_error", "hji_solve_noalloc", "hji_noalloc_last_error",
            "hji_engine_create", "hji_engine_submit", "hji_engine_step", "hji_engine_poll",
            "hji_engine_destroy", "hji_engine_last_error", "hji_autotune",
-           "hji_selftest_bounded_wait"]
+           "hji_stage_times", "hji_selftest_bounded_wait"]
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -131,6 +131,8 @@ def load(build_if_missing=False):
     lib.hji_engine_last_error.argtypes = [vp]
     lib.hji_engine_last_error.restype = ctypes.c_char_p
     lib.hji_selftest_bounded_wait.argtypes = [ctypes.c_int64, vp]
+    lib.hji_stage_times.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(hji_solve_opts),
+                                    ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double)]
     for name in EXPORTS:
         if name not in ("hji_status_string", "hji_last_error", "hji_noalloc_last_error",
                         "hji_engine_last_error"):
@@ -188,6 +190,10 @@ def hji_noalloc_last_error():
 
 def hji_autotune(g, l, ptr_is_device, opts, steps, stream, chosen, ms_per_step):
     return load().hji_autotune(g, l, ptr_is_device, opts, steps, stream, chosen, ms_per_step)
+
+
+def hji_stage_times(g, l, ptr_is_device, opts, steps, stream, ms_per_stage):
+    return load().hji_stage_times(g, l, ptr_is_device, opts, steps, stream, ms_per_stage)
 
 
 def hji_engine_create(ndim, prec, opts, max_slots, budget_bytes, stream, out):
@@ -395,6 +401,18 @@ class Grid:
         _check(hji_autotune(self._h, lp, ldev, ctypes.byref(o), int(steps), self._stream(stream),
                             ctypes.byref(chosen), ms), self._h)
         return chosen.value, list(ms)
+
+    def stage_times(self, l, steps=20, stream=None, **opts):
+        """hji_stage_times: march `steps` steps from V0 = l launching each RK
+        stage kernel between two CUDA events; returns the mean kernel
+        duration in ms of each stage (the last entry is the fused last
+        stage)."""
+        lp, ldev, keep = self._ptr(l)
+        o = solve_opts(**opts)
+        ms = (ctypes.c_double * 3)()
+        _check(hji_stage_times(self._h, lp, ldev, ctypes.byref(o), int(steps), self._stream(stream), ms),
+               self._h)
+        return list(ms)[:o.rk_order]
 
     def take_value(self, other, stream=None):
         """Make `other`'s current value this grid's resident value (device-side

@@ -127,7 +127,7 @@ struct hji_grid_s {
     std::string err;
     // Graph cache for single-grid solves.
     cudaGraphExec_t graph = nullptr;
-    long long graph_key[7] = {0, 0, 0, 0, 0, 0, 0};
+    long long graph_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     cudaStream_t cap_stream = nullptr;
 };
 
@@ -147,7 +147,7 @@ struct hji_engine_s {
     size_t tiles_cap = 0;
     int* h_counts = nullptr;          // pinned mirror of d_counts
     cudaGraphExec_t graph = nullptr;
-    int grid = 0;
+    int grid[2] = {0, 0};  // CTAs of the stage launches (non-last, last)
     int variant = 0;
     cudaEvent_t ev = nullptr;
     bool inflight = false;
@@ -282,14 +282,12 @@ hji::StageLauncher launcher(bool f32, int ndim, int scheme, bool last, int varia
                : hji::stage_launcher_f64(ndim, scheme, last, variant);
 }
 
-int stage_grid(bool f32, int ndim, int scheme, long long total_tiles, int variant) {
-    int per_sm = 1;
-    for (int last = 0; last < 2; ++last) {
-        const int b = f32 ? hji::stage_max_blocks_f32(ndim, scheme, last, variant)
-                          : hji::stage_max_blocks_f64(ndim, scheme, last, variant);
-        per_sm = last == 0 ? b : (b < per_sm ? b : per_sm);
-    }
-    long long g = (long long)num_sms() * per_sm;
+// CTAs of one stage launch: as many as fit on every SM at once (each stage
+// kernel has its own occupancy), at most one per tile.
+int stage_grid(bool f32, int ndim, int scheme, long long total_tiles, int variant, bool last) {
+    const int b = f32 ? hji::stage_max_blocks_f32(ndim, scheme, last, variant)
+                      : hji::stage_max_blocks_f64(ndim, scheme, last, variant);
+    long long g = (long long)num_sms() * b;
     if (g > total_tiles) g = total_tiles;
     return g < 1 ? 1 : (int)g;
 }
@@ -297,7 +295,15 @@ int stage_grid(bool f32, int ndim, int scheme, long long total_tiles, int varian
 // ---- tile-shape choices made by hji_autotune, per problem class ----
 std::mutex g_tune_mu;
 std::map<std::vector<long long>, int> g_tune;
-int g_force_variant = -1;  // set only while hji_autotune times a variant
+// Set only while hji_autotune times a variant (on the calling thread).
+thread_local int g_force_variant = -1;
+// Set only while hji_stage_times runs its march (on the calling thread):
+// where the per-stage kernel durations go.
+struct StageTimer {
+    double ms[3];
+    int ns;
+};
+thread_local StageTimer* g_stage_timer = nullptr;
 
 int size_bucket(long long cells) {
     int b = 0;
@@ -440,7 +446,7 @@ hji_status make_desc(hji_grid g, const hji_solve_opts* o, int* active, int varia
 
 // Capture `steps` steps of the march (all RK stages) into a graph.
 hji_status capture_chunk(hji_grid g, cudaStream_t cap, bool f32, int ndim, int scheme, int rk,
-                         int steps, const hji::StageArgs& base, int grid, int variant,
+                         int steps, const hji::StageArgs& base, const int* grid, int variant,
                          cudaGraphExec_t* out) {
     StagePlan plan[3];
     const int ns = rk_plan(rk, plan);
@@ -461,7 +467,7 @@ hji_status capture_chunk(hji_grid g, cudaStream_t cap, bool f32, int ndim, int s
             a.aVf = (float)plan[i].aV;
             a.aEf = (float)plan[i].aE;
             a.reads_v = plan[i].aV != 0.0 ? 1 : 0;
-            e = L[i](a, grid, cap);
+            e = L[i](a, grid[plan[i].last ? 1 : 0], cap);
         }
     }
     cudaGraph_t graph = nullptr;
@@ -475,6 +481,56 @@ hji_status capture_chunk(hji_grid g, cudaStream_t cap, bool f32, int ndim, int s
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(g, e, "cudaGraphInstantiate");
     return HJI_OK;
+}
+
+// The march of hji_stage_times: o->max_steps steps, each stage kernel
+// launched on its own between two events (no graph, no convergence check),
+// every event recorded before one synchronisation; the mean duration of each
+// RK stage's kernel goes to T.
+cudaError_t timed_march(const hji_solve_opts* o, bool f32, int ndim, const hji::StageArgs& base,
+                        const int* grid, int variant, cudaStream_t s, StageTimer* T) {
+    StagePlan plan[3];
+    const int ns = rk_plan(o->rk_order, plan);
+    hji::StageLauncher Lk[3];
+    for (int i = 0; i < ns; ++i) {
+        Lk[i] = launcher(f32, ndim, o->scheme, plan[i].last, variant);
+        if (!Lk[i]) return cudaErrorInvalidValue;
+    }
+    const int steps = o->max_steps;
+    std::vector<cudaEvent_t> ev(2 * (size_t)ns * steps, nullptr);
+    cudaError_t e = cudaSuccess;
+    size_t made = 0;
+    for (; made < ev.size() && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+    if (e != cudaSuccess) --made;
+    for (int st = 0; st < steps && e == cudaSuccess; ++st) {
+        for (int i = 0; i < ns && e == cudaSuccess; ++i) {
+            hji::StageArgs a = base;
+            a.stage_in = plan[i].in;
+            a.stage_out = plan[i].out;
+            a.aV = plan[i].aV;
+            a.aE = plan[i].aE;
+            a.aVf = (float)plan[i].aV;
+            a.aEf = (float)plan[i].aE;
+            a.reads_v = plan[i].aV != 0.0 ? 1 : 0;
+            const size_t k = 2 * ((size_t)st * ns + i);
+            e = cudaEventRecord(ev[k], s);
+            if (e == cudaSuccess) e = Lk[i](a, grid[plan[i].last ? 1 : 0], s);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[k + 1], s);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int i = 0; i < 3; ++i) T->ms[i] = 0.0;
+    T->ns = ns;
+    for (int st = 0; st < steps && e == cudaSuccess; ++st) {
+        for (int i = 0; i < ns && e == cudaSuccess; ++i) {
+            const size_t k = 2 * ((size_t)st * ns + i);
+            float ms = 0.0f;
+            e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            T->ms[i] += ms / steps;
+        }
+    }
+    for (size_t i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+    return e;
 }
 
 // The march shared by hji_solve (count == 1) and hji_batch_solve.
@@ -622,14 +678,18 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
 
     // The march: graphs of `chunk` steps, one in flight ahead of the check.
     const int chunk = o->check_every > 0 ? o->check_every : 32;
-    const int grid = stage_grid(f32, ndim, o->scheme, total_tiles, variant);
+    const int grid[2] = {stage_grid(f32, ndim, o->scheme, total_tiles, variant, false),
+                         stage_grid(f32, ndim, o->scheme, total_tiles, variant, true)};
     hji::StageArgs base{d_desc, d_tiles, d_ntiles, 0, 0, 0.0, 0.0, 0.0f, 0.0f, 0};
     cudaGraphExec_t exec = nullptr;
     // The graph's kernels read descriptors, tile list and its length from the
     // leader's scratch, so it stays valid while those buffers and the launch
     // shape (scheme, RK order, chunk, grid, tile shape) are unchanged.
-    const long long key[7] = {(long long)o->scheme, o->rk_order, chunk, grid, variant, ndim, f32 ? 1 : 0};
-    if (g0->graph && std::memcmp(key, g0->graph_key, sizeof(key)) == 0) {
+    const long long key[8] = {(long long)o->scheme, o->rk_order, chunk, grid[0], grid[1], variant, ndim,
+                              f32 ? 1 : 0};
+    if (g_stage_timer) {
+        // the timed march launches its stages one by one
+    } else if (g0->graph && std::memcmp(key, g0->graph_key, sizeof(key)) == 0) {
         exec = g0->graph;
     } else {
         drop_graph();
@@ -639,30 +699,38 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
         g0->graph = exec;
         std::memcpy(g0->graph_key, key, sizeof(key));
     }
-    int* h_active = g0->h_active;  // two pinned slots
-    cudaEvent_t ev[2];
-    cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
-    cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
-    e = cudaSuccess;
-    long long graphs = 0;
-    for (long long it = 0;; ++it) {
-        ++graphs;
-        e = cudaGraphLaunch(exec, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_active[it & 1], d_active, sizeof(int), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[it & 1], s);
-        if (e != cudaSuccess) break;
-        if (it > 0) {
-            e = cudaEventSynchronize(ev[(it - 1) & 1]);
+    long long stage_launches = 0;
+    if (g_stage_timer) {
+        e = timed_march(o, f32, ndim, base, grid, variant, s, g_stage_timer);
+        stage_launches = (long long)o->max_steps * o->rk_order;
+        if (e != cudaSuccess) return cuda_fail(g0, e, "timed march");
+    } else {
+        int* h_active = g0->h_active;  // two pinned slots
+        cudaEvent_t ev[2];
+        cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+        e = cudaSuccess;
+        long long graphs = 0;
+        for (long long it = 0;; ++it) {
+            ++graphs;
+            e = cudaGraphLaunch(exec, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&h_active[it & 1], d_active, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[it & 1], s);
             if (e != cudaSuccess) break;
-            if (h_active[(it - 1) & 1] <= 0) break;
+            if (it > 0) {
+                e = cudaEventSynchronize(ev[(it - 1) & 1]);
+                if (e != cudaSuccess) break;
+                if (h_active[(it - 1) & 1] <= 0) break;
+            }
         }
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaEventDestroy(ev[0]);
-    cudaEventDestroy(ev[1]);
-    if (e != cudaSuccess) {
-        cleanup();
-        return cuda_fail(g0, e, "march");
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        stage_launches = graphs * (long long)chunk * o->rk_order;
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_fail(g0, e, "march");
+        }
     }
     for (int i = 0; i < count; ++i) {
         e = cudaMemcpyAsync(grids[i]->h_state, grids[i]->state, sizeof(InstState), cudaMemcpyDeviceToHost, s);
@@ -699,7 +767,7 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
             o_.converged = S.converged;
             long long setup = 0;
             for (int j = 0; j < count; ++j) setup += 2 + (grids[j]->dyn.nterms > 0 ? 1 : 0);
-            o_.kernel_launches = setup + graphs * (long long)chunk * o->rk_order;
+            o_.kernel_launches = setup + stage_launches;
         }
     }
     return result;
@@ -950,7 +1018,8 @@ hji_status hji_engine_create(int ndim, hji_precision prec, const hji_solve_opts*
         return efail(nullptr, HJI_E_NOMEM, "engine allocation failed");
     }
     e->variant = pick_variant(prec, ndim, o, 1ll << 20);
-    e->grid = stage_grid(prec == HJI_F32, ndim, o->scheme, 1ll << 40, e->variant);
+    for (int last = 0; last < 2; ++last)
+        e->grid[last] = stage_grid(prec == HJI_F32, ndim, o->scheme, 1ll << 40, e->variant, last != 0);
     *out = e;
     return HJI_OK;
 }
@@ -1192,6 +1261,30 @@ hji_status hji_autotune(hji_grid g, const void* l, int ptr_is_device, const hji_
         g_tune[tune_key(g->prec, g->ndim, o, size_bucket(g->ncells))] = best;
     }
     if (chosen) *chosen = best;
+    return HJI_OK;
+}
+
+hji_status hji_stage_times(hji_grid g, const void* l, int ptr_is_device, const hji_solve_opts* o,
+                           int steps, void* cuda_stream, double* ms_per_stage) {
+    if (!g) return fail(nullptr, HJI_E_INVALID, "grid is NULL");
+    hji_status st = validate_opts(g, o);
+    if (st != HJI_OK) return st;
+    if (steps < 1 || steps > 4096) return fail(g, HJI_E_INVALID, "steps must be 1..4096");
+    if (!ms_per_stage) return fail(g, HJI_E_INVALID, "ms_per_stage is NULL");
+    hji_solve_opts t = *o;
+    t.tol = 0.0;
+    t.horizon = 0.0;
+    t.max_steps = steps;
+    t.check_every = steps;
+    t.init = HJI_INIT_STANDARD;
+    StageTimer T{};
+    g_stage_timer = &T;
+    const void* la[1] = {l};
+    const void* ka[1] = {nullptr};
+    hji_status r = run(1, &g, la, ka, ptr_is_device, &t, (cudaStream_t)cuda_stream, nullptr);
+    g_stage_timer = nullptr;
+    if (r != HJI_OK && r != HJI_E_NOT_CONVERGED) return r;
+    for (int i = 0; i < T.ns; ++i) ms_per_stage[i] = T.ms[i];
     return HJI_OK;
 }
 

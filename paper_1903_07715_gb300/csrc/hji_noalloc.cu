@@ -280,7 +280,10 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
         ins[1] = 1; outs[1] = 2; aV[1] = 0.75; aE[1] = 0.25;
         ins[2] = 2; outs[2] = 3; aV[2] = 1.0 / 3.0; aE[2] = 2.0 / 3.0;
     }
-    int per_sm = 1 << 30, sms = 1;
+    int sms = 1;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return ncuda(e, "cudaDeviceGetAttribute");
+    long long grid[3];  // per stage: as many CTAs as fit on every SM, at most one per tile
     for (int i = 0; i < ns; ++i) {
         const bool last = i == ns - 1;
         L[i] = f32 ? hji::stage_launcher_f32(ndim, o->scheme, last)
@@ -288,13 +291,10 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
         if (!L[i]) return nfail(HJI_E_INVALID, "no kernel for this ndim/scheme");
         const int b = f32 ? hji::stage_max_blocks_f32(ndim, o->scheme, last)
                           : hji::stage_max_blocks_f64(ndim, o->scheme, last);
-        per_sm = b < per_sm ? b : per_sm;
+        grid[i] = (long long)sms * b;
+        if (grid[i] > ntiles) grid[i] = ntiles;
+        if (grid[i] < 1) grid[i] = 1;
     }
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return ncuda(e, "cudaDeviceGetAttribute");
-    long long grid = (long long)sms * per_sm;
-    if (grid > ntiles) grid = ntiles;
-    if (grid < 1) grid = 1;
     const int chunk = o->check_every > 0 ? o->check_every : 32;
     long long launches = 2 + (dyn->nterms > 0 ? 1 : 0) + 1;
     for (;;) {
@@ -302,7 +302,7 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
             for (int i = 0; i < ns && e == cudaSuccess; ++i) {
                 hji::StageArgs a{d_desc, d_tiles, d_ints + 1, ins[i], outs[i], aV[i], aE[i],
                                  (float)aV[i], (float)aE[i], aV[i] != 0.0 ? 1 : 0};
-                e = L[i](a, (int)grid, s);
+                e = L[i](a, (int)grid[i], s);
                 ++launches;
             }
         }

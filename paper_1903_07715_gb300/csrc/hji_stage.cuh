@@ -618,8 +618,15 @@ struct TileWalk {
     }
 };
 
+// Resident CTAs per SM the register budget is cut for: FP32 1-D/2-D stages
+// four (64 registers), FP32 3-D/4-D and FP64 two.  (Five for the 2-D ENO2
+// stages before the last fits 48 registers without spills, but the tighter
+// budget costs more instructions than the fifth CTA hides.)
+template <typename T, int NDIM, int SCHEME, bool LAST>
+constexpr int kMinBlocks = sizeof(T) != 4 ? 2 : NDIM > 2 ? 2 : 4;
+
 template <typename T, int NDIM, int SCHEME, bool LAST, int V>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NDIM <= 2 ? 4 : 2) : 2)
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
     stage_kernel(const StageArgs a) {
     using L = StageSmem<T, NDIM, SCHEME, LAST, V>;
     constexpr int G = L::G, TY = L::TY, TX = L::TX, GROUPS = L::GROUPS;
