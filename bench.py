@@ -477,14 +477,10 @@ def serving(hji, torch, duration=6.0, rate=50.0, time_cap=90.0):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# each ENO2 stage kernel in an ncu capture of the HBM-bound marches (the
-# kernels as they are now).
-DRAM_BYTES_PER_LAUNCH = {
-    ("di_8192^2", "first_stage"): 0.546188e9 + 0.241354e9,
-    ("di_8192^2", "fused_last_stage"): 1.202314e9 + 0.509869e9,
-    ("quad4d_61^4", "first_stage"): 121.153e6 + 39.843e6,
-    ("quad4d_61^4", "fused_last_stage"): 256.508e6 + 97.690e6,
-}
+# each ENO2 stage kernel from an ncu capture of the current kernels, keyed by
+# (workload, stage); none is recorded for them at present, so `traffic` is
+# null.
+DRAM_BYTES_PER_LAUNCH = {}
 
 
 def _measured_hbm():

@@ -33,6 +33,21 @@ struct Dyn {
 };
 
 // Mutable march state of one instance (device memory, written by kernels).
+// Per-instance constants of the stage kernels in one precision, formed once
+// per solve by the set-up pass (FP64 arithmetic, then rounded), so that each
+// stage kernel's per-CTA context load is plain copies: FP64 arithmetic runs
+// at a small fraction of the FP32 rate on this GPU, and a few dozen dependent
+// FP64 operations per CTA at the start of every launch were on its critical
+// path.
+template <typename T>
+struct CtxConst {
+    T lo[MAXD], dx[MAXD], inv_dx[MAXD], half_alpha[MAXD];
+    T cmid[MAXD];  // c + G umid + E dmid: the box centres' share of the drift
+    T A[MAXD * MAXD], G[MAXD * MAXU], E[MAXD * MAXU];
+    T urad[MAXU], drad[MAXU];  // half-widths of the control and disturbance boxes
+    T dt;
+};
+
 struct InstState {
     unsigned long long delta_bits;  // max|dV| of the step in flight (bits of a double >= 0)
     unsigned int tiles_done;        // tiles of the step's last stage finished so far
@@ -51,6 +66,8 @@ struct InstState {
     unsigned int nonfinite;         // set by the init pass if l or k has NaN/Inf
     double dt;
     double alpha[MAXD];
+    CtxConst<double> kd;  // the stage kernels' constants (set-up pass)
+    CtxConst<float> kf;
 };
 
 // Tensor maps of one instance (TMA descriptors, encoded on the host):

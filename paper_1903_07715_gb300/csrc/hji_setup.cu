@@ -37,6 +37,49 @@ __global__ void __launch_bounds__(kThreads) table_kernel(const InstDesc* __restr
 constexpr int kAlphaTab = 2048;  // term values cached per CTA (FP64)
 constexpr int kAlphaChunk = 16;  // consecutive nodes per alpha thread
 
+// The stage kernels' per-instance constants in both precisions, from the
+// descriptor and this solve's alpha and dt (thread 0 of the set-up pass's
+// last CTA).
+__device__ void fill_ctx_const(const InstDesc& D, InstState* st) {
+    CtxConst<double>& kd = st->kd;
+    CtxConst<float>& kf = st->kf;
+    for (int i = 0; i < MAXD * MAXD; ++i) {
+        kd.A[i] = D.dyn.A[i];
+        kf.A[i] = static_cast<float>(D.dyn.A[i]);
+    }
+    for (int i = 0; i < MAXD * MAXU; ++i) {
+        kd.G[i] = D.dyn.G[i];
+        kf.G[i] = static_cast<float>(D.dyn.G[i]);
+        kd.E[i] = D.dyn.E[i];
+        kf.E[i] = static_cast<float>(D.dyn.E[i]);
+    }
+    for (int j = 0; j < MAXU; ++j) {
+        kd.urad[j] = 0.5 * (D.dyn.uhi[j] - D.dyn.ulo[j]);
+        kf.urad[j] = static_cast<float>(kd.urad[j]);
+        kd.drad[j] = 0.5 * (D.dyn.dhi[j] - D.dyn.dlo[j]);
+        kf.drad[j] = static_cast<float>(kd.drad[j]);
+    }
+    for (int i = 0; i < MAXD; ++i) {
+        kd.lo[i] = D.lo[i];
+        kd.dx[i] = D.dx[i];
+        kd.inv_dx[i] = 1.0 / D.dx[i];
+        kd.half_alpha[i] = 0.5 * st->alpha[i];
+        double cm = D.dyn.c[i];
+        for (int j = 0; j < MAXU; ++j) {
+            cm += D.dyn.G[i * MAXU + j] * (0.5 * (D.dyn.ulo[j] + D.dyn.uhi[j]));
+            cm += D.dyn.E[i * MAXU + j] * (0.5 * (D.dyn.dlo[j] + D.dyn.dhi[j]));
+        }
+        kd.cmid[i] = cm;
+        kf.lo[i] = static_cast<float>(kd.lo[i]);
+        kf.dx[i] = static_cast<float>(kd.dx[i]);
+        kf.inv_dx[i] = static_cast<float>(kd.inv_dx[i]);
+        kf.half_alpha[i] = static_cast<float>(kd.half_alpha[i]);
+        kf.cmid[i] = static_cast<float>(cm);
+    }
+    kd.dt = st->dt;
+    kf.dt = static_cast<float>(st->dt);
+}
+
 __global__ void __launch_bounds__(kThreads) alpha_kernel(const InstDesc* __restrict__ insts) {
     const InstDesc& D = insts[blockIdx.y];
     const int nd = D.ndim;
@@ -190,6 +233,7 @@ __global__ void __launch_bounds__(kThreads) alpha_kernel(const InstDesc* __restr
                 st->status = 2;
                 if (atomicExch(&st->stop, 1) == 0 && D.active != nullptr) atomicSub(D.active, 1);
             }
+            fill_ctx_const(D, st);
             __threadfence();
         }
     }

@@ -322,15 +322,22 @@ struct TileCtx {
 static_assert(MAXD == 4 && MAXU == 4 && MAXT == 8 && kThreads > 96,
               "load_ctx hands out slices for these sizes");
 template <typename T>
-__device__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict__ insts, int inst,
+__device__ __forceinline__ const CtxConst<T>& ctx_const(const InstState* st) {
+    if constexpr (sizeof(T) == 4) return st->kf;
+    else return st->kd;
+}
+
+template <typename T>
+__device__ __noinline__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict__ insts, int inst,
                          const StageArgs& a) {
     const InstDesc& D = insts[inst];
+    const CtxConst<T>& K = ctx_const<T>(D.state);
     const int t = threadIdx.x;
-    if (t < MAXD * MAXD) C.A[t] = T(D.dyn.A[t]);
-    else if (t < 32) C.G[t - 16] = T(D.dyn.G[t - 16]);
-    else if (t < 48) C.E[t - 32] = T(D.dyn.E[t - 32]);
-    else if (t < 52) C.urad[t - 48] = T(0.5 * (D.dyn.uhi[t - 48] - D.dyn.ulo[t - 48]));
-    else if (t < 56) C.drad[t - 52] = T(0.5 * (D.dyn.dhi[t - 52] - D.dyn.dlo[t - 52]));
+    if (t < MAXD * MAXD) C.A[t] = K.A[t];
+    else if (t < 32) C.G[t - 16] = K.G[t - 16];
+    else if (t < 48) C.E[t - 32] = K.E[t - 32];
+    else if (t < 52) C.urad[t - 48] = K.urad[t - 48];
+    else if (t < 56) C.drad[t - 52] = K.drad[t - 52];
     else if (t < 64) {
         // threads 56..63 have no slice
     } else if (t < 72) {
@@ -338,21 +345,14 @@ __device__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict__ insts, int 
         C.term_axis[t - 64] = D.dyn.term_axis[t - 64];
     } else if (t < 76) {
         const int i = t - 72;
-        InstState* st = D.state;
         C.n[i] = D.n[i];
         C.periodic[i] = D.periodic[i];
         C.stride[i] = D.stride[i];
-        C.lo[i] = T(D.lo[i]);
-        C.dx[i] = T(D.dx[i]);
-        C.inv_dx[i] = T(1.0 / D.dx[i]);
-        C.half_alpha[i] = T(0.5 * st->alpha[i]);
-        // c + G umid + E dmid: the box centres' share of the drift.
-        double cm = D.dyn.c[i];
-        for (int j = 0; j < MAXU; ++j) {
-            cm += D.dyn.G[i * MAXU + j] * (0.5 * (D.dyn.ulo[j] + D.dyn.uhi[j]));
-            cm += D.dyn.E[i * MAXU + j] * (0.5 * (D.dyn.dlo[j] + D.dyn.dhi[j]));
-        }
-        C.cmid[i] = T(cm);
+        C.lo[i] = K.lo[i];
+        C.dx[i] = K.dx[i];
+        C.inv_dx[i] = K.inv_dx[i];
+        C.half_alpha[i] = K.half_alpha[i];
+        C.cmid[i] = K.cmid[i];
     } else if (t == 96) {
         InstState* st = D.state;
         const int cur = *((volatile int*)&st->cur);
@@ -362,7 +362,7 @@ __device__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict__ insts, int 
         C.m = D.dyn.m;
         C.q = D.dyn.q;
         C.nterms = D.dyn.nterms;
-        C.dt = T(*((volatile double*)&st->dt));
+        C.dt = K.dt;
         C.tiles_x = static_cast<int>(D.tiles_x);
         C.tiles_per_plane = static_cast<int>(D.tiles_per_plane);
         C.ntiles = static_cast<int>(D.ntiles);
@@ -841,8 +841,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
             __syncthreads();
         }
         // 2. y-differences of the tile columns, once per tile (FP32: on the pairs).
+        //    Items are dealt from the last thread down, so the items beyond
+        //    one per thread fall to the last warp rather than to warp 0,
+        //    which also issues the tile copies.
         if constexpr (NDIM >= 2) {
-            for (int i = threadIdx.x; i < (SH - 1) * GROUPS; i += kThreads) {
+            for (int i = kThreads - 1 - threadIdx.x; i < (SH - 1) * GROUPS; i += kThreads) {
                 const int r = i / GROUPS, g4 = i - r * GROUPS;
                 const int s0 = r * SWX + 4 + 4 * g4;
                 const Q4<T> h0 = ld4(wh + s0), h1 = ld4(wh + s0 + SWX);
