@@ -328,8 +328,8 @@ __device__ __forceinline__ const CtxConst<T>& ctx_const(const InstState* st) {
 }
 
 template <typename T>
-__device__ __noinline__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict__ insts, int inst,
-                         const StageArgs& a) {
+__device__ __forceinline__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict__ insts, int inst,
+                                         const StageArgs& a) {
     const InstDesc& D = insts[inst];
     const CtxConst<T>& K = ctx_const<T>(D.state);
     const int t = threadIdx.x;
@@ -394,6 +394,15 @@ __device__ __noinline__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict_
         C.table = static_cast<const T*>(D.table);
         C.table_stride = D.table_stride;
     }
+}
+
+// The same, as a call: the stage kernels keep fewer registers live (the
+// FP32 1-D/2-D ones spill none) when the context load is not inlined, except
+// the FP32 3-D/4-D ones, which spill less with it inlined.
+template <typename T>
+__device__ __noinline__ void load_ctx_call(TileCtx<T>& C, const InstDesc* __restrict__ insts, int inst,
+                                           const StageArgs& a) {
+    load_ctx<T>(C, insts, inst, a);
 }
 
 // Stop an instance once: the thread that flips the flag lowers the
@@ -716,7 +725,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
         const int local = static_cast<int>(entry & 0xFFFFFFFFFFFFull);
         if (inst != loaded) {
             __syncthreads();  // everyone is done with the previous context
-            load_ctx<T>(C, a.insts, inst, a);
+            if constexpr (INCR && NDIM > 2) load_ctx<T>(C, a.insts, inst, a);
+            else load_ctx_call<T>(C, a.insts, inst, a);
             __syncthreads();
             if (threadIdx.x == 0 && !C.stop) {
                 tensormap_acquire(C.tm_win);
