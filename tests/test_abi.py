@@ -78,3 +78,10 @@ def test_product_has_no_oracle_dependency():
 def test_selftest_limit_is_validated_before_device_work(hji_lib):
     assert hji_lib.hji_selftest_bounded_wait(10, None) == hji_lib.HJI_E_INVALID
     assert hji_lib.hji_selftest_bounded_wait(10 ** 10, None) == hji_lib.HJI_E_INVALID
+
+
+def test_stage_times_rejects_null_arguments_before_device_work(hji_lib):
+    ms = (ctypes.c_double * 3)()
+    assert hji_lib.hji_stage_times(None, None, 0, None, 10, None, ms) == hji_lib.HJI_E_INVALID
+    assert "NULL" in hji_lib.hji_last_error(None)
+    assert hji_lib.hji_autotune(None, None, 0, None, 10, None, None, None) == hji_lib.HJI_E_INVALID
