@@ -33,6 +33,8 @@ import workloads as W  # noqa: E402
 
 N_SIDE, DMAX = 1001, 0.2
 SOLVE = dict(scheme="weno5", rk=3, cfl=0.5, tol=1e-6, max_steps=200000, check_every=32)
+WORKLOAD = ("double integrator x1'=x2, x2'=u+d, |u|<=1, |d|<=0.2, 1001x1001 on [-2,2]^2, "
+            "l=1-|x1|, WENO5/RK3, cfl 0.5, tol 1e-6, warm start from the d=0 solution")
 # Algorithmic work of one node through one RK stage of WENO5 in 2-D, counted
 # from the textbook formulas (FP operations: +, -, *, /, max, abs):
 #   per axis: 6 differences, 2 x 78 for the two WENO5 reconstructions
@@ -172,8 +174,9 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1000.0 * t_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "double integrator 1001x1001, |d|<=0.2, WENO5/RK3, cfl 0.5, "
-                                   "warm start; each step a bounded 4-step sample"},
+            "config": {"workload": WORKLOAD, "nodes": W.num_cells(W.di_config(N_SIDE, dmax=DMAX)[0]),
+                       "sample": "each step: 4 RK3 steps of the march by the FP64 oracle on the "
+                                 "host cores"},
             "cpu_baseline": {"value": value, "unit": "cell-updates/s",
                              "cores": samples[-1]["cores"], "kind": "oracle",
                              "sample": samples[-1]["sample"]},
@@ -324,9 +327,7 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": prec, "data": "synthetic",
-            "config": {"workload": "double integrator x1'=x2, x2'=u+d, |u|<=1, |d|<=0.2, "
-                                   "1001x1001 on [-2,2]^2, l=1-|x1|, WENO5/RK3, cfl 0.5, "
-                                   "tol 1e-6, warm start from the d=0 solution",
+            "config": {"workload": WORKLOAD,
                        "nodes": cells, "steps_per_solve": steps_per_solve,
                        "precision": prec + " storage and stencil, FP64 dt/alpha and max|dV|",
                        "l2": "flushed (512 MB write) before every timed solve; the 1001^2 "
