@@ -68,6 +68,7 @@ struct InstState {
     double alpha[MAXD];
     CtxConst<double> kd;  // the stage kernels' constants (set-up pass)
     CtxConst<float> kf;
+    double stop_delta;    // tol + tol_rate dt: a step whose max|dV| is below it converges
 };
 
 // Tensor maps of one instance (TMA descriptors, encoded on the host):

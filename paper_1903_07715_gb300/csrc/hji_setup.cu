@@ -78,6 +78,7 @@ __device__ void fill_ctx_const(const InstDesc& D, InstState* st) {
     }
     kd.dt = st->dt;
     kf.dt = static_cast<float>(st->dt);
+    st->stop_delta = D.tol + D.tol_rate * st->dt;
 }
 
 __global__ void __launch_bounds__(kThreads) alpha_kernel(const InstDesc* __restrict__ insts) {

@@ -309,6 +309,13 @@ struct TileCtx {
     const T* l;
     const T* table;
     long long table_stride;
+    // The last stage's step bookkeeping (finish_step), read at context load:
+    // none of it changes during a launch before the instance's last tile.
+    InstState* state;
+    int* active;
+    double* history;
+    long long history_len, steps0, max_steps;
+    double tau0, dt_d, stop_delta, horizon;
     // TMA descriptors of the fields this stage copies.
     const CUtensorMap* tm_win;   // stencil input (high word)
     const CUtensorMap* tm_lo;    // FP32 low word of V^n
@@ -317,19 +324,22 @@ struct TileCtx {
     const CUtensorMap* tm_vn;    // FP64 V^n at the tile nodes
 };
 
-// Fill the tile context; called by every thread of the CTA (each copies a
-// slice), followed by __syncthreads() at the call site.
-static_assert(MAXD == 4 && MAXU == 4 && MAXT == 8 && kThreads > 96,
-              "load_ctx hands out slices for these sizes");
+// The set-up pass's constants of an instance in precision T.
 template <typename T>
 __device__ __forceinline__ const CtxConst<T>& ctx_const(const InstState* st) {
     if constexpr (sizeof(T) == 4) return st->kf;
     else return st->kd;
 }
 
+// Fill the tile context; called by every thread of the CTA (each copies a
+// slice), followed by __syncthreads() at the call site.  Not inlined: the
+// stage kernels keep fewer registers live across their tile loop (the FP32
+// 1-D/2-D and 4-D ENO2 ones spill none) with the context load as a call.
+static_assert(MAXD == 4 && MAXU == 4 && MAXT == 8 && kThreads > 96,
+              "load_ctx hands out slices for these sizes");
 template <typename T>
-__device__ __forceinline__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict__ insts, int inst,
-                                         const StageArgs& a) {
+__device__ __noinline__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict__ insts, int inst,
+                                      const StageArgs& a) {
     const InstDesc& D = insts[inst];
     const CtxConst<T>& K = ctx_const<T>(D.state);
     const int t = threadIdx.x;
@@ -393,16 +403,17 @@ __device__ __forceinline__ void load_ctx(TileCtx<T>& C, const InstDesc* __restri
         C.l = static_cast<const T*>(D.l);
         C.table = static_cast<const T*>(D.table);
         C.table_stride = D.table_stride;
+        C.state = st;
+        C.active = D.active;
+        C.history = D.history;
+        C.history_len = D.history_len;
+        C.steps0 = st->steps;
+        C.max_steps = D.max_steps;
+        C.tau0 = st->tau;
+        C.dt_d = st->dt;
+        C.stop_delta = st->stop_delta;
+        C.horizon = D.horizon;
     }
-}
-
-// The same, as a call: the stage kernels keep fewer registers live (the
-// FP32 1-D/2-D ones spill none) when the context load is not inlined, except
-// the FP32 3-D/4-D ones, which spill less with it inlined.
-template <typename T>
-__device__ __noinline__ void load_ctx_call(TileCtx<T>& C, const InstDesc* __restrict__ insts, int inst,
-                                           const StageArgs& a) {
-    load_ctx<T>(C, insts, inst, a);
 }
 
 // Stop an instance once: the thread that flips the flag lowers the
@@ -411,35 +422,46 @@ __device__ inline void stop_instance(const InstDesc& D) {
     if (atomicExch(&D.state->stop, 1) == 0 && D.active != nullptr) atomicSub(D.active, 1);
 }
 
-// Finish one step of an instance: called by the single thread whose tile was
-// the instance's last one in this (last) stage.
-__device__ inline void finish_step(const InstDesc& D) {
-    InstState* st = D.state;
-    __threadfence();
+// Add v to the instance's count of finished tiles with acquire-release order
+// (PTX memory model, GPU scope): the caller's earlier max|dV| reduction is
+// visible before its count, and the thread whose addition completes the
+// count sees every CTA's reduction.
+__device__ __forceinline__ unsigned add_tiles_acq_rel(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// Finish one step of an instance: called by the single thread whose tile
+// count completed the instance's last stage (after add_tiles_acq_rel), with
+// the context it loaded for that instance.  The state it writes is read by
+// later launches and by the host, both after this kernel has ended.
+template <typename T>
+__device__ inline void finish_step(const TileCtx<T>& C) {
+    InstState* st = C.state;
     const double d = __longlong_as_double((long long)atomicAdd(&st->delta_bits, 0ull));
-    const long long steps = st->steps + 1;
-    const double tau = st->tau + st->dt;
+    const long long steps = C.steps0 + 1;
+    const double tau = C.tau0 + C.dt_d;
     st->last_delta = d;
     st->steps = steps;
     st->tau = tau;
-    st->cur ^= 1;
-    if (D.history != nullptr && steps - 1 < D.history_len) D.history[steps - 1] = d;
+    st->cur = C.cur ^ 1;
+    if (C.history != nullptr && steps - 1 < C.history_len) C.history[steps - 1] = d;
     st->delta_bits = 0ull;
     st->tiles_done = 0u;
     bool stop = false;
     if (!(d <= DBL_MAX)) {  // NaN or Inf
         st->status = 1;
         stop = true;
-    } else if (d < D.tol + D.tol_rate * st->dt) {
+    } else if (d < C.stop_delta) {
         st->converged = 1;
         stop = true;
-    } else if (D.horizon > 0.0 && tau >= D.horizon) {
+    } else if (C.horizon > 0.0 && tau >= C.horizon) {
         stop = true;
-    } else if (steps >= D.max_steps) {
+    } else if (steps >= C.max_steps) {
         stop = true;
     }
-    if (stop) stop_instance(D);
-    __threadfence();
+    if (stop && atomicExch(&st->stop, 1) == 0 && C.active != nullptr) atomicSub(C.active, 1);
 }
 
 // ---- TMA tensor copies and their mbarriers ----
@@ -725,8 +747,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
         const int local = static_cast<int>(entry & 0xFFFFFFFFFFFFull);
         if (inst != loaded) {
             __syncthreads();  // everyone is done with the previous context
-            if constexpr (INCR && NDIM > 2) load_ctx<T>(C, a.insts, inst, a);
-            else load_ctx_call<T>(C, a.insts, inst, a);
+            load_ctx<T>(C, a.insts, inst, a);
             __syncthreads();
             if (threadIdx.x == 0 && !C.stop) {
                 tensormap_acquire(C.tm_win);
@@ -1295,13 +1316,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
                     for (int w = 1; w < kThreads / 32; ++w)
                         mt = (red[w] > mt || red[w] != red[w]) ? red[w] : mt;
                     const double m = static_cast<double>(mt);
-                    const InstDesc& D = a.insts[inst];
-                    InstState* st = D.state;
+                    InstState* st = C.state;
                     atomicMax(&st->delta_bits, static_cast<unsigned long long>(__double_as_longlong(m)));
-                    __threadfence();
-                    const unsigned int prev = atomicAdd(&st->tiles_done, static_cast<unsigned int>(run_tiles));
+                    const unsigned int prev = add_tiles_acq_rel(&st->tiles_done, static_cast<unsigned int>(run_tiles));
                     if (prev + static_cast<unsigned int>(run_tiles) == static_cast<unsigned int>(C.ntiles))
-                        finish_step(D);
+                        finish_step(C);
                 }
                 dmax = T(0);
                 run_tiles = 0;
