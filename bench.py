@@ -298,11 +298,13 @@ def main():
         peak = 152 * 128 * 2 * 2070e6 / 1e12
     else:
         peak = 1.25
-    # DRAM bytes per stage launch of this kernel from one ncu capture
-    # (dram__bytes_read.sum + dram__bytes_write.sum, mean of the three RK3
-    # stage launches: 8.1, 12.2 and 16.2 MB, the first touch of each field;
-    # everything else is served by L2).  FP64 was not captured.
-    traffic = 12.16e6 if prec == "f32" else None
+    # DRAM bytes per stage launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    # from an ncu capture of the current stage kernels; none is recorded for
+    # them at present (the last capture, of the kernels before the change to
+    # the last stage's step bookkeeping, gave 8.1, 12.2 and 16.2 MB for the
+    # three RK3 stages: the first touch of each field, everything else served
+    # by L2), so `traffic` is null.
+    traffic = None
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved_tflops / peak, "traffic": traffic,
                 "kernel": "stage_kernel<%s,2,WENO5> (per-stage, 3 per RK3 step)" % prec,
