@@ -162,9 +162,11 @@ typedef struct {
                                 stop point)                                   */
 } hji_solve_stats;
 
-/* March the HJI VI on grid g for target l (grid-shaped) from the init mode
- * in `o`; k is read only for HJI_INIT_USER_K (else may be NULL).  The result
- * stays in the grid (read it with hji_value_get; HJI_INIT_RESIDENT starts
+/* March the HJI VI (Sec. II-B, Eq. (7); min(., l) after every full step,
+ * Eq. (8)) on grid g for target l (grid-shaped) from the init mode in `o`
+ * (V0 = l, Sec. II-B, or the warm start V0 = min(k, l), Sec. III); k is
+ * read only for HJI_INIT_USER_K (else may be NULL).  The result stays in
+ * the grid (read it with hji_value_get; HJI_INIT_RESIDENT starts
  * the next solve from it).  Returns HJI_OK when converged,
  * HJI_E_NOT_CONVERGED when a cap stopped it first (the value is still the
  * last iterate), HJI_E_INVALID for bad options or NaN/Inf in l or k,
@@ -272,8 +274,9 @@ hji_status hji_engine_poll(hji_engine e, int64_t* tags, hji_solve_stats* stats,
 hji_status hji_engine_destroy(hji_engine e);
 const char* hji_engine_last_error(hji_engine e);
 
-/* Tile-shape autotuner.  2-D grids can be marched with HJI_TILE_VARIANTS
- * tile shapes (16x32, 8x32 and 32x32 nodes); this times `steps` steps of a
+/* Tile-shape autotuner (the paper has no counterpart).  2-D grids can be
+ * marched with HJI_TILE_VARIANTS tile shapes (31x32, 15x64 and 63x16 nodes,
+ * rows x columns); this times `steps` steps of a
  * standard march of grid g (dynamics set, target l) with each and remembers
  * the fastest for this precision, ndim, scheme, RK order and grid-size class
  * (log2 of the node count).  Later hji_solve, hji_batch_solve and engines
@@ -315,7 +318,12 @@ hji_status hji_selftest_bounded_wait(int64_t limit_ns, void* cuda_stream);
 /* Grid facts: ndim, n[], and the number of nodes (may be NULL each). */
 hji_status hji_grid_info(hji_grid g, int* ndim, int64_t* n, int64_t* num_nodes);
 
+/* Static text of a status code ("unknown status" for other values). */
 const char* hji_status_string(hji_status s);
+/* The message of the last failed call on grid g; for g NULL, of the last
+ * failed call on this thread that had no grid (hji_grid_create, NULL
+ * arguments, hji_selftest_bounded_wait).  Owned by the library, valid until
+ * the next call that fails the same way. */
 const char* hji_last_error(hji_grid g);
 
 #ifdef __cplusplus
