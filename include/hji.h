@@ -78,15 +78,20 @@ typedef struct {
 
 /* Create a grid of ndim (1..4) axes with n[a] >= 3 nodes on [lo[a], hi[a]]
  * (hi > lo), at most 2^31 - 1 nodes in all, periodic[a] != 0 for a periodic
- * axis (may be NULL), storing V in `prec`.  Allocates the value buffers on
- * the current device.  `alloc` may be NULL; if not, it is copied and must
+ * axis (may be NULL), storing V in `prec`.  The grid is the discretised
+ * state space on which Sec. II-B computes the value function (the standard
+ * initialisation there sets V = l at every grid state; the update of each
+ * grid state after Eq. (8) is the march of hji_solve); node placement and
+ * spacing are stated at the top of this header.  Allocates the value
+ * buffers on the current device.  `alloc` may be NULL; if not, it is copied and must
  * stay callable until hji_grid_destroy.
  * Errors: HJI_E_INVALID (sizes, bounds), HJI_E_NOMEM, HJI_E_CUDA. */
 hji_status hji_grid_create(int ndim, const int64_t* n, const double* lo, const double* hi,
                            const int* periodic, hji_precision prec, const hji_allocator* alloc,
                            hji_grid* out);
 
-/* Release every device buffer of the grid.  NULL is accepted. */
+/* Release every device buffer of the grid.  NULL is accepted.  The paper
+ * has no counterpart (resource management of this C ABI). */
 hji_status hji_grid_destroy(hji_grid g);
 
 typedef enum { HJI_FN_TAN = 0, HJI_FN_SIN = 1, HJI_FN_COS = 2 } hji_fn;
@@ -176,7 +181,9 @@ typedef struct {
 hji_status hji_solve(hji_grid g, const void* l, const void* k, int ptr_is_device,
                      const hji_solve_opts* o, void* cuda_stream, hji_solve_stats* stats);
 
-/* Several grids in one march: every RK stage of every grid is one persistent
+/* Several grids in one march (each grid is the march of Sec. II-B, Eq. (7),
+ * exactly as hji_solve runs it; the paper solves one problem at a time and
+ * has no batched form): every RK stage of every grid is one persistent
  * kernel launch over a shared tile list, captured in CUDA graphs; each grid
  * stops on its own test while the others go on.  All grids must share
  * precision and ndim; l[i], k[i] belong to grids[i] (k may be NULL, or hold
@@ -187,7 +194,10 @@ hji_status hji_batch_solve(int count, hji_grid* grids, const void* const* l,
                            const void* const* k, int ptr_is_device, const hji_solve_opts* o,
                            void* cuda_stream, hji_solve_stats* stats);
 
-/* Copy the grid's current value (grid-shaped, the grid's precision) to out.
+/* Copy the grid's current value (grid-shaped, the grid's precision) to out:
+ * the value function V(x, tau) of Sec. II-B, Eq. (4), at the nodes, which
+ * after a converged solve is the infinite-horizon value V*(x) of Eq. (7)
+ * whose sub-zero level set is the unsafe set (Sec. II-B, after Eq. (5)).
  * Errors: HJI_E_STATE (no value yet), HJI_E_INVALID, HJI_E_CUDA. */
 hji_status hji_value_get(hji_grid g, void* out, int ptr_is_device, void* cuda_stream);
 
@@ -199,14 +209,21 @@ hji_status hji_value_get(hji_grid g, void* out, int ptr_is_device, void* cuda_st
  * NULL otherwise) and v_out (output, grid-shaped, the grid's precision; for
  * HJI_INIT_RESIDENT it also holds the previous value on entry).  Grid,
  * dynamics and options mean what they mean for hji_grid_create,
- * hji_dynamics_set and hji_solve.  Every scratch buffer lives in one static
+ * hji_dynamics_set and hji_solve, with two differences: tile_variant 0
+ * takes the default tile shape (no autotuned choice is consulted), and an
+ * FP32 HJI_INIT_RESIDENT start begins from the float values in v_out alone,
+ * while hji_solve's resident FP32 start also carries the low words of its
+ * compensated value, so the two marches may differ by FP32 rounding.
+ * Every scratch buffer lives in one static
  * device array of HJI_NOALLOC_SCRATCH_BYTES bytes that each GPU loading the
  * library holds until exit; a grid that needs more (5 values per node for
  * FP64 RK3, 7 for FP32 RK3, rows padded to a multiple of 8 nodes, plus small
  * tables) returns HJI_E_INVALID.
  * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress, once per device); make it before any stream
- * capture.  Calls share the array: calls whose GPU work overlaps race.  No
+ * (cudaGetSymbolAddress, once per device and CUDA context: a call in a new
+ * context of the device, e.g. after cudaDeviceReset, looks it up again);
+ * make it before any stream capture (a look-up due inside a capture is
+ * refused with HJI_E_STATE).  Calls share the array: calls whose GPU work overlaps race.  No
  * cudaMalloc, cudaFree or other allocating routine is called.  Errors as for
  * hji_solve; the message is in hji_noalloc_last_error(). */
 #define HJI_NOALLOC_SCRATCH_BYTES (32u << 20)
@@ -214,6 +231,8 @@ hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double* lo, const
                              const int* periodic, hji_precision prec, const hji_dynamics* dyn,
                              const void* l, const void* k, void* v_out,
                              const hji_solve_opts* o, void* cuda_stream, hji_solve_stats* stats);
+/* The message of this thread's last failed hji_solve_noalloc call.  The
+ * paper has no counterpart (error reporting of this C ABI). */
 const char* hji_noalloc_last_error(void);
 
 /* Copy src's current value into dst as dst's resident value (converting
@@ -271,7 +290,11 @@ hji_status hji_engine_step(hji_engine e, int* active, int* queued);
 hji_status hji_engine_poll(hji_engine e, int64_t* tags, hji_solve_stats* stats,
                            hji_status* status, int cap, int* count);
 
+/* Release the engine (requests still queued or marching are dropped).  The
+ * paper has no counterpart (resource management of this C ABI). */
 hji_status hji_engine_destroy(hji_engine e);
+/* The message of the engine's last failed call.  The paper has no
+ * counterpart (error reporting of this C ABI). */
 const char* hji_engine_last_error(hji_engine e);
 
 /* Tile-shape autotuner (the paper has no counterpart).  2-D grids can be
@@ -315,12 +338,15 @@ hji_status hji_stage_times(hji_grid g, const void* l, int ptr_is_device, const h
  * Synchronous on cuda_stream; the message is in hji_last_error(NULL). */
 hji_status hji_selftest_bounded_wait(int64_t limit_ns, void* cuda_stream);
 
-/* Grid facts: ndim, n[], and the number of nodes (may be NULL each). */
+/* Grid facts: ndim, n[], and the number of nodes (may be NULL each).  The
+ * paper has no counterpart (introspection of this C ABI). */
 hji_status hji_grid_info(hji_grid g, int* ndim, int64_t* n, int64_t* num_nodes);
 
-/* Static text of a status code ("unknown status" for other values). */
+/* Static text of a status code ("unknown status" for other values).  The
+ * paper has no counterpart: error reporting of this C ABI only. */
 const char* hji_status_string(hji_status s);
-/* The message of the last failed call on grid g; for g NULL, of the last
+/* The paper has no counterpart: error reporting of this C ABI only.
+ * The message of the last failed call on grid g; for g NULL, of the last
  * failed call on this thread that had no grid (hji_grid_create, NULL
  * arguments, hji_selftest_bounded_wait).  Owned by the library, valid until
  * the next call that fails the same way. */

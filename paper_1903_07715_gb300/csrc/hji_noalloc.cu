@@ -7,17 +7,25 @@
 // the tile list, the instance description and march state) lives in one
 // file-scope device array of fixed size, HJI_NOALLOC_SCRATCH_BYTES.
 //
-// The array's host-side name is not a device address: once per device, with
-// that device current, the first call takes its address with
-// cudaGetSymbolAddress and caches it.  Make that first call on a device
-// before any stream capture.  Every call shares the array and leaves its
+// The array's host-side name is not a device address: the first call on a
+// device, with that device current, takes its address with
+// cudaGetSymbolAddress and caches it per device together with the identity of
+// the CUDA context it belongs to; a later call in another context of that
+// device (after cudaDeviceReset, or a primary context released and made
+// again, where the module is loaded anew and the array may move) looks the
+// address up again.  Make the first call on a device before any stream
+// capture.  Every call shares the array and leaves its
 // contents behind; the march state is cleared at the start of each call.
 // Calls whose GPU work overlaps (different streams or threads) race on it.
 // Nothing here calls cudaMalloc, cudaFree, cudaMallocHost, graph
 // instantiation or any other allocating routine.
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+
+#include <cudaTypedefs.h>
 
 #include "hji_common.cuh"
 
@@ -27,8 +35,89 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char hji_noalloc_scratch[HJI_NOALLOC_SCRATCH_BYTES];
 
-void* g_scratch[kMaxDevices] = {nullptr};
+// Per device: the scratch array's device address and the id of the context
+// it was taken in (0: none yet).  Guarded by g_scratch_mu.
+struct ScratchSlot {
+    unsigned long long ctx_id;
+    void* ptr;
+};
+std::mutex g_scratch_mu;
+ScratchSlot g_scratch[kMaxDevices] = {};
 thread_local char g_err[256] = "";
+
+// The id of the calling thread's current CUDA context (0 if none), from the
+// driver through the runtime's entry-point lookup (no link against the
+// driver library).  Returns false if the driver does not offer the lookup.
+bool current_ctx_id(unsigned long long* id) {
+    static std::once_flag once;
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
+        else
+            cudaGetLastError();
+        fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(fn);
+        else
+            cudaGetLastError();
+    });
+    if (!get_current || !get_id) return false;
+    CUcontext c = nullptr;
+    *id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || c == nullptr) return true;
+    unsigned long long v = 0;
+    if (get_id(c, &v) != CUDA_SUCCESS) return false;
+    *id = v;
+    return true;
+}
+
+// The scratch array's device address in the current context of device dev
+// (set-up once per device and context; see the top of this file).
+hji_status scratch_address(int dev, cudaStream_t s, unsigned char** out) {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    unsigned long long id = 0;
+    if (!current_ctx_id(&id)) {
+        std::snprintf(g_err, sizeof(g_err), "the driver offers no context identity lookup");
+        return HJI_E_CUDA;
+    }
+    if (id != 0 && g_scratch[dev].ctx_id == id && g_scratch[dev].ptr != nullptr) {
+        *out = static_cast<unsigned char*>(g_scratch[dev].ptr);
+        return HJI_OK;
+    }
+    // A look-up is due: refuse it inside a stream capture.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) {
+        std::snprintf(g_err, sizeof(g_err), "cudaStreamIsCapturing: %s", cudaGetErrorString(e));
+        return HJI_E_CUDA;
+    }
+    if (cs != cudaStreamCaptureStatusNone) {
+        std::snprintf(g_err, sizeof(g_err),
+                      "the first call in this device context came during a stream capture; "
+                      "make one call before capturing");
+        return HJI_E_STATE;
+    }
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, hji_noalloc_scratch);
+    if (e != cudaSuccess) {
+        std::snprintf(g_err, sizeof(g_err), "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        return HJI_E_CUDA;
+    }
+    if (id == 0 && (!current_ctx_id(&id) || id == 0)) {  // the look-up made the context
+        std::snprintf(g_err, sizeof(g_err), "no current CUDA context after the symbol look-up");
+        return HJI_E_CUDA;
+    }
+    g_scratch[dev].ctx_id = id;
+    g_scratch[dev].ptr = p;
+    *out = static_cast<unsigned char*>(p);
+    return HJI_OK;
+}
 
 hji_status nfail(hji_status s, const char* msg) {
     std::snprintf(g_err, sizeof(g_err), "%s", msg);
@@ -66,6 +155,7 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
                                         hji_solve_stats* stats) {
     using hji::InstDesc;
     using hji::InstState;
+    const auto t_start = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (ndim < 1 || ndim > HJI_MAX_DIM || !n || !lo || !hi) return nfail(HJI_E_INVALID, "bad grid");
     if (prec != HJI_F64 && prec != HJI_F32) return nfail(HJI_E_INVALID, "unknown precision");
@@ -77,6 +167,10 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
     if (!(o->tol >= 0.0) || !std::isfinite(o->tol) || !(o->horizon >= 0.0) ||
         !std::isfinite(o->horizon))
         return nfail(HJI_E_INVALID, "tol and horizon must be finite and >= 0");
+    if (!(o->tol_rate >= 0.0) || !std::isfinite(o->tol_rate))
+        return nfail(HJI_E_INVALID, "tol_rate must be finite and >= 0");
+    if (o->tile_variant < 0 || o->tile_variant > hji::kTileVariants)
+        return nfail(HJI_E_INVALID, "tile_variant must be 0..HJI_TILE_VARIANTS");
     if (o->init == HJI_INIT_USER_K && !k) return nfail(HJI_E_INVALID, "HJI_INIT_USER_K needs k");
     if (o->init != HJI_INIT_STANDARD && o->init != HJI_INIT_USER_K && o->init != HJI_INIT_RESIDENT)
         return nfail(HJI_E_INVALID, "unknown init mode");
@@ -139,9 +233,12 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
     // Scratch layout and the size check.
     const bool f32 = prec == HJI_F32;
     const size_t es = f32 ? 4 : 8;
+    // Tile shape: a forced 2-D variant (tile_variant 1..3) or variant 0
+    // (no autotuned choice is consulted here).
+    const int variant = (ndim == 2 && o->tile_variant > 0) ? o->tile_variant - 1 : 0;
     long long tx, ty, planes = 1;
     int TX, TY;
-    hji::tile_dims(ndim, 0, TY, TX);
+    hji::tile_dims(ndim, variant, TY, TX);
     tx = (n[ndim - 1] + TX - 1) / TX;
     ty = ndim >= 2 ? (n[ndim - 2] + TY - 1) / TY : 1;
     for (int a = 0; a < ndim - 2; ++a) planes *= n[a];
@@ -170,18 +267,16 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
         return HJI_E_INVALID;
     }
 
-    // Once per device: the device address of the scratch array.
+    // Once per device and context: the device address of the scratch array.
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return ncuda(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return nfail(HJI_E_INVALID, "device index out of range");
-    if (!g_scratch[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, hji_noalloc_scratch);
-        if (e != cudaSuccess) return ncuda(e, "cudaGetSymbolAddress");
-        g_scratch[dev] = p;
+    unsigned char* base = nullptr;
+    {
+        const hji_status as = scratch_address(dev, s, &base);
+        if (as != HJI_OK) return as;
     }
-    unsigned char* base = static_cast<unsigned char*>(g_scratch[dev]);
     InstState* d_state = reinterpret_cast<InstState*>(base + o_state);
     InstDesc* d_desc = reinterpret_cast<InstDesc*>(base + o_desc);
     int* d_ints = reinterpret_cast<int*>(base + o_ints);  // [0] active, [1] ntiles
@@ -207,7 +302,7 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
     D.nalloc = nalloc;
     D.cfl = o->cfl;
     D.tol = o->tol;
-    D.tol_rate = o->tol_rate >= 0.0 && std::isfinite(o->tol_rate) ? o->tol_rate : 0.0;
+    D.tol_rate = o->tol_rate;
     D.horizon = o->horizon;
     D.max_steps = o->max_steps > 0 ? o->max_steps : 1000000;
     D.V[0] = base + o_v0;
@@ -229,7 +324,7 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
     D.kinit_lo = nullptr;
     {
         const char* why = nullptr;
-        if (!hji::encode_maps(D, f32, o->scheme, 0, &why)) return nfail(HJI_E_CUDA, why);
+        if (!hji::encode_maps(D, f32, o->scheme, variant, &why)) return nfail(HJI_E_CUDA, why);
     }
     // l (and k, or the caller's previous value for HJI_INIT_RESIDENT) into
     // the padded scratch fields.
@@ -286,11 +381,11 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
     long long grid[3];  // per stage: as many CTAs as fit on every SM, at most one per tile
     for (int i = 0; i < ns; ++i) {
         const bool last = i == ns - 1;
-        L[i] = f32 ? hji::stage_launcher_f32(ndim, o->scheme, last)
-                   : hji::stage_launcher_f64(ndim, o->scheme, last);
+        L[i] = f32 ? hji::stage_launcher_f32(ndim, o->scheme, last, variant)
+                   : hji::stage_launcher_f64(ndim, o->scheme, last, variant);
         if (!L[i]) return nfail(HJI_E_INVALID, "no kernel for this ndim/scheme");
-        const int b = f32 ? hji::stage_max_blocks_f32(ndim, o->scheme, last)
-                          : hji::stage_max_blocks_f64(ndim, o->scheme, last);
+        const int b = f32 ? hji::stage_max_blocks_f32(ndim, o->scheme, last, variant)
+                          : hji::stage_max_blocks_f64(ndim, o->scheme, last, variant);
         grid[i] = (long long)sms * b;
         if (grid[i] > ntiles) grid[i] = ntiles;
         if (grid[i] < 1) grid[i] = 1;
@@ -322,7 +417,8 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
         stats->tau = hs.tau;
         stats->dt = hs.dt;
         stats->final_max_dV = hs.last_delta;
-        stats->wall_ms = 0.0;
+        stats->wall_ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
         for (int a = 0; a < HJI_MAX_DIM; ++a) stats->alpha[a] = a < ndim ? hs.alpha[a] : 0.0;
         stats->converged = hs.converged;
         stats->kernel_launches = launches;

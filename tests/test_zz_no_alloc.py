@@ -4,6 +4,10 @@ they run where allocator calls are forbidden).  It keeps its scratch in one
 static device array, so two calls in a row must each give what the
 allocating entry point hji_solve gives for the same problem, and a grid too
 large for the array must be refused before any device work.
+
+Both arms march with the same tile shape: the allocating solve is given
+tile_variant=1 (shape 0, the one hji_solve_noalloc takes by default), so the
+comparison does not rest on any autotuned choice made earlier in the session.
 """
 import ctypes
 
@@ -26,15 +30,21 @@ def _grid_args(gd):
     return nd, n, lo, hi, per
 
 
-def _noalloc(hji, torch, gd, dyn, l, k, prec, **opts):
+def _noalloc(hji, torch, gd, dyn, l, k, prec, resident=None, **opts):
+    """One hji_solve_noalloc call; `resident` (optional) is the previous value
+    placed in v_out for an HJI_INIT_RESIDENT start."""
     nd, n, lo, hi, per = _grid_args(gd)
     tdt = torch.float64 if prec == "f64" else torch.float32
     lt = torch.as_tensor(l, dtype=tdt, device="cuda").contiguous()
     kt = None if k is None else torch.as_tensor(k, dtype=tdt, device="cuda").contiguous()
-    out = torch.empty_like(lt)
+    if resident is not None:
+        out = torch.as_tensor(resident, dtype=tdt, device="cuda").contiguous().clone()
+        init = hji.HJI_INIT_RESIDENT
+    else:
+        out = torch.empty_like(lt)
+        init = hji.HJI_INIT_USER_K if k is not None else hji.HJI_INIT_STANDARD
     dstruct, keep = hji.dynamics_struct(dyn, nd)
-    o = hji.solve_opts(init=hji.HJI_INIT_USER_K if k is not None else hji.HJI_INIT_STANDARD,
-                       **opts)
+    o = hji.solve_opts(init=init, **opts)
     st = hji.hji_solve_stats()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     rc = hji.hji_solve_noalloc(nd, n, lo, hi, per, hji.HJI_F64 if prec == "f64" else hji.HJI_F32,
@@ -48,7 +58,7 @@ def _noalloc(hji, torch, gd, dyn, l, k, prec, **opts):
 def _allocating(hji, gd, dyn, l, k, prec, **opts):
     g = hji.Grid(gd, prec)
     g.set_dynamics(dyn)
-    st = g.solve(l, k, **opts)
+    st = g.solve(l, k, tile_variant=1, **opts)
     V = g.value()
     g.close()
     return V, st
@@ -91,3 +101,42 @@ def test_noalloc_refuses_grids_beyond_its_scratch(hji_lib):
                                l.data_ptr(), None, l.data_ptr(), ctypes.byref(o), None, None)
     assert rc == hji.HJI_E_INVALID
     assert "scratch" in hji.hji_noalloc_last_error()
+
+
+def test_noalloc_4d_and_resident_start_match_hji_solve(hji_lib):
+    """A 4-D grid (21^4 quadrotor subsystem, FP32, ENO2/RK2: the N-D tensor
+    maps and strides of the scratch layout) and then an HJI_INIT_RESIDENT
+    call that starts from the value left in v_out.  An FP32 resident start
+    through hji_solve_noalloc begins from the float values alone, which is
+    what hji_solve does for a user warm start k holding those floats."""
+    import torch
+    assert torch.cuda.is_available()
+    hji = hji_lib
+    gd, dyn, l = W.quad4d_config(21, dmax=0.1)
+    l32 = l.astype(np.float32)
+    opts = dict(scheme="eno2", rk=2, cfl=0.5, tol=0.0, max_steps=40)
+    rc, V1, s1 = _noalloc(hji, torch, gd, dyn, l32, None, "f32", **opts)
+    assert rc == hji.HJI_OK or rc == hji.HJI_E_NOT_CONVERGED, hji.hji_noalloc_last_error()
+    R1, r1 = _allocating(hji, gd, dyn, l32, None, "f32", **opts)
+    assert s1.steps == r1["steps"] == 40
+    assert np.abs(V1.astype(np.float64) - R1.astype(np.float64)).max() <= TOL
+    _, dyn2, _ = W.quad4d_config(21, dmax=0.2)
+    rc2, V2, s2 = _noalloc(hji, torch, gd, dyn2, l32, None, "f32", resident=V1, **opts)
+    assert rc2 == hji.HJI_OK or rc2 == hji.HJI_E_NOT_CONVERGED, hji.hji_noalloc_last_error()
+    R2, r2 = _allocating(hji, gd, dyn2, l32, V1, "f32", **opts)
+    assert s2.steps == r2["steps"] == 40
+    assert np.abs(V2.astype(np.float64) - R2.astype(np.float64)).max() <= TOL
+
+
+def test_noalloc_rejects_bad_options_before_device_work(hji_lib):
+    import torch
+    hji = hji_lib
+    gd, dyn, l = W.di_config(21)
+    lt = torch.as_tensor(l, device="cuda")
+    nd, n, lo, hi, per = _grid_args(gd)
+    dstruct, keep = hji.dynamics_struct(dyn, nd)
+    for bad in (dict(tol_rate=-1.0), dict(tol_rate=float("nan")), dict(tile_variant=7)):
+        o = hji.solve_opts(scheme="eno2", rk=2, **bad)
+        rc = hji.hji_solve_noalloc(nd, n, lo, hi, per, hji.HJI_F64, ctypes.byref(dstruct),
+                                   lt.data_ptr(), None, lt.data_ptr(), ctypes.byref(o), None, None)
+        assert rc == hji.HJI_E_INVALID, bad
