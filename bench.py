@@ -195,6 +195,10 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="profiling aid: run only this many steps of the workload's march "
+                         "with each RK stage kernel launched on its own (hji_stage_times), "
+                         "from V0 = l, and print their mean durations; no bench line")
     ap.add_argument("--workload", default="di1001",
                     choices=["di1001", "quad61", "batch256", "di8192"],
                     help="di1001: whole warm-started solves of the 1001^2 double integrator "
@@ -217,6 +221,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     hji.load()
+    if args.profile_steps > 0:
+        return profile_stages(args, hji, torch)
     if args.workload != "di1001":
         return run_hbm_workload(args, hji, torch, dist, rank, world, local_rank)
 
@@ -291,13 +297,11 @@ def main():
     avg_stage_ms = (ms / args.steps) / stage_launches_with_work
     flops = FLOPS_PER_NODE_STAGE * cells
     achieved_tflops = flops / (avg_stage_ms * 1e-3) / 1e12
-    sm_mhz = clk.get("sm_mhz") or 2070.0
-    # FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock.
-    # FP64 peak: GB300 lists 1.25 TFLOP/s (at the 2070 MHz maximum clock).
-    if prec == "f32":
-        peak = 152 * 128 * 2 * 2070e6 / 1e12
-    else:
-        peak = 1.25
+    # The arithmetic roofline's denominator: this GPU's FMA rate in the
+    # kernel's precision, measured here (after the timed region) by the
+    # library's FMA microbenchmark, CUDA-event timed, fastest of five.
+    peak, peak_ms = hji.peak_fma(prec, target_ms=20.0)
+    peak_other, _ = hji.peak_fma("f64" if prec == "f32" else "f32", target_ms=20.0)
     # DRAM bytes per stage launch (dram__bytes_read.sum + dram__bytes_write.sum)
     # from an ncu capture of the current stage kernels; none is recorded for
     # them at present (the last capture, of the kernels before the change to
@@ -310,8 +314,11 @@ def main():
                 "kernel": "stage_kernel<%s,2,WENO5> (per-stage, 3 per RK3 step)" % prec,
                 "flops_per_node_stage": FLOPS_PER_NODE_STAGE,
                 "mem_words_per_node_step": WORDS_PER_NODE_STEP[prec],
-                "peak_source": "derived from unit counts at 2070 MHz max SM clock"
-                               if prec == "f32" else "GB300 datasheet FP64 rate"}
+                "peak_source": "measured: hji_peak_fma (%s FMA chains on every SM, "
+                               "CUDA events, fastest of 5 launches of %.1f ms)" % (prec, peak_ms),
+                "measured_fma_tflops": {prec: peak,
+                                        ("f64" if prec == "f32" else "f32"): peak_other},
+                "unit_count_fp32_tflops": 152 * 128 * 2 * 2070e6 / 1e12}
 
     # Each stage kernel alone between two CUDA events on this stream
     # (hji_stage_times: 300 steps from V0 = l, after the timed region): the
@@ -350,6 +357,31 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def profile_stages(args, hji, torch):
+    """A short march of one workload with each stage kernel launched alone
+    (few launches, for a profiler): FP32, the workload's scheme and RK order."""
+    if args.workload == "di1001":
+        gd, dyn, l = W.di_config(N_SIDE, dmax=DMAX)
+        opts = dict(scheme="weno5", rk=3, cfl=0.5)
+    elif args.workload == "di8192":
+        gd, dyn, l = W.di_config(8192)
+        opts = dict(scheme="eno2", rk=2, cfl=0.5)
+    elif args.workload == "quad61":
+        gd, dyn, l = W.quad4d_config(61, dmax=0.3)
+        opts = dict(scheme="eno2", rk=2, cfl=0.5)
+    else:
+        raise SystemExit("--profile-steps supports di1001, di8192 and quad61")
+    g = hji.Grid(gd, args.precision)
+    g.set_dynamics(dyn)
+    npdt = np.float32 if args.precision == "f32" else np.float64
+    l_dev = torch.from_numpy(l.astype(npdt)).cuda()
+    ms = g.stage_times(l_dev, steps=args.profile_steps, **opts)
+    g.close()
+    print(json.dumps({"profile": args.workload, "precision": args.precision,
+                      "steps": args.profile_steps, "stage_ms": ms}), flush=True)
     return 0
 
 
@@ -556,18 +588,38 @@ def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=N
             # (20 steps from V0 = l): stage 1 moves 12 B per node, the fused
             # last stage (min(l), max|dV|) 24 B.
             sms = grids[0].stage_times(ldev[0], steps=20, scheme="eno2", rk=2, cfl=0.5)
+            # Two byte counts per node: what the compensated FP32 layout moves
+            # (high and low words of V^n, stage increments) and the method's
+            # own per-stage count with one FP32 word per field (stage 1 reads
+            # V and writes W1: 8 B; the last stage reads W1, V^n, l and writes
+            # V^{n+1}: 16 B).
             stage = {}
-            for key, t, b in (("first_stage", sms[0], 12), ("fused_last_stage", sms[1], 24)):
+            for key, t, b, bm in (("first_stage", sms[0], 12, 8),
+                                  ("fused_last_stage", sms[1], 24, 16)):
                 a = b * cells / (t * 1e-3) / 1e9
+                am = bm * cells / (t * 1e-3) / 1e9
                 stage[key] = {"ms": t, "bytes_per_node": b, "achieved": a, "frac": a / peak,
+                              "method_bytes_per_node": bm, "method_achieved": am,
+                              "method_frac": am / peak,
                               "traffic": DRAM_BYTES_PER_LAUNCH.get((name, key))}
         gbs = upd * bytes_per_update / (ms * 1e-3) / 1e9
+        # The method's counts per node-step: per-stage kernels of RK2 move 6
+        # words (24 B in FP32); a march fused in time needs 3 (read V^n and l,
+        # write V^{n+1}: 12 B).
+        gbs_stage = upd * 24 / (ms * 1e-3) / 1e9
+        gbs_strict = upd * 12 / (ms * 1e-3) / 1e9
         out[name] = {"nodes": cells, "steps": steps, "ms": ms / repeats, "tile_shape": ["31x32", "15x64", "63x16"][tuned],
                      "cell_updates_per_s": upd / (ms * 1e-3), "ms_total": ms,
                      "updates_total": upd, "launches": launches, "clocks": clk,
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                                   "frac": gbs / peak, "peak_source": src,
                                   "bytes_per_node_step": bytes_per_update, "traffic": None,
+                                  "method_per_stage": {"bytes_per_node_step": 24,
+                                                       "achieved": gbs_stage,
+                                                       "frac": gbs_stage / peak},
+                                  "method_strict": {"bytes_per_node_step": 12,
+                                                    "achieved": gbs_strict,
+                                                    "frac": gbs_strict / peak},
                                   "note": "whole-march time (set-up, init and 50 steps of "
                                           "2 stage launches) in the denominator"},
                      "stage_kernels": stage}

@@ -338,6 +338,21 @@ hji_status hji_stage_times(hji_grid g, const void* l, int ptr_is_device, const h
  * Synchronous on cuda_stream; the message is in hji_last_error(NULL). */
 hji_status hji_selftest_bounded_wait(int64_t limit_ns, void* cuda_stream);
 
+/* Measured fused-multiply-add rate of the current GPU in `prec` (a
+ * measurement aid for the arithmetic roofline of the stage kernels; the
+ * paper has no counterpart).  Every thread of a grid that fills every SM
+ * runs independent multiply-add chains; the loop count is calibrated so a
+ * launch takes about target_ms (1 .. 1000), five launches are timed with
+ * CUDA events on cuda_stream, and the fastest gives *tflops (one FMA = two
+ * floating-point operations) and *ms_per_launch (may be NULL).  Allocates
+ * nothing; synchronous.  Errors: HJI_E_INVALID (precision, target_ms,
+ * tflops NULL), HJI_E_CUDA; the message is in hji_peak_last_error(). */
+hji_status hji_peak_fma(hji_precision prec, double target_ms, void* cuda_stream, double* tflops,
+                        double* ms_per_launch);
+/* The message of this thread's last failed hji_peak_fma call.  The paper
+ * has no counterpart (error reporting of this C ABI). */
+const char* hji_peak_last_error(void);
+
 /* Grid facts: ndim, n[], and the number of nodes (may be NULL each).  The
  * paper has no counterpart (introspection of this C ABI). */
 hji_status hji_grid_info(hji_grid g, int* ndim, int64_t* n, int64_t* num_nodes);

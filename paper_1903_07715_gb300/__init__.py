@@ -35,7 +35,8 @@ EXPORTS = ["hji_grid_create", "hji_grid_destroy", "hji_dynamics_set", "hji_solve
            "hji_status_string", "hji_last_error", "hji_solve_noalloc", "hji_noalloc_last_error",
            "hji_engine_create", "hji_engine_submit", "hji_engine_step", "hji_engine_poll",
            "hji_engine_destroy", "hji_engine_last_error", "hji_autotune",
-           "hji_stage_times", "hji_selftest_bounded_wait"]
+           "hji_stage_times", "hji_selftest_bounded_wait", "hji_peak_fma",
+           "hji_peak_last_error"]
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -133,9 +134,12 @@ def load(build_if_missing=False):
     lib.hji_selftest_bounded_wait.argtypes = [ctypes.c_int64, vp]
     lib.hji_stage_times.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(hji_solve_opts),
                                     ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.hji_peak_fma.argtypes = [ctypes.c_int, ctypes.c_double, vp, dp, dp]
+    lib.hji_peak_last_error.argtypes = []
+    lib.hji_peak_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name not in ("hji_status_string", "hji_last_error", "hji_noalloc_last_error",
-                        "hji_engine_last_error"):
+                        "hji_engine_last_error", "hji_peak_last_error"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -194,6 +198,26 @@ def hji_autotune(g, l, ptr_is_device, opts, steps, stream, chosen, ms_per_step):
 
 def hji_stage_times(g, l, ptr_is_device, opts, steps, stream, ms_per_stage):
     return load().hji_stage_times(g, l, ptr_is_device, opts, steps, stream, ms_per_stage)
+
+
+def hji_peak_fma(prec, target_ms, stream, tflops, ms_per_launch):
+    return load().hji_peak_fma(prec, target_ms, stream, tflops, ms_per_launch)
+
+
+def hji_peak_last_error():
+    return load().hji_peak_last_error().decode()
+
+
+def peak_fma(precision="f32", target_ms=20.0, stream=None):
+    """Measured FMA rate of the current GPU (TFLOP/s, one FMA = 2 flops) and
+    the duration of the fastest timed launch (ms)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    st = None if stream is None else ctypes.c_void_p(stream)
+    rc = hji_peak_fma(HJI_F32 if precision == "f32" else HJI_F64, float(target_ms), st,
+                      ctypes.byref(tf), ctypes.byref(ms))
+    if rc != HJI_OK:
+        raise HJIError(rc, hji_peak_last_error())
+    return tf.value, ms.value
 
 
 def hji_engine_create(ndim, prec, opts, max_slots, budget_bytes, stream, out):

@@ -85,3 +85,11 @@ def test_stage_times_rejects_null_arguments_before_device_work(hji_lib):
     assert hji_lib.hji_stage_times(None, None, 0, None, 10, None, ms) == hji_lib.HJI_E_INVALID
     assert "NULL" in hji_lib.hji_last_error(None)
     assert hji_lib.hji_autotune(None, None, 0, None, 10, None, None, None) == hji_lib.HJI_E_INVALID
+
+
+def test_peak_fma_validates_before_device_work(hji_lib):
+    tf = ctypes.c_double()
+    assert hji_lib.hji_peak_fma(7, 20.0, None, ctypes.byref(tf), None) == hji_lib.HJI_E_INVALID
+    assert hji_lib.hji_peak_fma(0, 0.0, None, ctypes.byref(tf), None) == hji_lib.HJI_E_INVALID
+    assert hji_lib.hji_peak_fma(1, 20.0, None, None, None) == hji_lib.HJI_E_INVALID
+    assert "target_ms" in hji_lib.hji_peak_last_error()

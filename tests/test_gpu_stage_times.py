@@ -58,3 +58,16 @@ def test_stage_times_rejects_bad_steps(hji_lib):
             g.stage_times(l, steps=steps)
         assert e.value.status == hji_lib.HJI_E_INVALID
     g.close()
+
+
+def test_peak_fma_rates_are_plausible(hji_lib):
+    """The measured FMA rates used as the arithmetic roofline: FP32 between a
+    tenth and 1.2 times the unit-count rate of 152 SMs x 128 lanes x 2 flops x
+    2.07 GHz (80.5 TFLOP/s), FP64 far below FP32 on this GPU."""
+    import torch
+    assert torch.cuda.is_available()
+    f32, ms32 = hji_lib.peak_fma("f32", target_ms=10.0)
+    f64, ms64 = hji_lib.peak_fma("f64", target_ms=10.0)
+    assert 8.0 <= f32 <= 1.2 * 80.5, f32
+    assert 0.0 < f64 < f32 / 4, (f64, f32)
+    assert ms32 > 1.0 and ms64 > 1.0
