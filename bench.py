@@ -349,6 +349,8 @@ def main():
     if rank == 0 and not args.no_variants:
         line["time_to_converge"] = time_to_converge(hji, torch, gd, dyn, l, l_dev, k_dev)
         line["hbm_workloads"] = hbm_workloads(hji, torch)
+        line["config_rows"] = config_rows(hji, torch)
+        line["north_star_batch"] = north_star_batch(hji, torch)
         line["serving"] = serving_both(hji, torch)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(budget_s=12.0)
@@ -474,41 +476,378 @@ def run_hbm_workload(args, hji, torch, dist, rank, world, local_rank):
     return 0
 
 
+def _brt_cells(torch, a, b):
+    """Hausdorff distance in grid cells between the sub-zero node sets of two
+    device arrays (Euclidean, by brute force over boundary-free sets: the
+    symmetric difference's nodes against the other set), for the bench's
+    accuracy rows.  Returns 0 when the sets agree."""
+    ma, mb = (a <= 0), (b <= 0)
+    if bool(torch.equal(ma, mb)):
+        return 0.0
+    import numpy as _np
+    from scipy.ndimage import distance_transform_edt
+    A, B = ma.cpu().numpy(), mb.cpu().numpy()
+    if not A.any() or not B.any():
+        return float("inf")
+    da, db = distance_transform_edt(~A), distance_transform_edt(~B)
+    return float(max(da[B].max(), db[A].max()))
+
+
+def _errs(torch, v, ref, scale):
+    d = float((v.double() - ref.double()).abs().max().item())
+    return {"max_abs": d, "max_abs_over_max_l": d / scale,
+            "brt_hausdorff_cells": _brt_cells(torch, v, ref)}
+
+
+def _solve_timed(torch, g, l, k=None, init=None, **opts):
+    st, ms = _timed(torch, lambda: g.solve(l, k, init=init, **opts))
+    return {"ms": ms, "steps": st["steps"], "converged": st["converged"],
+            "intervals_0.01": st["tau"] / 0.01, "dt": st["dt"]}
+
+
+def config_rows(hji, torch):
+    """Warm vs standard time-to-converge on the paper's other scenarios, one
+    solve each on device-resident inputs (wall time of the C-ABI call):
+      c1: 101^2 double integrator, FP64 ENO2/RK2, tol 1e-6, warm start from
+          the umax = 1.2 solution (control authority shrinks: Sec. V-B,
+          Table 1's control-authority rows);
+      c2: the benchmark's 1001^2 problem (FP32 WENO5/RK3, d 0 -> 0.2), under
+          the per-step rule (max|dV| < 1e-6) and Sec. IV's rate rule
+          (max|dV| < 0.001 per 0.01 of time), with where the last step's
+          largest change sits and after how many steps the sub-zero set
+          reaches its final shape;
+      c3: quadrotor subsystems of Sec. VI, FP32 ENO2/RK2: 4-D at 41^4 and
+          61^4 (|d| 0 -> 0.3 on v) under the rate rule (ENO2 settles into a
+          small limit cycle there, about 3e-5 per step, so no per-step
+          tolerance near 1e-6 is ever met), and the 2-D vertical subsystem
+          at 501^2 (m 1.0 -> 1.3, |d| 0 -> 0.3) under max|dV| < 1e-6 max|l|."""
+    out = {}
+    # ---- c1
+    gd, dyn, l = W.di_config(101)
+    _, dyn12, _ = W.di_config(101, umax=1.2)
+    o1 = dict(scheme="eno2", rk=2, cfl=0.5, tol=1e-6, max_steps=100000)
+    l64 = torch.from_numpy(l).cuda()
+    g = hji.Grid(gd, "f64")
+    g.set_dynamics(dyn12)
+    g.solve(l64, **o1)
+    k = torch.empty_like(l64)
+    g.value(k)
+    g.set_dynamics(dyn)
+    std = _solve_timed(torch, g, l64, **o1)
+    vs = torch.empty_like(l64)
+    g.value(vs)
+    warm = _solve_timed(torch, g, l64, k, **o1)
+    vw = torch.empty_like(l64)
+    g.value(vw)
+    g.close()
+    out["c1_di101_f64_umax_1.2_to_1.0"] = {
+        "standard": std, "warm": warm, "step_ratio": std["steps"] / max(1, warm["steps"]),
+        "time_ratio": std["ms"] / warm["ms"], "warm_vs_standard": _errs(torch, vw, vs, 1.0)}
+    # ---- c2
+    out["c2_di1001_f32_weno5"] = c2_analysis(hji, torch)
+    # ---- c3
+    rate = dict(scheme="eno2", rk=2, cfl=0.5, tol=0.0, tol_rate=0.1, max_steps=40000,
+                check_every=64)
+    for n in (41, 61):
+        gd, dyn0, l = W.quad4d_config(n, dmax=0.0)
+        _, dyn3, _ = W.quad4d_config(n, dmax=0.3)
+        l32 = torch.from_numpy(l.astype(np.float32)).cuda()
+        g = hji.Grid(gd, "f32")
+        g.set_dynamics(dyn0)
+        prior = _solve_timed(torch, g, l32, **rate)
+        k = torch.empty_like(l32)
+        g.value(k)
+        g.set_dynamics(dyn3)
+        std = _solve_timed(torch, g, l32, **rate)
+        vs = torch.empty_like(l32)
+        g.value(vs)
+        warm = _solve_timed(torch, g, l32, k, **rate)
+        vw = torch.empty_like(l32)
+        g.value(vw)
+        g.close()
+        cells = W.num_cells(gd)
+        out["c3_quad4d_%d^4_f32_d_0_to_0.3" % n] = {
+            "prior_d0": prior, "standard": std, "warm": warm,
+            "step_ratio": std["steps"] / max(1, warm["steps"]),
+            "time_ratio": std["ms"] / warm["ms"],
+            "cell_updates_per_s_standard": cells * std["steps"] / (std["ms"] * 1e-3),
+            "warm_vs_standard": _errs(torch, vw, vs, 4.0),
+            "rule": "Sec. IV rate rule: max|dV| < 0.001 per 0.01 of time (tol_rate 0.1)"}
+    gd, dyn_a, l = W.quadz_config(501, mass=1.0, dmax=0.0)
+    _, dyn_b, _ = W.quadz_config(501, mass=1.3, dmax=0.3)
+    oz = dict(scheme="eno2", rk=2, cfl=0.5, tol=4e-6, max_steps=200000)
+    l32 = torch.from_numpy(l.astype(np.float32)).cuda()
+    g = hji.Grid(gd, "f32")
+    g.set_dynamics(dyn_a)
+    prior = _solve_timed(torch, g, l32, **oz)
+    k = torch.empty_like(l32)
+    g.value(k)
+    g.set_dynamics(dyn_b)
+    std = _solve_timed(torch, g, l32, **oz)
+    vs = torch.empty_like(l32)
+    g.value(vs)
+    warm = _solve_timed(torch, g, l32, k, **oz)
+    vw = torch.empty_like(l32)
+    g.value(vw)
+    g.close()
+    out["c3_quadz_501^2_f32_m_1.0_to_1.3_d_0_to_0.3"] = {
+        "prior": prior, "standard": std, "warm": warm,
+        "step_ratio": std["steps"] / max(1, warm["steps"]), "time_ratio": std["ms"] / warm["ms"],
+        "warm_vs_standard": _errs(torch, vw, vs, 4.0), "rule": "max|dV| < 1e-6 max|l| = 4e-6"}
+    return out
+
+
+def c2_analysis(hji, torch):
+    """Why the warm start saves few steps on the benchmark problem: the
+    per-step test's last steps are set by the slow drift of V far from the
+    zero level set, at the grid's edges."""
+    gd, dyn0, l = W.di_config(N_SIDE, dmax=0.0)
+    _, dyn, _ = W.di_config(N_SIDE, dmax=DMAX)
+    l32 = torch.from_numpy(l.astype(np.float32)).cuda()
+    g = hji.Grid(gd, "f32")
+    out = {}
+    for rule_name, rule in (("per_step_1e-6", dict(tol=1e-6)),
+                            ("sec4_rate_0.001_per_0.01", dict(tol=0.0, tol_rate=0.1))):
+        o = dict(scheme="weno5", rk=3, cfl=0.5, max_steps=200000, **rule)
+        g.set_dynamics(dyn0)
+        g.solve(l32, **o)
+        k = torch.empty_like(l32)
+        g.value(k)
+        g.set_dynamics(dyn)
+        row = {}
+        finals = {}
+        for name, kk in (("standard", None), ("warm", k)):
+            row[name] = _solve_timed(torch, g, l32, kk, **o)
+            v = torch.empty_like(l32)
+            g.value(v)
+            finals[name] = v
+        row["step_ratio"] = row["standard"]["steps"] / max(1, row["warm"]["steps"])
+        row["warm_vs_standard"] = _errs(torch, finals["warm"], finals["standard"], 1.0)
+        out[rule_name] = row
+    # Where the standard solve's last changes sit: one more step from its
+    # converged value (the resident value continues the march exactly).
+    o = dict(scheme="weno5", rk=3, cfl=0.5, tol=1e-6, max_steps=200000)
+    g.set_dynamics(dyn)
+    g.solve(l32, **o)
+    v0 = torch.empty_like(l32)
+    g.value(v0)
+    g.solve(l32, init=hji.HJI_INIT_RESIDENT, scheme="weno5", rk=3, cfl=0.5, tol=0.0, max_steps=1)
+    v1 = torch.empty_like(l32)
+    g.value(v1)
+    dv = (v1.double() - v0.double()).abs()
+    i = int(dv.argmax().item())
+    r, c = divmod(i, N_SIDE)
+    xs = W.node_coords(gd)
+    band = v0.abs() < 0.05
+    out["last_step_change"] = {
+        "max_dV": float(dv.max().item()), "at_x1": float(xs[0][r]), "at_x2": float(xs[1][c]),
+        "V_there": float(v0[r, c].item()),
+        "cells_from_grid_edge": int(min(r, c, N_SIDE - 1 - r, N_SIDE - 1 - c)),
+        "max_dV_where_|V|<0.05": float(dv[band].max().item()) if bool(band.any()) else None,
+        "max_dV_beyond_10_cells_of_the_edge": float(dv[10:-10, 10:-10].max().item())}
+    # After how many steps the sub-zero set takes its final shape: march in
+    # chunks of 50 steps (resident continuation) and compare with the final
+    # converged set.
+    chunk = 50
+    for name, kk in (("standard", None), ("warm", k)):
+        g.set_dynamics(dyn)
+        st = g.solve(l32, kk, **o)
+        final = torch.empty_like(l32)
+        g.value(final)
+        fin = final <= 0
+        total = st["steps"]
+        steps = 0
+        last_diff = 0
+        g.solve(l32, kk, scheme="weno5", rk=3, cfl=0.5, tol=0.0, max_steps=chunk)
+        while steps < total:
+            steps += chunk
+            v = torch.empty_like(l32)
+            g.value(v)
+            if not bool(torch.equal(v <= 0, fin)):
+                last_diff = steps
+            if steps < total:
+                g.solve(l32, init=hji.HJI_INIT_RESIDENT, scheme="weno5", rk=3, cfl=0.5, tol=0.0,
+                        max_steps=chunk)
+        out["steps_until_final_sub_zero_set_" + name] = {
+            "steps": last_diff + chunk if last_diff else chunk, "of_total": total,
+            "resolution_steps": chunk}
+    g.close()
+    return out
+
+
+def north_star_batch(hji, torch, budget_s=40.0):
+    """The 256-instance batch (config 4) solved as the batched FP32 warm
+    form (one hji_batch_solve, each instance warm-started from its d = 0
+    solution) against the plain per-instance FP64 standard solve (V0 = l,
+    one hji_solve per instance, one after another) on the same GPU: time to
+    converge and the FP32 results' distance to the FP64 ones.  ENO2/RK2,
+    cfl 0.5, tol 1e-6.  The FP64 solves run in instance order until
+    budget_s of wall time is spent; the comparison covers those instances
+    (their count is reported) and the batched time is scaled by their share
+    of the batch's cell-updates."""
+    insts = W.batch_instances(count=256, seed=1903)
+    o = dict(scheme="eno2", rk=2, cfl=0.5, tol=1e-6, max_steps=100000, check_every=32)
+    ls = [W.instance_target(i) for i in insts]
+    l32 = [torch.from_numpy(x.astype(np.float32)).cuda() for x in ls]
+    grids = []
+    for inst in insts:
+        grids.append(hji.Grid(inst["grid"], "f32"))
+    # priors (untimed): d = 0
+    for g, inst in zip(grids, insts):
+        g.set_dynamics(W.double_integrator(umax=inst["umax"], dmax=0.0))
+    hji.batch_solve(grids, l32, **o)
+    ks = []
+    for g, x in zip(grids, l32):
+        k = torch.empty_like(x)
+        g.value(k)
+        ks.append(k)
+    for g, inst in zip(grids, insts):
+        g.set_dynamics(inst["dyn"])
+    (sts, rc), ms_batch = _timed(torch, lambda: hji.batch_solve(grids, l32, ks, **o))
+    v32 = []
+    for g, x in zip(grids, l32):
+        v = torch.empty_like(x)
+        g.value(v)
+        v32.append(v)
+        g.close()
+    upd_batch = [W.num_cells(i["grid"]) * s["steps"] for i, s in zip(insts, sts)]
+    # per-instance FP64 standard solves
+    t0 = time.perf_counter()
+    done, ms64, worst_abs, worst_h, upd64 = 0, 0.0, 0.0, 0.0, 0
+    for i, inst in enumerate(insts):
+        if time.perf_counter() - t0 > budget_s:
+            break
+        g = hji.Grid(inst["grid"], "f64")
+        g.set_dynamics(inst["dyn"])
+        l64 = torch.from_numpy(ls[i]).cuda()
+        st, ms = _timed(torch, lambda: g.solve(l64, **o))
+        v = torch.empty_like(l64)
+        g.value(v)
+        g.close()
+        ms64 += ms
+        upd64 += W.num_cells(inst["grid"]) * st["steps"]
+        scale = float(l64.abs().max().item())
+        e = _errs(torch, v32[i], v, scale)
+        worst_abs = max(worst_abs, e["max_abs_over_max_l"])
+        worst_h = max(worst_h, e["brt_hausdorff_cells"])
+        done += 1
+    share = sum(upd_batch[:done]) / max(1, sum(upd_batch))
+    return {"instances": len(insts), "batched_f32_warm": {"ms": ms_batch, "all_converged": rc == 0,
+                                                         "cell_updates": sum(upd_batch)},
+            "per_instance_f64_standard": {"instances_solved": done, "ms": ms64,
+                                          "cell_updates": upd64},
+            "batched_ms_for_those_instances": ms_batch * share,
+            "speedup": ms64 / max(1e-9, ms_batch * share),
+            "worst_max_abs_over_max_l": worst_abs, "worst_brt_hausdorff_cells": worst_h,
+            "rule": "ENO2/RK2, cfl 0.5, max|dV| < 1e-6"}
+
+
 def serving_both(hji, torch):
-    """The specified stream (50 requests/s, far above one GPU's capacity for
-    these grid sizes) and a stream below capacity (1.5 requests/s)."""
-    return {"rate_50_per_s": serving(hji, torch, duration=6.0, rate=50.0, time_cap=60.0),
-            "rate_1.5_per_s": serving(hji, torch, duration=20.0, rate=1.5, time_cap=60.0)}
+    """The specified stream (50 requests/s for 60 s: far above one GPU's
+    capacity for these grid sizes, so requests still queued or marching at
+    the 60 s cap are counted as censored) and a stream below capacity (1.5
+    requests/s for 20 s), whose requests are then compared with plain
+    per-request FP64 standard solves."""
+    return {"rate_50_per_s": serving(hji, torch, duration=60.0, rate=50.0, time_cap=60.0),
+            "rate_1.5_per_s": serving(hji, torch, duration=20.0, rate=1.5, time_cap=60.0,
+                                      compare_f64_s=30.0)}
 
 
-def serving(hji, torch, duration=6.0, rate=50.0, time_cap=90.0):
-    """Config-5 serving: a Poisson stream (rate 50/s, seed 7715) of mass /
-    disturbance updates for quadrotor 4-D subsystems (sides 31, 41, 51, 61)
+def serving(hji, torch, duration=6.0, rate=50.0, time_cap=90.0, compare_f64_s=0.0):
+    """Config-5 serving: a Poisson stream (seed 7715) of mass / disturbance
+    updates for quadrotors (4-D horizontal subsystems, sides 31, 41, 51, 61)
     and 2-D double integrators (sides 201..1001 in steps of 200), each
-    warm-started from its system's resident previous value.  Every system is
-    solved once before the clock starts (untimed), so each timed request is
-    an update of a resident solution.  FP32 storage, FP64 convergence test,
-    ENO2/RK2, stopping by Sec. IV's rule (max|dV| below 0.001 per 0.01 of
-    time: tol_rate = 0.1)."""
+    warm-started from its system's resident previous value.  A quadrotor
+    mass update is a solve of its 2-D vertical subsystem (mass enters Eq.
+    (22) only there; side 8 (s - 1) + 1 for a quadrotor of side s), a
+    disturbance update a solve of a 4-D horizontal subsystem.  Every system
+    is solved once before the clock starts (untimed), so each timed request
+    is an update of a resident solution.  FP32 storage, FP64 convergence
+    test, ENO2/RK2, stopping by Sec. IV's rule (max|dV| below 0.001 per 0.01
+    of time: tol_rate = 0.1).  With compare_f64_s > 0, the completed
+    requests are then solved one by one as plain FP64 standard solves
+    (V0 = l) on the same GPU, in arrival order until that much wall time is
+    spent, and each system's last served result is compared with its FP64
+    counterpart."""
     from paper_1903_07715_gb300.serve import ReachabilityServer, summarize
     quad_sides, di_sides = [31, 41, 51, 61], [201, 401, 601, 801, 1001]
     rng = np.random.Generator(np.random.PCG64(7715))
     reqs = W.poisson_requests(rate=rate, duration=duration, seed=7715)
     for r in reqs:  # the stream's sizes, quantised to the resident systems
         r["side"] = int(rng.choice(quad_sides if r["kind"] == "quad4d" else di_sides))
+    reqs = [W.route_request(r) for r in reqs]
     opts = dict(scheme="eno2", rk=2, cfl=0.5, tol=0.0, tol_rate=0.1, max_steps=20000,
                 check_every=16)
     srv = ReachabilityServer(W.serving_system, precision="f32", max_slots=64, opts=opts)
+    systems = sorted({(r["kind"], r["side"]) for r in reqs})
     warm = [{"t": 0.0, "kind": k, "side": s, "change": "disturbance", "value": 0.0}
-            for k, sides in (("quad4d", quad_sides), ("di", di_sides)) for s in sides]
-    srv.run(warm, time_cap=time_cap)
+            for k, s in systems]
+    srv.run(warm, time_cap=300.0)
     records, wall = srv.run(reqs, time_cap=time_cap)
-    srv.close()
     out = summarize(records, wall)
-    out.update({"rate_per_s": rate, "stream_s": duration, "systems": len(warm),
-                "mix": "50% quad4d (31..61^4), 50% double integrator (201..1001^2); mass x "
-                       "U[1,1.5] or |d| ~ U[0,0.3]"})
+    out.update({"rate_per_s": rate, "stream_s": duration, "time_cap_s": time_cap,
+                "systems": len(systems),
+                "by_kind": {k: sum(1 for r in reqs if r["kind"] == k)
+                            for k in ("quad4d", "quadz", "di")},
+                "mix": "50% quadrotor (disturbance: 4-D 31..61^4; mass: vertical 2-D "
+                       "241..481^2), 50% double integrator (201..1001^2); mass x U[1,1.5] "
+                       "or |d| ~ U[0,0.3]"})
+    if compare_f64_s > 0.0:
+        out["vs_f64_standard"] = _served_vs_f64(hji, torch, srv, reqs, records, opts,
+                                                compare_f64_s)
+    srv.close()
     return out
+
+
+def _served_vs_f64(hji, torch, srv, reqs, records, opts, budget_s):
+    """Completed requests of the stream re-solved as plain FP64 standard
+    solves (V0 = l, same dynamics, same stopping rule) on the same GPU, in
+    arrival order until budget_s of wall time is spent: the FP64 solve time
+    against the served latency, and, for the last served request of each
+    system (the value still resident in the server), the distance of the
+    served FP32 value to the FP64 one."""
+    order = sorted(records, key=lambda i: reqs[i]["t"])
+    last_of = {}
+    for rid in order:
+        if "latency" in records[rid]:
+            last_of[(reqs[rid]["kind"], reqs[rid]["side"])] = rid
+    t0 = time.perf_counter()
+    rows = []
+    for rid in order:
+        rec = records[rid]
+        if "latency" not in rec:
+            continue
+        if time.perf_counter() - t0 > budget_s:
+            break
+        r = reqs[rid]
+        gd, dyn_fn, l = W.serving_system(r["kind"], r["side"])
+        g = hji.Grid(gd, "f64")
+        g.set_dynamics(dyn_fn(r["change"], r["value"]))
+        l64 = torch.from_numpy(l).cuda()
+        st, ms = _timed(torch, lambda: g.solve(l64, **opts))
+        row = {"kind": r["kind"], "side": r["side"], "change": r["change"],
+               "f64_standard_ms": ms, "f64_steps": st["steps"],
+               "served_latency_ms": rec["latency"] * 1e3, "served_steps": rec["steps"]}
+        if last_of.get((r["kind"], r["side"])) == rid:
+            v = torch.empty_like(l64)
+            g.value(v)
+            vs = torch.empty(v.shape, dtype=torch.float32, device="cuda")
+            srv.sys[(r["kind"], r["side"])]["grid"].value(vs)
+            row.update(_errs(torch, vs, v, float(l64.abs().max().item())))
+        g.close()
+        rows.append(row)
+    tot64 = sum(x["f64_standard_ms"] for x in rows)
+    totlat = sum(x["served_latency_ms"] for x in rows)
+    checked = [x for x in rows if "max_abs" in x]
+    return {"requests_compared": len(rows), "f64_standard_total_ms": tot64,
+            "served_latency_total_ms": totlat,
+            "f64_standard_over_served_latency": tot64 / max(1e-9, totlat),
+            "value_checks": len(checked),
+            "worst_max_abs_over_max_l": max((x["max_abs_over_max_l"] for x in checked),
+                                            default=None),
+            "worst_brt_hausdorff_cells": max((x["brt_hausdorff_cells"] for x in checked),
+                                             default=None),
+            "rows": rows}
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of

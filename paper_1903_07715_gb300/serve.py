@@ -124,12 +124,38 @@ class ReachabilityServer:
 
 
 def summarize(records, wall):
-    lat = np.array([r["latency"] for r in records.values() if "latency" in r])
+    """Latency percentiles over every arrival.  A request still queued or
+    marching when the loop stopped is censored: its latency is at least
+    (wall - arrival), and that lower bound enters the percentiles; a
+    percentile is flagged as a lower bound when a censored request could
+    move it."""
+    lat_done = [r["latency"] for r in records.values() if "latency" in r]
+    cens = [max(0.0, wall - r["arrival"]) for r in records.values() if "latency" not in r]
     ok = sum(1 for r in records.values() if r.get("status") == HJI_OK)
     upd = sum(r["cells"] * r["steps"] for r in records.values() if "steps" in r)
-    return {"requests": len(records), "completed": int(lat.size), "converged": ok,
-            "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
-            "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
-            "mean_ms": float(lat.mean() * 1e3) if lat.size else None,
-            "throughput_req_per_s": lat.size / wall if wall > 0 else None,
+    allv = np.array(lat_done + cens)
+    done = np.array(lat_done)
+
+    srt = np.sort(allv)
+
+    def pct(q):
+        # numpy's linear interpolation between the order statistics at
+        # floor(h) and ceil(h), h = (N - 1) q / 100: a censored request at or
+        # below the upper one of them could still move the result.
+        if not allv.size:
+            return None, False
+        v = float(np.percentile(allv, q))
+        upper = float(srt[int(np.ceil((allv.size - 1) * q / 100.0))])
+        return v * 1e3, bool(cens) and min(cens) <= upper
+
+    p50, p50_lb = pct(50)
+    p99, p99_lb = pct(99)
+    return {"requests": len(records), "completed": int(done.size), "converged": ok,
+            "unfinished": len(cens),
+            "p50_ms": p50, "p50_is_lower_bound": p50_lb,
+            "p99_ms": p99, "p99_is_lower_bound": p99_lb,
+            "completed_p50_ms": float(np.percentile(done, 50) * 1e3) if done.size else None,
+            "completed_p99_ms": float(np.percentile(done, 99) * 1e3) if done.size else None,
+            "mean_completed_ms": float(done.mean() * 1e3) if done.size else None,
+            "throughput_req_per_s": done.size / wall if wall > 0 else None,
             "cell_updates_per_s": upd / wall if wall > 0 else None, "wall_s": wall}

@@ -145,3 +145,32 @@ def test_time_cap_stops_the_loop(monkeypatch):
     assert records == {} and wall < 5.0
     s = serve.summarize(records, wall)
     assert s["completed"] == 0 and s["p50_ms"] is None
+
+
+def test_summary_counts_unfinished_requests_as_censored():
+    """Percentiles are taken over every arrival: a request still running at
+    the cap enters with the lower bound (wall - arrival) and flags the
+    percentiles it can move."""
+    recs = {0: {"arrival": 0.0, "latency": 0.1, "steps": 1, "status": hji.HJI_OK, "cells": 10},
+            1: {"arrival": 0.0, "latency": 0.2, "steps": 1, "status": hji.HJI_OK, "cells": 10},
+            2: {"arrival": 1.0},   # unfinished at wall = 5 s: latency >= 4 s
+            3: {"arrival": 4.5}}   # unfinished: latency >= 0.5 s
+    s = serve.summarize(recs, 5.0)
+    assert s["requests"] == 4 and s["completed"] == 2 and s["unfinished"] == 2
+    assert s["p99_ms"] >= 3800.0 and s["p99_is_lower_bound"]
+    assert abs(s["p50_ms"] - 350.0) < 1e-6 and s["p50_is_lower_bound"]
+    assert abs(s["completed_p50_ms"] - 150.0) < 1e-6
+    done_only = serve.summarize({k: recs[k] for k in (0, 1)}, 5.0)
+    assert not done_only["p99_is_lower_bound"] and done_only["unfinished"] == 0
+
+
+def test_quadrotor_mass_updates_go_to_the_vertical_subsystem():
+    import workloads as W
+    r = W.route_request({"t": 0.1, "kind": "quad4d", "side": 41, "change": "mass", "value": 1.2})
+    assert r["kind"] == "quadz" and r["side"] == 321 and r["value"] == 1.2
+    d = {"t": 0.1, "kind": "quad4d", "side": 41, "change": "disturbance", "value": 0.2}
+    assert W.route_request(d) == d
+    gd, dyn_fn, l = W.serving_system("quadz", 321)
+    assert gd["n"] == [321, 321]
+    assert abs(dyn_fn("mass", 1.25)["G"][1][0] - W.QUAD_KT / 1.25) < 1e-15
+    assert dyn_fn("disturbance", 0.2)["dhi"] == [0.2]

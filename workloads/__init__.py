@@ -211,13 +211,44 @@ def poisson_requests(rate=50.0, duration=60.0, seed=7715, quad_side=(31, 61),
     return out
 
 
+def quadz_side(side4d):
+    """Grid side of the vertical (p_z, v_z) subsystem that goes with a
+    quadrotor whose horizontal subsystems use `side4d` nodes per axis: eight
+    times the spacing refinement of one 4-D axis (31 -> 241, 61 -> 481)."""
+    return 8 * (int(side4d) - 1) + 1
+
+
+def route_request(req):
+    """Where a serving request lands.  Mass enters the near-hover quadrotor
+    of Eq. (22) only through the vertical thrust term, so a quadrotor `mass`
+    update is a solve of its 2-D vertical subsystem (grid side quadz_side);
+    a `disturbance` update re-solves a 4-D horizontal subsystem.  Double
+    integrator requests stay as they are."""
+    if req["kind"] == "quad4d" and req["change"] == "mass":
+        out = dict(req)
+        out["kind"] = "quadz"
+        out["side"] = quadz_side(req["side"])
+        return out
+    return req
+
+
 def serving_system(kind, side):
     """A resident system of the serving workload: (grid, dynamics factory
     taking (change, value), target l).  Double integrator: `mass` scales the
     control gain to 1/m, `disturbance` sets |d| on the velocity equation.
-    Quadrotor 4-D subsystem: `disturbance` sets |d| on v; `mass` leaves the
-    dynamics as they are (the horizontal subsystem of Eq. (22) has no mass
-    term), so that update converges from the resident value at once."""
+    Quadrotor 4-D subsystem: `disturbance` sets |d| on v (the horizontal
+    subsystem of Eq. (22) has no mass term; mass updates go to the vertical
+    subsystem, see route_request).  Quadrotor vertical subsystem (`quadz`):
+    `mass` sets m = value (base mass 1.0), `disturbance` sets |d| on v_z."""
+    if kind == "quadz":
+        gd = grid([side, side], QUADZ_BOX[0], QUADZ_BOX[1])
+        l = target_strip(gd, 0, 4.0)
+
+        def dyn(change, value):
+            if change == "mass":
+                return quad_z(mass=value, dmax=0.0)
+            return quad_z(mass=1.0, dmax=value)
+        return gd, dyn, l
     if kind == "di":
         gd = grid([side, side], [-2.0, -2.0], [2.0, 2.0])
         l = target_strip(gd, 0, 1.0)
