@@ -302,17 +302,14 @@ def main():
     # library's FMA microbenchmark, CUDA-event timed, fastest of five.
     peak, peak_ms = hji.peak_fma(prec, target_ms=20.0)
     peak_other, _ = hji.peak_fma("f64" if prec == "f32" else "f32", target_ms=20.0)
-    # DRAM bytes per stage launch (dram__bytes_read.sum + dram__bytes_write.sum)
-    # from an ncu capture of the current stage kernels; none is recorded for
-    # them at present (the last capture, of the kernels before the change to
-    # the last stage's step bookkeeping, gave 8.1, 12.2 and 16.2 MB for the
-    # three RK3 stages: the first touch of each field, everything else served
-    # by L2), so `traffic` is null.
-    traffic = None
+    # DRAM bytes per stage launch from the ncu capture of these kernels (mean
+    # over the three RK3 stages; cold caches under ncu, so an upper bound).
+    traffic = statistics.mean(DRAM_BYTES_DI1001)
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved_tflops / peak, "traffic": traffic,
                 "kernel": "stage_kernel<%s,2,WENO5> (per-stage, 3 per RK3 step)" % prec,
                 "flops_per_node_stage": FLOPS_PER_NODE_STAGE,
+                "traffic_per_stage": DRAM_BYTES_DI1001,
                 "mem_words_per_node_step": WORDS_PER_NODE_STEP[prec],
                 "peak_source": "measured: hji_peak_fma (%s FMA chains on every SM, "
                                "CUDA events, fastest of 5 launches of %.1f ms)" % (prec, peak_ms),
@@ -851,10 +848,22 @@ def _served_vs_f64(hji, torch, srv, reqs, records, opts, budget_s):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# each ENO2 stage kernel from an ncu capture of the current kernels, keyed by
-# (workload, stage); none is recorded for them at present, so `traffic` is
-# null.
-DRAM_BYTES_PER_LAUNCH = {}
+# each ENO2 stage kernel, keyed by (workload, stage), from the ncu capture
+# `ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,
+# dram__bytes_write.sum --clock-control none python bench.py
+# --profile-steps 2 --workload W` of the current stage kernels (mean of the
+# two launches of each stage; summaries under profiles/).
+DRAM_BYTES_PER_LAUNCH = {
+    ("di_8192^2", "first_stage"): (545649664 + 237907200 + 547152128 + 238781952) / 2,
+    ("di_8192^2", "fused_last_stage"): (1198846208 + 506711040 + 1201185280 + 505523456) / 2,
+    ("quad4d_61^4", "first_stage"): (121092352 + 36559616 + 121172992 + 36836352) / 2,
+    ("quad4d_61^4", "fused_last_stage"): (254417408 + 94041088 + 254025728 + 94262784) / 2,
+}
+# The same capture of the 1001^2 WENO5 stage kernels (first touch of each
+# field per launch: ncu flushes the caches between launches, so these are
+# upper bounds of what a launch inside a solve moves).
+DRAM_BYTES_DI1001 = [(8122112 + 8122368) / 2, (12158720 + 12157952) / 2,
+                     (16206080 + 16199936) / 2]
 
 
 def _measured_hbm():
@@ -952,7 +961,11 @@ def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=N
                      "updates_total": upd, "launches": launches, "clocks": clk,
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                                   "frac": gbs / peak, "peak_source": src,
-                                  "bytes_per_node_step": bytes_per_update, "traffic": None,
+                                  "bytes_per_node_step": bytes_per_update,
+                                  "traffic": (DRAM_BYTES_PER_LAUNCH.get((name, "first_stage"), 0) +
+                                              DRAM_BYTES_PER_LAUNCH.get((name, "fused_last_stage"), 0))
+                                  or None,
+                                  "traffic_unit": "DRAM bytes per RK2 step (both stage launches, ncu)",
                                   "method_per_stage": {"bytes_per_node_step": 24,
                                                        "achieved": gbs_stage,
                                                        "frac": gbs_stage / peak},

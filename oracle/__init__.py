@@ -28,6 +28,8 @@ PINS = {
     "one_sided": "exact on polynomials of the scheme's degree; convergence order on smooth data",
     "hamiltonian": "brute-force max-min over dense samples of U x D",
     "alpha_dt": "hand-computed values for the double integrator and quadrotor; brute force",
+    "control_at / optimal_control": "brute-force argmax-min over dense samples of U x D; "
+                                    "the double integrator's closed-form braking control",
     "step/solve": "closed-form double-integrator value (Sec. II-B cost, Eq. (3)-(4)); "
                   "1-D advection closed form; stationary case; refinement order; "
                   "Thm. 1 / Lemma 1 / Thm. 2 / Props. 1-2 / Remarks 1-2 orderings",
@@ -98,6 +100,8 @@ def _load():
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int64, _D, _D,
                                      _D, ctypes.POINTER(_Stats), _D, ctypes.c_int64,
                                      ctypes.c_double]
+        lib.oracle_control_at.argtypes = [_P, _D, _D, _D, _D]
+        lib.oracle_optimal_control.argtypes = [_P, ctypes.c_int, _D, _D, _D]
         lib.oracle_max_threads.restype = ctypes.c_int
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_ghost_width.argtypes = [ctypes.c_int]
@@ -283,6 +287,25 @@ def solve(P, l, k=None, scheme="eno2", rk=2, cfl=0.5, tol=1e-6, horizon=0.0, max
     if history:
         return V, stats, hist[: min(int(history), st.steps)]
     return V, stats
+
+
+def control_at(P, x, p):
+    """Eq. (9) at one state for the gradient p: (u*, d*)."""
+    x, p = _f64(x), _f64(p)
+    u = np.zeros(MAXU)
+    d = np.zeros(MAXU)
+    _load().oracle_control_at(ctypes.byref(P), _ptr(x), _ptr(p), _ptr(u), _ptr(d))
+    return u[: P.m].copy(), d[: P.q].copy()
+
+
+def optimal_control(P, scheme, V):
+    """Eq. (9) at every node of V: arrays u* of shape (m,) + V.shape and d*
+    of shape (q,) + V.shape."""
+    V = _f64(V)
+    u = np.zeros((max(P.m, 1),) + V.shape)
+    d = np.zeros((max(P.q, 1),) + V.shape)
+    _load().oracle_optimal_control(ctypes.byref(P), SCHEMES[scheme], _ptr(V), _ptr(u), _ptr(d))
+    return u[: P.m], d[: P.q]
 
 
 def max_threads():

@@ -358,6 +358,72 @@ static void spatial_operator(const oracle_problem* P, int scheme, const double* 
     }
 }
 
+/* -------------------------------------------- optimal control, Eq. (9) */
+
+/* Eq. (9) at one state: u* = argmax_u min_d <p, f(x,u,d)> with p standing
+ * for grad V(x), and the disturbance d* that attains the inner minimum for
+ * u*.  As for H, the max and min of these affine functions over boxes are
+ * attained at vertices, which are enumerated.  Ties: the U-vertices are
+ * visited from the all-upper vertex (bits 2^m - 1) down and a later vertex
+ * must be strictly better to replace the kept one; the D-vertices from the
+ * all-lower vertex (bits 0) up, again keeping the first of equal values. */
+void oracle_control_at(const oracle_problem* P, const double* x, const double* p, double* u_opt,
+                       double* d_opt) {
+    double u[OR_MAXU], d[OR_MAXU], f[OR_MAXD];
+    double best = -INFINITY;
+    int best_ub = (1 << P->m) - 1, best_db = 0;
+    for (int ub = (1 << P->m) - 1; ub >= 0; --ub) {
+        box_vertex(P->m, P->ulo, P->uhi, ub, u);
+        double worst = INFINITY;
+        int worst_db = 0;
+        for (int db = 0; db < (1 << P->q); ++db) {
+            box_vertex(P->q, P->dlo, P->dhi, db, d);
+            oracle_dynamics(P, x, u, d, f);
+            double v = dot(P->ndim, p, f);
+            if (v < worst) {
+                worst = v;
+                worst_db = db;
+            }
+        }
+        if (worst > best) {
+            best = worst;
+            best_ub = ub;
+            best_db = worst_db;
+        }
+    }
+    box_vertex(P->m, P->ulo, P->uhi, best_ub, u_opt);
+    if (d_opt) box_vertex(P->q, P->dlo, P->dhi, best_db, d_opt);
+}
+
+/* Eq. (9) at every node of the grid for the value V: grad V is taken as the
+ * average of the scheme's one-sided derivatives, (p- + p+)/2, the same
+ * gradient at which the march evaluates the Hamiltonian (ghost nodes as in
+ * the march).  u_out holds m grid-shaped arrays one after another
+ * (u_out[j * N + node]), d_out (may be NULL) q of them. */
+void oracle_optimal_control(const oracle_problem* P, int scheme, const double* V, double* u_out,
+                            double* d_out) {
+    int64_t total = oracle_num_cells(P);
+    int g = ghost_width(scheme);
+    double dx[OR_MAXD];
+    for (int a = 0; a < P->ndim; ++a) dx[a] = oracle_spacing(P, a);
+#pragma omp parallel for schedule(static)
+    for (int64_t cidx = 0; cidx < total; ++cidx) {
+        int64_t idx[OR_MAXD];
+        double x[OR_MAXD], pbar[OR_MAXD], pm, pp, line[7], u[OR_MAXU], d[OR_MAXU];
+        unravel(P, cidx, idx);
+        node_coords(P, idx, x);
+        for (int a = 0; a < P->ndim; ++a) {
+            for (int o = -g; o <= g; ++o) line[o + g] = value_at(P, V, idx, a, o);
+            oracle_one_sided(scheme, line, dx[a], &pm, &pp);
+            pbar[a] = 0.5 * (pp + pm);
+        }
+        oracle_control_at(P, x, pbar, u, d);
+        for (int j = 0; j < P->m; ++j) u_out[(int64_t)j * total + cidx] = u[j];
+        if (d_out)
+            for (int k = 0; k < P->q; ++k) d_out[(int64_t)k * total + cidx] = d[k];
+    }
+}
+
 /* The operator L(W) on its own, exposed for tests. */
 int oracle_operator(const oracle_problem* P, int scheme, const double* alpha, const double* W,
                     double* L) {
