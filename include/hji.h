@@ -338,6 +338,24 @@ hji_status hji_stage_times(hji_grid g, const void* l, int ptr_is_device, const h
  * Synchronous on cuda_stream; the message is in hji_last_error(NULL). */
 hji_status hji_selftest_bounded_wait(int64_t limit_ns, void* cuda_stream);
 
+/* The instantaneous optimal control of Sec. II-B, Eq. (9),
+ *     u*(x) = argmax_u min_d <grad V(x), f(x,u,d)>,
+ * at every node of the grid's current value (normally a converged V*), and
+ * the disturbance d*(x) attaining the inner minimum.  grad V is the average
+ * (p- + p+)/2 of `scheme`'s one-sided derivatives (the gradient at which the
+ * march evaluates the Hamiltonian, same ghost nodes).  Over the boxes the
+ * choice separates by component: u*_j = uhi_j where (G^T grad V)_j >= 0, else
+ * ulo_j; d*_k = dlo_k where (E^T grad V)_k >= 0, else dhi_k (a zero
+ * component, where every value is optimal, takes uhi_j / dlo_k).  Computed
+ * in the grid's precision (FP32 grids: from the compensated value).
+ * u_out: m grid-shaped dense arrays one after another (u_out[j*N + node],
+ * N nodes, C order, the grid's precision); d_out: q such arrays, or NULL.
+ * Synchronous.  Errors: HJI_E_INVALID (NULL grid or u_out with m > 0,
+ * scheme, grid too small for the stencil), HJI_E_STATE (no dynamics or no
+ * value yet), HJI_E_NOMEM, HJI_E_CUDA. */
+hji_status hji_optimal_control(hji_grid g, hji_scheme scheme, void* u_out, void* d_out,
+                               int ptr_is_device, void* cuda_stream);
+
 /* Measured fused-multiply-add rate of the current GPU in `prec` (a
  * measurement aid for the arithmetic roofline of the stage kernels; the
  * paper has no counterpart).  Every thread of a grid that fills every SM

@@ -102,6 +102,7 @@ def _load():
                                      ctypes.c_double]
         lib.oracle_control_at.argtypes = [_P, _D, _D, _D, _D]
         lib.oracle_optimal_control.argtypes = [_P, ctypes.c_int, _D, _D, _D]
+        lib.oracle_gradient.argtypes = [_P, ctypes.c_int, _D, _D]
         lib.oracle_max_threads.restype = ctypes.c_int
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_ghost_width.argtypes = [ctypes.c_int]
@@ -306,6 +307,14 @@ def optimal_control(P, scheme, V):
     d = np.zeros((max(P.q, 1),) + V.shape)
     _load().oracle_optimal_control(ctypes.byref(P), SCHEMES[scheme], _ptr(V), _ptr(u), _ptr(d))
     return u[: P.m], d[: P.q]
+
+
+def gradient(P, scheme, V):
+    """(p- + p+)/2 at every node: shape (ndim,) + V.shape."""
+    V = _f64(V)
+    g = np.zeros((P.ndim,) + V.shape)
+    _load().oracle_gradient(ctypes.byref(P), SCHEMES[scheme], _ptr(V), _ptr(g))
+    return g
 
 
 def max_threads():

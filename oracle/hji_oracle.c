@@ -424,6 +424,27 @@ void oracle_optimal_control(const oracle_problem* P, int scheme, const double* V
     }
 }
 
+/* The averaged gradient (p- + p+)/2 of the scheme at every node (grad[a * N
+ * + node]), the gradient oracle_optimal_control uses; exposed for tests that
+ * need to know where a control choice is decided by a clear margin. */
+void oracle_gradient(const oracle_problem* P, int scheme, const double* V, double* grad) {
+    int64_t total = oracle_num_cells(P);
+    int g = ghost_width(scheme);
+    double dx[OR_MAXD];
+    for (int a = 0; a < P->ndim; ++a) dx[a] = oracle_spacing(P, a);
+#pragma omp parallel for schedule(static)
+    for (int64_t cidx = 0; cidx < total; ++cidx) {
+        int64_t idx[OR_MAXD];
+        double pm, pp, line[7];
+        unravel(P, cidx, idx);
+        for (int a = 0; a < P->ndim; ++a) {
+            for (int o = -g; o <= g; ++o) line[o + g] = value_at(P, V, idx, a, o);
+            oracle_one_sided(scheme, line, dx[a], &pm, &pp);
+            grad[(int64_t)a * total + cidx] = 0.5 * (pp + pm);
+        }
+    }
+}
+
 /* The operator L(W) on its own, exposed for tests. */
 int oracle_operator(const oracle_problem* P, int scheme, const double* alpha, const double* W,
                     double* L) {

@@ -36,7 +36,7 @@ EXPORTS = ["hji_grid_create", "hji_grid_destroy", "hji_dynamics_set", "hji_solve
            "hji_engine_create", "hji_engine_submit", "hji_engine_step", "hji_engine_poll",
            "hji_engine_destroy", "hji_engine_last_error", "hji_autotune",
            "hji_stage_times", "hji_selftest_bounded_wait", "hji_peak_fma",
-           "hji_peak_last_error"]
+           "hji_peak_last_error", "hji_optimal_control"]
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -135,6 +135,7 @@ def load(build_if_missing=False):
     lib.hji_stage_times.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(hji_solve_opts),
                                     ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double)]
     lib.hji_peak_fma.argtypes = [ctypes.c_int, ctypes.c_double, vp, dp, dp]
+    lib.hji_optimal_control.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, vp]
     lib.hji_peak_last_error.argtypes = []
     lib.hji_peak_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -198,6 +199,10 @@ def hji_autotune(g, l, ptr_is_device, opts, steps, stream, chosen, ms_per_step):
 
 def hji_stage_times(g, l, ptr_is_device, opts, steps, stream, ms_per_stage):
     return load().hji_stage_times(g, l, ptr_is_device, opts, steps, stream, ms_per_stage)
+
+
+def hji_optimal_control(g, scheme, u_out, d_out, ptr_is_device, stream):
+    return load().hji_optimal_control(g, scheme, u_out, d_out, ptr_is_device, stream)
 
 
 def hji_peak_fma(prec, target_ms, stream, tflops, ms_per_launch):
@@ -361,6 +366,18 @@ class Grid:
     def set_dynamics(self, dyn):
         s, keep = dynamics_struct(dyn, self.ndim)
         _check(hji_dynamics_set(self._h, ctypes.byref(s)), self._h)
+        self._mq = (s.m, s.q)
+
+    def optimal_control(self, scheme="eno2", stream=None):
+        """Eq. (9) at every node of the current value: numpy arrays u* of
+        shape (m,) + grid shape and d* of shape (q,) + grid shape."""
+        m, q = self._mq
+        u = np.zeros((max(m, 1),) + self.shape, dtype=self.dtype)
+        d = np.zeros((max(q, 1),) + self.shape, dtype=self.dtype)
+        _check(hji_optimal_control(self._h, SCHEMES[scheme], u.ctypes.data,
+                                   d.ctypes.data if q else None, 0, self._stream(stream)),
+               self._h)
+        return u[:m], d[:q]
 
     def _ptr(self, a):
         """(pointer, is_device, keepalive) for a numpy array or CUDA tensor."""

@@ -1309,6 +1309,65 @@ hji_status hji_selftest_bounded_wait(int64_t limit_ns, void* cuda_stream) {
     return fail(nullptr, HJI_E_CUDA, "self-test kernel wrote no result");
 }
 
+hji_status hji_optimal_control(hji_grid g, hji_scheme scheme, void* u_out, void* d_out,
+                               int ptr_is_device, void* cuda_stream) {
+    if (!g) return fail(nullptr, HJI_E_INVALID, "grid is NULL");
+    if (scheme != HJI_ENO1 && scheme != HJI_ENO2 && scheme != HJI_WENO5)
+        return fail(g, HJI_E_INVALID, "unknown scheme");
+    if (!g->has_dyn) return fail(g, HJI_E_STATE, "dynamics not set");
+    if (!g->has_value) return fail(g, HJI_E_STATE, "no value yet");
+    const int m = g->dyn.m, q = g->dyn.q;
+    if (m > 0 && !u_out) return fail(g, HJI_E_INVALID, "u_out is NULL");
+    const int gw = hji::ghost_width(scheme);
+    for (int a = 0; a < g->ndim; ++a)
+        if (g->n[a] < 2 * gw + 1) return fail(g, HJI_E_INVALID, "grid too small for the scheme's stencil");
+    if (m == 0 && (q == 0 || !d_out)) return HJI_OK;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    hji::ControlArgs A;
+    std::memset(&A, 0, sizeof(A));
+    for (int a = 0; a < HJI_MAX_DIM; ++a) {
+        A.n[a] = a < g->ndim ? (int)g->n[a] : 1;
+        A.periodic[a] = a < g->ndim ? g->periodic[a] : 0;
+        A.inv_dx[a] = a < g->ndim ? 1.0 / g->dx[a] : 1.0;
+    }
+    field_strides(g->ndim, g->n, g->pitch, A.stride);
+    A.v_hi = g->V[g->cur];
+    A.v_lo = g->prec == HJI_F32 ? g->Vlo[g->cur] : nullptr;
+    std::memcpy(A.G, g->dyn.G, sizeof(A.G));
+    std::memcpy(A.E, g->dyn.E, sizeof(A.E));
+    std::memcpy(A.ulo, g->dyn.ulo, sizeof(A.ulo));
+    std::memcpy(A.uhi, g->dyn.uhi, sizeof(A.uhi));
+    std::memcpy(A.dlo, g->dyn.dlo, sizeof(A.dlo));
+    std::memcpy(A.dhi, g->dyn.dhi, sizeof(A.dhi));
+    A.m = m;
+    A.q = d_out ? q : 0;
+    A.ncells = g->ncells;
+    const size_t ubytes = (size_t)m * g->ncells * g->esize;
+    const size_t dbytes = (size_t)A.q * g->ncells * g->esize;
+    void* tmp = nullptr;
+    if (ptr_is_device) {
+        A.u_out = u_out;
+        A.d_out = A.q ? d_out : nullptr;
+    } else {
+        tmp = dev_alloc(g, ubytes + dbytes, s);
+        if (!tmp) return fail(g, HJI_E_NOMEM, "control output allocation failed");
+        A.u_out = tmp;
+        A.d_out = A.q ? static_cast<unsigned char*>(tmp) + ubytes : nullptr;
+    }
+    cudaError_t e = hji::launch_control(A, g->prec == HJI_F32, g->ndim, scheme, s);
+    if (e == cudaSuccess && !ptr_is_device) {
+        if (ubytes) e = cudaMemcpyAsync(u_out, A.u_out, ubytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && dbytes) e = cudaMemcpyAsync(d_out, A.d_out, dbytes, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (tmp) {
+        dev_free(g, tmp, s);
+        cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) return cuda_fail(g, e, "optimal control");
+    return HJI_OK;
+}
+
 hji_status hji_grid_info(hji_grid g, int* ndim, int64_t* n, int64_t* num_nodes) {
     if (!g) return fail(nullptr, HJI_E_INVALID, "grid is NULL");
     if (ndim) *ndim = g->ndim;

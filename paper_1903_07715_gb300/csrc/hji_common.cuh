@@ -189,6 +189,25 @@ StageLauncher stage_launcher_f32(int ndim, int scheme, bool last, int variant = 
 int stage_max_blocks_f64(int ndim, int scheme, bool last, int variant = 0);
 int stage_max_blocks_f32(int ndim, int scheme, bool last, int variant = 0);
 
+// Arguments of the optimal-control pass (hji_control.cu): a grid's current
+// value (padded C-order fields; FP32 grids add the low word) and the input
+// matrices and bounds, in FP64 (converted to the kernel's precision).
+struct ControlArgs {
+    int n[MAXD];
+    int periodic[MAXD];
+    long long stride[MAXD];
+    double inv_dx[MAXD];
+    const void* v_hi;
+    const void* v_lo;   // FP32: low word of the value (null for FP64)
+    double G[MAXD * MAXU], E[MAXD * MAXU];
+    double ulo[MAXU], uhi[MAXU], dlo[MAXU], dhi[MAXU];
+    int m, q;
+    long long ncells;
+    void* u_out;        // m dense grid-shaped arrays, one after another
+    void* d_out;        // q of them, or null
+};
+cudaError_t launch_control(const ControlArgs& a, bool f32, int ndim, int scheme, cudaStream_t s);
+
 // Set-up kernels (hji_setup.cu).
 cudaError_t launch_setup(const InstDesc* d_insts, const InstDesc* h_insts, int count, bool f32,
                          cudaStream_t s);
