@@ -137,7 +137,7 @@ typedef enum {
  * horizon >= 0: stop once tau >= horizon (0 = none).  max_steps: step cap
  * (<= 0 means 1,000,000).  check_every: steps per host check of the stop
  * flag (<= 0 means 32); steps after the stop point never run.  Results do
- * not depend on check_every or the tile shape. */
+ * not depend on check_every or the tile shape (see march below). */
 typedef struct {
     hji_scheme scheme;
     int rk_order;
@@ -152,7 +152,33 @@ typedef struct {
     double tol_rate;  /* >= 0: the test becomes max|dV| < tol + tol_rate * dt, a
                          bound on the rate of change; tol = 0, tol_rate = 0.1 is
                          Sec. IV's rule (change < 0.001 per 0.01 of time) */
+    int march;        /* how the steps are launched (results are identical):
+                         HJI_MARCH_AUTO, HJI_MARCH_PER_STAGE or
+                         HJI_MARCH_MULTI_STEP */
+    double interval;  /* > 0: also stop once the largest change of V over one
+                         interval of this much time is below interval_tol:
+                         Sec. V's test (interval 0.01, interval_tol 0.001).
+                         An interval is K = max(1, round(interval / dt)) CFL
+                         steps; V is compared with its copy from K steps
+                         earlier after every K-th step.  0: off. */
+    double interval_tol; /* >= 0, see interval */
 } hji_solve_opts;
+
+/* hji_solve_opts.march.  PER_STAGE: one kernel launch per Runge-Kutta
+ * stage, check_every steps captured in one CUDA graph.  MULTI_STEP: one
+ * cooperative launch runs every stage of check_every steps, with a
+ * bounded grid-wide barrier after each stage (no launch gaps, no per-launch
+ * ramp and tail); it needs every CTA resident at once and falls back to
+ * PER_STAGE where that cannot be launched.  AUTO: MULTI_STEP for 1-D and
+ * 2-D grids, PER_STAGE otherwise (the 3-D/4-D multi-step kernels would spill
+ * registers).  Both forms run the same per-node arithmetic from the same
+ * source; compiled as different kernels, the compiler may fuse a different
+ * set of multiply-adds, so their results agree to rounding, not bit for bit.
+ * Within one form, results do not depend on check_every, on the batch an
+ * instance marches in, or on the tile shape. */
+#define HJI_MARCH_AUTO 0
+#define HJI_MARCH_PER_STAGE 1
+#define HJI_MARCH_MULTI_STEP 2
 
 typedef struct {
     int64_t steps;       /* full Runge-Kutta steps taken                      */
@@ -209,11 +235,14 @@ hji_status hji_value_get(hji_grid g, void* out, int ptr_is_device, void* cuda_st
  * NULL otherwise) and v_out (output, grid-shaped, the grid's precision; for
  * HJI_INIT_RESIDENT it also holds the previous value on entry).  Grid,
  * dynamics and options mean what they mean for hji_grid_create,
- * hji_dynamics_set and hji_solve, with two differences: tile_variant 0
- * takes the default tile shape (no autotuned choice is consulted), and an
- * FP32 HJI_INIT_RESIDENT start begins from the float values in v_out alone,
- * while hji_solve's resident FP32 start also carries the low words of its
- * compensated value, so the two marches may differ by FP32 rounding.
+ * hji_dynamics_set and hji_solve, with these differences: tile_variant 0
+ * takes the default tile shape (no autotuned choice is consulted); the
+ * march always launches one kernel per RK stage (opts.march is ignored);
+ * the interval test needs a snapshot buffer and is refused (opts.interval
+ * != 0 returns HJI_E_INVALID); and an FP32 HJI_INIT_RESIDENT start begins
+ * from the float values in v_out alone, while hji_solve's resident FP32
+ * start also carries the low words of its compensated value, so the two
+ * marches may differ by FP32 rounding.
  * Every scratch buffer lives in one static
  * device array of HJI_NOALLOC_SCRATCH_BYTES bytes that each GPU loading the
  * library holds until exit; a grid that needs more (5 values per node for
@@ -260,7 +289,10 @@ hji_status hji_value_transfer(hji_grid dst, hji_grid src, void* cuda_stream);
  * next step.  A request's arithmetic does not depend on what else is in the
  * batch, so its result equals a solo hji_solve bit for bit.
  * All grids of an engine share ndim and precision; the options (scheme,
- * rk_order, cfl, tol, horizon, max_steps, check_every) are the engine's.
+ * rk_order, cfl, tol, tol_rate, interval, interval_tol, horizon, max_steps,
+ * check_every) are the engine's.  Engines always launch one kernel per RK
+ * stage (opts.march is ignored), so that engines on different streams
+ * interleave on the device.
  * hji_engine_step never blocks on the chunk it launches: it waits for the
  * previous chunk, retires and admits, then launches the next, so engines on
  * different streams overlap on the device when stepped in turn. */

@@ -99,7 +99,7 @@ def _load():
         lib.oracle_solve.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int64, _D, _D,
                                      _D, ctypes.POINTER(_Stats), _D, ctypes.c_int64,
-                                     ctypes.c_double]
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_double]
         lib.oracle_control_at.argtypes = [_P, _D, _D, _D, _D]
         lib.oracle_optimal_control.argtypes = [_P, ctypes.c_int, _D, _D, _D]
         lib.oracle_gradient.argtypes = [_P, ctypes.c_int, _D, _D]
@@ -269,9 +269,10 @@ def step(P, scheme, rk, dt, alpha, l, V):
 
 
 def solve(P, l, k=None, scheme="eno2", rk=2, cfl=0.5, tol=1e-6, horizon=0.0, max_steps=0,
-          history=0, tol_rate=0.0):
-    """March to convergence (max|dV| < tol + tol_rate dt).  Returns
-    (V, stats dict[, history array])."""
+          history=0, tol_rate=0.0, interval=0.0, interval_tol=0.0):
+    """March to convergence: max|dV| of one step < tol + tol_rate dt, or (with
+    interval > 0) the change of V over K = round(interval / dt) steps below
+    interval_tol (Sec. V).  Returns (V, stats dict[, history array])."""
     l = _f64(l)
     V = np.empty_like(l)
     kk = None if k is None else _f64(k)
@@ -280,7 +281,8 @@ def solve(P, l, k=None, scheme="eno2", rk=2, cfl=0.5, tol=1e-6, horizon=0.0, max
     rc = _load().oracle_solve(ctypes.byref(P), SCHEMES[scheme], int(rk), float(cfl), float(tol),
                               float(horizon), int(max_steps), _ptr(l),
                               None if kk is None else _ptr(kk), _ptr(V), ctypes.byref(st),
-                              _ptr(hist), int(history), float(tol_rate))
+                              _ptr(hist), int(history), float(tol_rate), float(interval),
+                              float(interval_tol))
     if rc < 0:
         raise ValueError("oracle_solve rejected its input")
     stats = {"steps": st.steps, "tau": st.tau, "dt": st.dt, "last_delta": st.last_delta,

@@ -109,6 +109,7 @@ struct hji_grid_s {
     void* W2 = nullptr;
     void* Vlo[2] = {nullptr, nullptr};  // FP32 grids: low words of the compensated value (with V[])
     void* l = nullptr;
+    void* snap = nullptr;            // snapshot of V for the interval test (allocated on first use)
     void* table = nullptr;
     size_t table_bytes = 0;
     InstState* state = nullptr;      // device
@@ -364,12 +365,22 @@ hji_status validate_opts(hji_grid g, const hji_solve_opts* o) {
         return fail(g, HJI_E_INVALID, "tol_rate must be finite and >= 0");
     if (o->tile_variant < 0 || o->tile_variant > hji::kTileVariants)
         return fail(g, HJI_E_INVALID, "tile_variant must be 0..HJI_TILE_VARIANTS");
+    if (o->march < HJI_MARCH_AUTO || o->march > HJI_MARCH_MULTI_STEP)
+        return fail(g, HJI_E_INVALID, "unknown march mode");
+    if (!(o->interval >= 0.0) || !std::isfinite(o->interval) || !(o->interval_tol >= 0.0) ||
+        !std::isfinite(o->interval_tol))
+        return fail(g, HJI_E_INVALID, "interval and interval_tol must be finite and >= 0");
     return HJI_OK;
 }
 
-// Make sure the stage buffers and the term table exist for this solve.
-hji_status ensure_buffers(hji_grid g, int rk, cudaStream_t s) {
+// Make sure the stage buffers, the interval test's snapshot and the term
+// table exist for this solve.
+hji_status ensure_buffers(hji_grid g, int rk, cudaStream_t s, bool snapshot) {
     const size_t bytes = (size_t)g->nalloc * g->esize;
+    if (snapshot && !g->snap) {
+        g->snap = dev_alloc(g, bytes, s);
+        if (!g->snap) return fail(g, HJI_E_NOMEM, "snapshot buffer allocation failed");
+    }
     if (rk >= 2 && !g->W1) {
         g->W1 = dev_alloc(g, bytes, s);
         if (!g->W1) return fail(g, HJI_E_NOMEM, "stage buffer allocation failed");
@@ -415,6 +426,9 @@ hji_status make_desc(hji_grid g, const hji_solve_opts* o, int* active, int varia
     D.cfl = o->cfl;
     D.tol = o->tol;
     D.tol_rate = o->tol_rate;
+    D.interval = o->interval;
+    D.interval_tol = o->interval_tol;
+    D.snap = o->interval > 0.0 ? g->snap : nullptr;
     D.horizon = o->horizon;
     D.max_steps = o->max_steps > 0 ? o->max_steps : 1000000;
     D.V[0] = g->V[0];
@@ -475,6 +489,50 @@ hji_status capture_chunk(hji_grid g, cudaStream_t cap, bool f32, int ndim, int s
     if (e != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
         return cuda_fail(g, e, "stage launch during capture");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(g, e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaGraphInstantiate");
+    return HJI_OK;
+}
+
+// Capture one multi-step march launch (every stage of `steps` steps, with
+// grid-wide barriers) into a graph: the barrier counter is zeroed first.
+hji_status capture_march(hji_grid g, cudaStream_t cap, bool f32, int ndim, int scheme, int rk,
+                         int steps, const hji::StageArgs& base, int grid, int variant,
+                         const int* active, unsigned* barrier, int* fault, cudaGraphExec_t* out) {
+    hji::MarchLauncher L = f32 ? hji::march_launcher_f32(ndim, scheme, variant)
+                               : hji::march_launcher_f64(ndim, scheme, variant);
+    if (!L) return fail(g, HJI_E_INVALID, "no march kernel for this ndim/scheme");
+    StagePlan plan[3];
+    const int ns = rk_plan(rk, plan);
+    hji::MarchArgs m;
+    std::memset(&m, 0, sizeof(m));
+    for (int i = 0; i < ns; ++i) {
+        hji::StageArgs a = base;
+        a.stage_in = plan[i].in;
+        a.stage_out = plan[i].out;
+        a.aV = plan[i].aV;
+        a.aE = plan[i].aE;
+        a.aVf = (float)plan[i].aV;
+        a.aEf = (float)plan[i].aE;
+        a.reads_v = plan[i].aV != 0.0 ? 1 : 0;
+        m.st[i] = a;
+    }
+    m.ns = ns;
+    m.steps = steps;
+    m.barrier = barrier;
+    m.active = active;
+    m.fault = fault;
+    HJI_CUDA(g, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemsetAsync(barrier, 0, sizeof(unsigned), cap);
+    if (e == cudaSuccess) e = L(m, grid, cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(g, e, "march launch during capture");
     }
     if (e2 != cudaSuccess) return cuda_fail(g, e2, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(out, graph, 0);
@@ -559,7 +617,7 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
             return fail(g, HJI_E_STATE, "HJI_INIT_RESIDENT without a previous value");
         for (int j = 0; j < i; ++j)
             if (grids[j] == g) return fail(g0, HJI_E_INVALID, "grid listed twice in a batch");
-        st = ensure_buffers(g, o->rk_order, s);
+        st = ensure_buffers(g, o->rk_order, s, o->interval > 0.0);
         if (st != HJI_OK) return st;
     }
     const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -677,27 +735,49 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
     }
 
     // The march: graphs of `chunk` steps, one in flight ahead of the check.
+    // Each graph is either one launch per RK stage, or one multi-step march
+    // launch (every CTA resident: at most march_max_blocks per SM).
     const int chunk = o->check_every > 0 ? o->check_every : 32;
-    const int grid[2] = {stage_grid(f32, ndim, o->scheme, total_tiles, variant, false),
-                         stage_grid(f32, ndim, o->scheme, total_tiles, variant, true)};
+    bool multi = !g_stage_timer && (o->march == HJI_MARCH_MULTI_STEP ||
+                                    (o->march == HJI_MARCH_AUTO && ndim <= 2));
+    int mgrid = 0;
+    if (multi) {
+        const int b = f32 ? hji::march_max_blocks_f32(ndim, o->scheme, variant)
+                          : hji::march_max_blocks_f64(ndim, o->scheme, variant);
+        long long gm = (long long)num_sms() * b;
+        if (gm > total_tiles) gm = total_tiles;
+        mgrid = (int)gm;
+        multi = mgrid >= 1;
+    }
+    const int grid[2] = {multi ? mgrid : stage_grid(f32, ndim, o->scheme, total_tiles, variant, false),
+                         multi ? 0 : stage_grid(f32, ndim, o->scheme, total_tiles, variant, true)};
     hji::StageArgs base{d_desc, d_tiles, d_ntiles, 0, 0, 0.0, 0.0, 0.0f, 0.0f, 0};
+    unsigned* d_barrier = reinterpret_cast<unsigned*>(d_active + 2);
+    int* d_fault = d_active + 3;
     cudaGraphExec_t exec = nullptr;
     // The graph's kernels read descriptors, tile list and its length from the
     // leader's scratch, so it stays valid while those buffers and the launch
-    // shape (scheme, RK order, chunk, grid, tile shape) are unchanged.
-    const long long key[8] = {(long long)o->scheme, o->rk_order, chunk, grid[0], grid[1], variant, ndim,
-                              f32 ? 1 : 0};
+    // shape (scheme, RK order, chunk, grid, tile shape, launch mode) are
+    // unchanged.
+    const long long key[8] = {(long long)o->scheme, o->rk_order, chunk, grid[0], grid[1],
+                              variant + (multi ? 16 : 0), ndim, f32 ? 1 : 0};
     if (g_stage_timer) {
         // the timed march launches its stages one by one
     } else if (g0->graph && std::memcmp(key, g0->graph_key, sizeof(key)) == 0) {
         exec = g0->graph;
     } else {
         drop_graph();
-        st = capture_chunk(g0, g0->cap_stream, f32, ndim, o->scheme, o->rk_order, chunk, base, grid,
-                           variant, &exec);
+        st = multi ? capture_march(g0, g0->cap_stream, f32, ndim, o->scheme, o->rk_order, chunk, base,
+                                   mgrid, variant, d_active, d_barrier, d_fault, &exec)
+                   : capture_chunk(g0, g0->cap_stream, f32, ndim, o->scheme, o->rk_order, chunk, base,
+                                   grid, variant, &exec);
         if (st != HJI_OK) return st;
         g0->graph = exec;
         std::memcpy(g0->graph_key, key, sizeof(key));
+    }
+    if (multi) {
+        e = cudaMemsetAsync(d_fault, 0, sizeof(int), s);
+        if (e != cudaSuccess) return cuda_fail(g0, e, "march fault flag");
     }
     long long stage_launches = 0;
     if (g_stage_timer) {
@@ -726,7 +806,7 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         cudaEventDestroy(ev[0]);
         cudaEventDestroy(ev[1]);
-        stage_launches = graphs * (long long)chunk * o->rk_order;
+        stage_launches = multi ? graphs : graphs * (long long)chunk * o->rk_order;
         if (e != cudaSuccess) {
             cleanup();
             return cuda_fail(g0, e, "march");
@@ -736,7 +816,11 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
         e = cudaMemcpyAsync(grids[i]->h_state, grids[i]->state, sizeof(InstState), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) break;
     }
+    int h_fault = 0;
+    if (e == cudaSuccess && multi)
+        e = cudaMemcpyAsync(&g0->h_active[1], d_fault, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && multi) h_fault = g0->h_active[1];
     cleanup();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(g0, e, "final state");
@@ -752,6 +836,8 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
             si = fail(g, HJI_E_NONFINITE, "the march produced NaN or Inf");
         } else if (S.status == 4) {
             si = fail(g, HJI_E_TIMEOUT, "a bounded device wait gave up (a tile copy never arrived)");
+        } else if (h_fault) {
+            si = fail(g, HJI_E_TIMEOUT, "a bounded grid-barrier wait of the march kernel gave up");
         } else if (!S.converged) {
             si = fail(g, HJI_E_NOT_CONVERGED, "stopped by the horizon or the step cap");
         }
@@ -842,7 +928,9 @@ hji_status hji_grid_create(int ndim, const int64_t* n, const double* lo, const d
     g->state = (InstState*)dev_alloc(g, sizeof(InstState), s);
     g->d_desc = (InstDesc*)dev_alloc(g, sizeof(InstDesc), s);
     g->desc_cap = g->d_desc ? 1 : 0;
-    g->d_active = (int*)dev_alloc(g, sizeof(int) * 2, s);
+    // [0] marching instances, [1] tiles in the list, [2] grid-barrier counter
+    // and [3] fault flag of the multi-step march kernel
+    g->d_active = (int*)dev_alloc(g, sizeof(int) * 4, s);
     bool ok = g->V[0] && g->V[1] && g->l && g->state && g->d_desc && g->d_active &&
               (prec != HJI_F32 || (g->Vlo[0] && g->Vlo[1]));
     g->d_ntiles = ok ? g->d_active + 1 : nullptr;
@@ -864,8 +952,8 @@ hji_status hji_grid_destroy(hji_grid g) {
     cudaStream_t s = nullptr;
     cudaStreamSynchronize(s);
     if (g->graph) cudaGraphExecDestroy(g->graph);
-    void* bufs[] = {g->V[0], g->V[1], g->W1, g->W2, g->Vlo[0], g->Vlo[1], g->l, g->table, g->state,
-                    g->d_desc, g->d_active, g->d_tiles};
+    void* bufs[] = {g->V[0], g->V[1], g->W1, g->W2, g->Vlo[0], g->Vlo[1], g->l, g->snap, g->table,
+                    g->state, g->d_desc, g->d_active, g->d_tiles};
     for (void* p : bufs) dev_free(g, p, s);
     if (g->h_state) cudaFreeHost(g->h_state);
     if (g->h_active) cudaFreeHost(g->h_active);
@@ -1057,7 +1145,7 @@ hji_status hji_engine_submit(hji_engine e, hji_grid g, const void* l, const void
         if (r.g == g) return efail(e, HJI_E_STATE, "grid already has a queued request");
     for (const auto& sl : e->slots)
         if (sl.used && sl.g == g) return efail(e, HJI_E_STATE, "grid already has a marching request");
-    hji_status st = ensure_buffers(g, e->o.rk_order, e->s);
+    hji_status st = ensure_buffers(g, e->o.rk_order, e->s, e->o.interval > 0.0);
     if (st != HJI_OK) return efail(e, st, g->err);
     if (e->budget && grid_bytes(g, e->o.rk_order) > e->budget)
         return efail(e, HJI_E_INVALID, "grid larger than the engine's whole budget");

@@ -69,6 +69,11 @@ struct InstState {
     CtxConst<double> kd;  // the stage kernels' constants (set-up pass)
     CtxConst<float> kf;
     double stop_delta;    // tol + tol_rate dt: a step whose max|dV| is below it converges
+    // Interval test (Sec. V): every K-th step compares V with the snapshot
+    // taken K steps earlier; K = 0 when the test is off.
+    long long interval_K;
+    unsigned long long interval_bits;  // max|V - snapshot| of the step in flight (bits of a double)
+    double last_interval_change;       // of the last finished interval
 };
 
 // Tensor maps of one instance (TMA descriptors, encoded on the host):
@@ -100,6 +105,8 @@ struct InstDesc {
     double lo[MAXD], dx[MAXD];
     Dyn dyn;
     double cfl, tol, horizon, tol_rate;
+    double interval, interval_tol;  // Sec. V's interval test (interval 0: off)
+    void* snap;               // its snapshot of V (the high word for FP32), or null
     long long max_steps;
     void* V[2];               // ping-pong value buffers: V[cur] = V^n
     void* W1;                 // stage buffers of the Runge-Kutta step: stage
@@ -181,6 +188,23 @@ struct StageArgs {
 };
 
 using StageLauncher = cudaError_t (*)(const StageArgs&, int grid, cudaStream_t);
+
+// Arguments of the multi-step march kernel: one cooperative launch runs
+// every RK stage (st[0..ns-1]) of up to `steps` steps, with a grid-wide
+// barrier after each stage, and ends early once no instance is marching.
+struct MarchArgs {
+    StageArgs st[3];
+    int ns;            // RK stages per step
+    int steps;         // steps this launch may run
+    unsigned* barrier; // grid-barrier counter, zero at launch
+    const int* active; // instances of the batch still marching
+    int* fault;        // set to 1 when a bounded wait gave up
+};
+using MarchLauncher = cudaError_t (*)(const MarchArgs&, int grid, cudaStream_t);
+MarchLauncher march_launcher_f64(int ndim, int scheme, int variant = 0);
+MarchLauncher march_launcher_f32(int ndim, int scheme, int variant = 0);
+int march_max_blocks_f64(int ndim, int scheme, int variant = 0);
+int march_max_blocks_f32(int ndim, int scheme, int variant = 0);
 
 // Kernel dispatch tables (one per precision); `variant` selects the tile
 // shape (only 2-D grids have more than variant 0).

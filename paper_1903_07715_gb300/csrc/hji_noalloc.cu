@@ -171,6 +171,8 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
         return nfail(HJI_E_INVALID, "tol_rate must be finite and >= 0");
     if (o->tile_variant < 0 || o->tile_variant > hji::kTileVariants)
         return nfail(HJI_E_INVALID, "tile_variant must be 0..HJI_TILE_VARIANTS");
+    if (o->interval != 0.0)
+        return nfail(HJI_E_INVALID, "the interval test is not available without allocation");
     if (o->init == HJI_INIT_USER_K && !k) return nfail(HJI_E_INVALID, "HJI_INIT_USER_K needs k");
     if (o->init != HJI_INIT_STANDARD && o->init != HJI_INIT_USER_K && o->init != HJI_INIT_RESIDENT)
         return nfail(HJI_E_INVALID, "unknown init mode");

@@ -79,6 +79,13 @@ __device__ void fill_ctx_const(const InstDesc& D, InstState* st) {
     kd.dt = st->dt;
     kf.dt = static_cast<float>(st->dt);
     st->stop_delta = D.tol + D.tol_rate * st->dt;
+    long long K = 0;
+    if (D.interval > 0.0 && D.snap != nullptr) {
+        K = llround(D.interval / st->dt);
+        if (K < 1) K = 1;
+    }
+    st->interval_K = K;
+    st->interval_bits = 0ull;
 }
 
 __global__ void __launch_bounds__(kThreads) alpha_kernel(const InstDesc* __restrict__ insts) {
@@ -250,6 +257,7 @@ __global__ void __launch_bounds__(kThreads) init_kernel(const InstDesc* __restri
     // FP32 grids: the low word of V starts at zero, or, when k is the grid's
     // own resident value, keeps that value's low word.
     T* Vlo = static_cast<T*>(D.Vlo[0]);
+    T* snap = static_cast<T*>(D.snap);
     // Fields are rows of the fastest axis padded to the pitch; pad elements
     // are left alone.
     const int nx = D.n[D.ndim - 1];
@@ -276,6 +284,7 @@ __global__ void __launch_bounds__(kThreads) init_kernel(const InstDesc* __restri
         }
         V[c] = v;
         if (Vlo != nullptr) Vlo[c] = vlo;
+        if (snap != nullptr) snap[c] = v;  // the interval test's first reference
     }
     bad = __any_sync(0xffffffffu, bad) ? 1u : 0u;
     if (bad && (threadIdx.x & 31) == 0) atomicOr(&D.state->nonfinite, 1u);

@@ -179,14 +179,24 @@ struct Pair {
     T h, l;
 };
 
-template <typename T>
+// Loads of fields a kernel never writes go through the read-only data path
+// (__ldg).  COH = true marks a caller (the multi-step march kernel) in which
+// the field may have been written earlier in the same launch by another CTA:
+// those loads are made at L2 (__ldcg), which is coherent, instead.
+template <bool COH, typename T>
+__device__ __forceinline__ T ld_field(const T* p) {
+    if constexpr (COH) return __ldcg(p);
+    else return __ldg(p);
+}
+
+template <typename T, bool COH = false>
 __device__ __forceinline__ Pair<T> load_pair(const T* __restrict__ h, const T* __restrict__ lo,
                                             const T* __restrict__ d, long long i) {
     Pair<T> p;
-    p.h = __ldg(h + i);
+    p.h = ld_field<COH>(h + i);
     p.l = T(0);
-    if (lo != nullptr) p.l = __ldg(lo + i);
-    if (d != nullptr) p.l += __ldg(d + i);
+    if (lo != nullptr) p.l = ld_field<COH>(lo + i);
+    if (d != nullptr) p.l += ld_field<COH>(d + i);
     return p;
 }
 
@@ -216,20 +226,20 @@ __device__ __forceinline__ Pair<T> extrapolate(Pair<T> e, Pair<T> i1, int k) {
 
 // Node j (possibly outside [0, n)) of a line with element stride s whose
 // node 0 is at element offset 0 of h/lo/d: periodic wrap, or extrapolation.
-template <typename T>
+template <typename T, bool COH = false>
 __device__ __forceinline__ Pair<T> line_pair(const T* __restrict__ h, const T* __restrict__ lo,
                                             const T* __restrict__ d, int j, int n, long long s,
                                             int periodic) {
-    if (j >= 0 && j < n) return load_pair(h, lo, d, (long long)j * s);
+    if (j >= 0 && j < n) return load_pair<T, COH>(h, lo, d, (long long)j * s);
     if (periodic) {
         int w = j % n;
         if (w < 0) w += n;
-        return load_pair(h, lo, d, (long long)w * s);
+        return load_pair<T, COH>(h, lo, d, (long long)w * s);
     }
     const bool low = j < 0;
     const int k = low ? -j : j - (n - 1);
-    const Pair<T> e = load_pair(h, lo, d, (long long)(low ? 0 : n - 1) * s);
-    const Pair<T> i1 = load_pair(h, lo, d, (long long)(low ? 1 : n - 2) * s);
+    const Pair<T> e = load_pair<T, COH>(h, lo, d, (long long)(low ? 0 : n - 1) * s);
+    const Pair<T> i1 = load_pair<T, COH>(h, lo, d, (long long)(low ? 1 : n - 2) * s);
     return extrapolate(e, i1, k);
 }
 
@@ -261,15 +271,15 @@ __device__ __forceinline__ Q4<T> ld4(const T* p) {  // shared or global, 16-byte
     }
     return q;
 }
-template <typename T>
-__device__ __forceinline__ Q4<T> ldg4(const T* p) {  // read-only global, 16-byte aligned
+template <typename T, bool COH = false>
+__device__ __forceinline__ Q4<T> ldg4(const T* p) {  // global, 16-byte aligned (see ld_field)
     Q4<T> q;
     if constexpr (sizeof(T) == 4) {
-        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        const float4 a = ld_field<COH>(reinterpret_cast<const float4*>(p));
         q.v[0] = a.x; q.v[1] = a.y; q.v[2] = a.z; q.v[3] = a.w;
     } else {
-        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-        const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+        const double2 a = ld_field<COH>(reinterpret_cast<const double2*>(p));
+        const double2 b = ld_field<COH>(reinterpret_cast<const double2*>(p) + 1);
         q.v[0] = a.x; q.v[1] = a.y; q.v[2] = b.x; q.v[3] = b.y;
     }
     return q;
@@ -281,6 +291,29 @@ __device__ __forceinline__ void st4(T* p, const T* v) {  // 16-byte aligned
     } else {
         reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
         reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+    }
+}
+
+// The interval test's per-node work on a step that ends an interval: the
+// largest |V^{n+1} - snapshot| over a run's valid nodes goes into imax and
+// V^{n+1} (the high word for FP32) replaces the snapshot.  Each node's
+// snapshot is read and written by the thread that owns the node.
+template <typename T, bool COH>
+__device__ __forceinline__ void interval_check(T* snap, const T* v, int nvalid, T& imax) {
+    if (nvalid == 4) {
+        const Q4<T> s = ldg4<T, COH>(snap);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const T ch = fabs(v[i] - s.v[i]);
+            imax = (ch > imax || ch != ch) ? ch : imax;
+        }
+        st4(snap, v);
+    } else {
+        for (int i = 0; i < nvalid; ++i) {
+            const T ch = fabs(v[i] - ld_field<COH>(snap + i));
+            imax = (ch > imax || ch != ch) ? ch : imax;
+            snap[i] = v[i];
+        }
     }
 }
 
@@ -316,6 +349,11 @@ struct TileCtx {
     double* history;
     long long history_len, steps0, max_steps;
     double tau0, dt_d, stop_delta, horizon;
+    // Interval test (Sec. V): on a step that ends an interval the last stage
+    // compares V^{n+1} with the snapshot and replaces it.
+    T* snap;
+    int boundary;
+    double interval_tol;
     // TMA descriptors of the fields this stage copies.
     const CUtensorMap* tm_win;   // stencil input (high word)
     const CUtensorMap* tm_lo;    // FP32 low word of V^n
@@ -407,12 +445,18 @@ __device__ __noinline__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict_
         C.active = D.active;
         C.history = D.history;
         C.history_len = D.history_len;
-        C.steps0 = st->steps;
+        // steps and tau change at the end of every step (finish_step), which
+        // the multi-step march kernel runs inside the same launch.
+        C.steps0 = *reinterpret_cast<volatile long long*>(&st->steps);
         C.max_steps = D.max_steps;
-        C.tau0 = st->tau;
+        C.tau0 = *reinterpret_cast<volatile double*>(&st->tau);
         C.dt_d = st->dt;
         C.stop_delta = st->stop_delta;
         C.horizon = D.horizon;
+        const long long K = st->interval_K;
+        C.snap = static_cast<T*>(D.snap);
+        C.boundary = (K > 0 && D.snap != nullptr && (C.steps0 + 1) % K == 0) ? 1 : 0;
+        C.interval_tol = D.interval_tol;
     }
 }
 
@@ -449,11 +493,17 @@ __device__ inline void finish_step(const TileCtx<T>& C) {
     if (C.history != nullptr && steps - 1 < C.history_len) C.history[steps - 1] = d;
     st->delta_bits = 0ull;
     st->tiles_done = 0u;
+    double di = DBL_MAX;  // the interval's largest change, on a step that ends one
+    if (C.boundary) {
+        di = __longlong_as_double((long long)atomicAdd(&st->interval_bits, 0ull));
+        st->interval_bits = 0ull;
+        st->last_interval_change = di;
+    }
     bool stop = false;
     if (!(d <= DBL_MAX)) {  // NaN or Inf
         st->status = 1;
         stop = true;
-    } else if (d < C.stop_delta) {
+    } else if (d < C.stop_delta || di < C.interval_tol) {
         st->converged = 1;
         stop = true;
     } else if (C.horizon > 0.0 && tau >= C.horizon) {
@@ -656,9 +706,19 @@ struct TileWalk {
 template <typename T, int NDIM, int SCHEME, bool LAST>
 constexpr int kMinBlocks = sizeof(T) != 4 ? 2 : NDIM > 2 ? 2 : 4;
 
-template <typename T, int NDIM, int SCHEME, bool LAST, int V>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
-    stage_kernel(const StageArgs a) {
+// One Runge-Kutta stage of every live instance, as run by one CTA over its
+// share of the tile list (the body of a stage launch).  The caller owns the
+// shared state: the dynamic shared memory `sb` (128-byte aligned, at least
+// StageSmem<...>::BYTES - 128), the tile context C, the reduction slots
+// `red`, the two mbarriers at shared address bar0 (initialised, count 1)
+// and their phase bits, and the tile placements geo_s.  COH selects
+// coherent loads for fields that another CTA may have written earlier in
+// the same launch.  Returns false when a bounded wait gave up (the failure
+// is recorded in the instance's state; the CTA must leave).
+template <typename T, int NDIM, int SCHEME, bool LAST, int V, bool COH>
+__device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned char* sb, TileCtx<T>& C,
+                                           T* red, unsigned bar0, TileGeo* geo_s,
+                                           unsigned& phase) {
     using L = StageSmem<T, NDIM, SCHEME, LAST, V>;
     constexpr int G = L::G, TY = L::TY, TX = L::TX, GROUPS = L::GROUPS;
     constexpr int GY = L::GY, SWX = L::SWX, SH = L::SH, WIN = L::WIN;
@@ -666,13 +726,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
     constexpr int AY = NDIM >= 2 ? NDIM - 2 : 0;  // second fastest axis (used if NDIM >= 2)
     constexpr bool INCR = L::INCR;                // FP32: increments + compensated V
 
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* sb = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<unsigned long long>(smem_raw) + 127ull) & ~127ull);
-    __shared__ TileCtx<T> C;
-    __shared__ T red[kThreads / 32];
-    __shared__ __align__(8) unsigned long long bars[2];
-    __shared__ TileGeo geo_s[2];  // where the tile in each buffer sits (written by thread 0)
     T* dys = reinterpret_cast<T*>(sb + L::DYS);  // dys[r][c] = W(r+1, c) - W(r, c), tile columns
 
     const int ntiles = *a.ntiles;
@@ -692,15 +745,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
     const int grp = threadIdx.x % GROUPS;
     const int ry = threadIdx.x / GROUPS;
     const bool thread_works = NDIM >= 2 ? ry < TY : threadIdx.x < GROUPS;
-
-    const unsigned bar0 = smem_addr(&bars[0]);
-    if (threadIdx.x == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar0 + 8, 1);
-        mbar_init_fence();
-    }
-    __syncthreads();
-    unsigned phase = 0u;  // bit b: parity of the next completion of buffer b
 
     // Bytes one tile's copies deliver to its buffer's barrier.
     const unsigned tile_bytes =
@@ -740,6 +784,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
     // current instance, published (with the tile count) when the CTA moves
     // on to another instance or runs out of tiles.
     T dmax = T(0);
+    T imax = T(0);  // the same for the interval test's change, on a step that ends an interval
     int run_tiles = 0;
     while (t >= 0) {
         const unsigned long long entry = a.tiles[t];
@@ -783,7 +828,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
                 atomicExch(&D.state->status, 4);
                 stop_instance(D);
             }
-            return;
+            return false;
         }
         const TileGeo& tg = geo_s[buf];  // read from shared memory where used
         // Prefetch the next tile of the walk while this one is computed.
@@ -838,7 +883,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
                     if ((NDIM >= 2 && gy >= ny) || c < 4 - G || c >= 4 + TX + G) continue;
                     if (C.periodic[AX]) {
                         const long long r0 = (long long)gy * sy;
-                        v = line_pair<T>(hp + r0, lp ? lp + r0 : nullptr, dp ? dp + r0 : nullptr,
+                        v = line_pair<T, COH>(hp + r0, lp ? lp + r0 : nullptr, dp ? dp + r0 : nullptr,
                                          gx, nx, 1, 1);
                     } else {
                         const bool low = gx < 0;
@@ -855,7 +900,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
                     r = gy - y0 + GY;
                     if (gx >= nx || r < 0 || r >= SH) continue;
                     if (C.periodic[AY]) {
-                        v = line_pair<T>(hp + gx, lp ? lp + gx : nullptr, dp ? dp + gx : nullptr,
+                        v = line_pair<T, COH>(hp + gx, lp ? lp + gx : nullptr, dp ? dp + gx : nullptr,
                                          gy, ny, sy, 1);
                     } else {
                         const bool low = gy < 0;
@@ -959,11 +1004,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
                 const long long l0 = gidx - (long long)si * st;  // node 0 of these lines
                 auto plane = [&](int j, Pair<T>* out) {
                     const long long o = l0 + (long long)j * st;
-                    const Q4<T> h = ldg4(C.win + o);
+                    const Q4<T> h = ldg4<T, COH>(C.win + o);
                     Q4<T> lo, dd;
                     if constexpr (INCR) {
-                        lo = ldg4(C.vlo + o);
-                        if (C.din) dd = ldg4(C.din + o);
+                        lo = ldg4<T, COH>(C.vlo + o);
+                        if (C.din) dd = ldg4<T, COH>(C.din + o);
                     }
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
@@ -1261,6 +1306,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
                             C.vlo_out[gidx + i] = nl[i];
                         }
                     }
+                    if (C.boundary) interval_check<T, COH>(C.snap + gidx, nh, nvalid, imax);
                 }
             } else {
                 T vn[4], out[4];
@@ -1271,7 +1317,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
                     if constexpr (LAST)
                         q = ld4(reinterpret_cast<const T*>(sb + L::VN(buf)) + ry * TX + 4 * grp);
                     else
-                        q = ldg4(C.vcur + gidx);
+                        q = ldg4<T, COH>(C.vcur + gidx);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) vn[i] = q.v[i];
                 }
@@ -1295,6 +1341,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
                 if (nvalid == 4) st4(C.wout + gidx, out);
                 else
                     for (int i = 0; i < nvalid; ++i) C.wout[gidx + i] = out[i];
+                if constexpr (LAST) {
+                    if (C.boundary) interval_check<T, COH>(C.snap + gidx, out, nvalid, imax);
+                }
             }
         }
 
@@ -1309,7 +1358,18 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
                     const T other = __shfl_xor_sync(0xffffffffu, dmax, o);
                     dmax = (other > dmax || other != other) ? other : dmax;
                 }
-                if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dmax;
+                const bool bnd = C.boundary != 0;  // uniform
+                if (bnd) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const T other = __shfl_xor_sync(0xffffffffu, imax, o);
+                        imax = (other > imax || other != other) ? other : imax;
+                    }
+                }
+                if ((threadIdx.x & 31) == 0) {
+                    red[threadIdx.x >> 5] = dmax;
+                    red[kThreads / 32 + (threadIdx.x >> 5)] = imax;
+                }
                 __syncthreads();
                 if (threadIdx.x == 0) {
                     T mt = red[0];
@@ -1317,12 +1377,22 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
                         mt = (red[w] > mt || red[w] != red[w]) ? red[w] : mt;
                     const double m = static_cast<double>(mt);
                     InstState* st = C.state;
+                    if (bnd) {
+                        T mi = red[kThreads / 32];
+                        for (int w = 1; w < kThreads / 32; ++w) {
+                            const T r = red[kThreads / 32 + w];
+                            mi = (r > mi || r != r) ? r : mi;
+                        }
+                        atomicMax(&st->interval_bits,
+                                  static_cast<unsigned long long>(__double_as_longlong(static_cast<double>(mi))));
+                    }
                     atomicMax(&st->delta_bits, static_cast<unsigned long long>(__double_as_longlong(m)));
                     const unsigned int prev = add_tiles_acq_rel(&st->tiles_done, static_cast<unsigned int>(run_tiles));
                     if (prev + static_cast<unsigned int>(run_tiles) == static_cast<unsigned int>(C.ntiles))
                         finish_step(C);
                 }
                 dmax = T(0);
+                imax = T(0);
                 run_tiles = 0;
             }
         }
@@ -1330,6 +1400,157 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
         t = tn;
         issued = pref;
     }
+    return true;
+}
+
+__device__ __forceinline__ unsigned char* align_smem(unsigned char* p) {
+    return reinterpret_cast<unsigned char*>((reinterpret_cast<unsigned long long>(p) + 127ull) &
+                                            ~127ull);
+}
+
+// One launch per Runge-Kutta stage (see stage_pass).
+template <typename T, int NDIM, int SCHEME, bool LAST, int V>
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
+    stage_kernel(const StageArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ TileCtx<T> C;
+    __shared__ T red[2 * (kThreads / 32)];
+    __shared__ __align__(8) unsigned long long bars[2];
+    __shared__ TileGeo geo_s[2];  // where the tile in each buffer sits (written by thread 0)
+    const unsigned bar0 = smem_addr(&bars[0]);
+    if (threadIdx.x == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    unsigned phase = 0u;  // bit b: parity of the next completion of buffer b
+    stage_pass<T, NDIM, SCHEME, LAST, V, false>(a, align_smem(smem_raw), C, red, bar0, geo_s,
+                                                phase);
+}
+
+// ---- the multi-step march: every stage of `steps` steps in one launch ----
+
+// Grid-wide barrier of a cooperative launch: every CTA adds one to
+// *counter (release, GPU scope) and waits until it reaches `target`
+// (acquire), so all global writes made before the barrier by any CTA are
+// visible after it, to plain loads and (through the proxy fences) to the
+// tensor copies.  The wait is bounded: after kWaitNs, or when another CTA
+// has already given up (*fault != 0), the CTA records the failure in
+// *fault and the caller leaves.
+__device__ __forceinline__ bool grid_sync(unsigned* counter, unsigned target, int* fault) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        unsigned prev;
+        asm volatile("atom.release.gpu.global.add.u32 %0, [%1], 1;"
+                     : "=r"(prev)
+                     : "l"(counter)
+                     : "memory");
+        unsigned long long t0 = 0ull;
+        for (unsigned it = 0; it < (1u << 30); ++it) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
+            if (v >= target) break;
+            if (it == 0u) {
+                t0 = global_ns();
+            } else if ((it & 255u) == 0u) {
+                if (global_ns() - t0 > kWaitNs || *reinterpret_cast<volatile int*>(fault) != 0) {
+                    ok = 0;
+                    break;
+                }
+            }
+            if (it > 64u) __nanosleep(32);
+            if (it + 1u == (1u << 30)) ok = 0;
+        }
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        if (!ok) atomicExch(fault, 1);
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+template <typename T, int NDIM, int SCHEME, int V>
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, true>)
+    march_kernel(const MarchArgs m) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ TileCtx<T> C;
+    __shared__ T red[2 * (kThreads / 32)];
+    __shared__ __align__(8) unsigned long long bars[2];
+    __shared__ TileGeo geo_s[2];
+    __shared__ int go;
+    unsigned char* sb = align_smem(smem_raw);
+    const unsigned bar0 = smem_addr(&bars[0]);
+    if (threadIdx.x == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    unsigned phase = 0u;
+    unsigned barriers = 0u;
+    for (int step = 0; step < m.steps; ++step) {
+        for (int i = 0; i < m.ns; ++i) {
+            const bool ok =
+                i + 1 < m.ns
+                    ? stage_pass<T, NDIM, SCHEME, false, V, true>(m.st[i], sb, C, red, bar0, geo_s, phase)
+                    : stage_pass<T, NDIM, SCHEME, true, V, true>(m.st[i], sb, C, red, bar0, geo_s, phase);
+            if (!ok) {
+                if (threadIdx.x == 0) atomicExch(m.fault, 1);
+                return;
+            }
+            ++barriers;
+            if (!grid_sync(m.barrier, barriers * gridDim.x, m.fault)) return;
+        }
+        // Every instance's step bookkeeping is done and visible: stop when
+        // none is still marching (a uniform decision of all CTAs).
+        if (threadIdx.x == 0) go = *reinterpret_cast<const volatile int*>(m.active) > 0;
+        __syncthreads();
+        if (!go) return;
+    }
+}
+
+template <typename T, int NDIM, int SCHEME, int V>
+cudaError_t launch_march(const MarchArgs& m, int grid, cudaStream_t s) {
+    using L0 = StageSmem<T, NDIM, SCHEME, false, V>;
+    using L1 = StageSmem<T, NDIM, SCHEME, true, V>;
+    constexpr int BYTES = L0::BYTES > L1::BYTES ? L0::BYTES : L1::BYTES;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(march_kernel<T, NDIM, SCHEME, V>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, BYTES);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, march_kernel<T, NDIM, SCHEME, V>, m);
+}
+
+template <typename T, int NDIM, int SCHEME, int V>
+int max_blocks_march() {
+    using L0 = StageSmem<T, NDIM, SCHEME, false, V>;
+    using L1 = StageSmem<T, NDIM, SCHEME, true, V>;
+    constexpr int BYTES = L0::BYTES > L1::BYTES ? L0::BYTES : L1::BYTES;
+    if (cudaFuncSetAttribute(march_kernel<T, NDIM, SCHEME, V>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, BYTES) != cudaSuccess)
+        return 0;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, march_kernel<T, NDIM, SCHEME, V>, kThreads,
+                                                      BYTES) != cudaSuccess)
+        return 0;
+    return b;
 }
 
 template <typename T, int NDIM, int SCHEME, bool LAST, int V>

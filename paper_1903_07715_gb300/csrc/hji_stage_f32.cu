@@ -30,4 +30,21 @@ int stage_max_blocks_f32(int ndim, int scheme, bool last, int variant) {
     return 1;
 }
 
+#define HJI_MARCH(ND, SC, V) \
+    if (ndim == ND && scheme == SC && v == V) return launch_march<float, ND, SC, V>;
+#define HJI_MOCC(ND, SC, V) \
+    if (ndim == ND && scheme == SC && v == V) return max_blocks_march<float, ND, SC, V>();
+
+MarchLauncher march_launcher_f32(int ndim, int scheme, int variant) {
+    const int v = ndim == 2 ? variant : 0;
+    HJI_ALL(HJI_MARCH)
+    return nullptr;
+}
+
+int march_max_blocks_f32(int ndim, int scheme, int variant) {
+    const int v = ndim == 2 ? variant : 0;
+    HJI_ALL(HJI_MOCC)
+    return 0;
+}
+
 }  // namespace hji

@@ -46,7 +46,7 @@ def _check(orc, hji, gd, dyn, V, scheme, prec, rel):
     _, mask_u = _decisive(orc, P, scheme, Vg, G, rel)
     assert u.shape == uo.shape
     for j in range(G.shape[1]):
-        assert np.isin(u[j], [dyn["ulo"][j], dyn["uhi"][j]]).all()
+        assert np.isin(u[j], np.array([dyn["ulo"][j], dyn["uhi"][j]]).astype(u.dtype)).all()
         m = mask_u[j]
         assert m.sum() >= min(100, m.size // 10)
         assert np.array_equal(u[j][m], uo[j][m].astype(u.dtype)), j
@@ -54,7 +54,7 @@ def _check(orc, hji, gd, dyn, V, scheme, prec, rel):
         E = np.asarray(dyn["E"], float).reshape(len(gd["n"]), -1)
         _, mask_d = _decisive(orc, P, scheme, Vg, E, rel)
         for k in range(E.shape[1]):
-            assert np.isin(d[k], [dyn["dlo"][k], dyn["dhi"][k]]).all()
+            assert np.isin(d[k], np.array([dyn["dlo"][k], dyn["dhi"][k]]).astype(d.dtype)).all()
             assert np.array_equal(d[k][mask_d[k]], do[k][mask_d[k]].astype(d.dtype))
 
 

@@ -338,3 +338,42 @@ def test_rate_rule_stops_at_first_slow_step(orc):
     assert hist[want - 1] < 0.1 * dt and np.all(hist[: want - 1] >= 0.1 * dt)
     V, st = orc.solve(P, l, tol=0.0, tol_rate=0.1, max_steps=600)
     assert st["converged"] and st["steps"] == want
+
+
+def test_interval_rule_bookkeeping(orc):
+    """Sec. V's test: converged once the largest change of V over one
+    interval (K = round(interval/dt) steps) is below interval_tol.  The march
+    re-run step by step here must stop at the same step with the same V."""
+    gd, dyn, l = W.di_config(41, dmax=0.1)
+    P = orc.problem(gd, dyn)
+    alpha, dt = orc.alpha_dt(P, 0.5)
+    V, st = orc.solve(P, l, scheme="eno2", rk=2, cfl=0.5, tol=0.0, interval=0.05,
+                      interval_tol=2e-3, max_steps=20000)
+    assert st["converged"]
+    K = max(1, int(round(0.05 / dt)))
+    U = orc.init(P, l)
+    snap = U.copy()
+    n = 0
+    while True:
+        U, _ = orc.step(P, "eno2", 2, dt, alpha, l, U)
+        n += 1
+        if n % K == 0:
+            ch = np.abs(U - snap).max()
+            snap = U.copy()
+            if ch < 2e-3:
+                break
+    assert n == st["steps"] and n % K == 0 and n > K
+    assert np.array_equal(U, V)
+
+
+def test_interval_rule_stops_the_running_example_limit_cycle(orc):
+    """ENO2 on the running example (l = |p| - 2) settles into a small limit
+    cycle that no per-step tolerance near 1e-6 ever meets; the paper's
+    interval test (change below 0.001 over 0.01 of time) stops it."""
+    gd = W.grid([61, 61], [-4.0, -3.0], [4.0, 3.0])
+    dyn = W.double_integrator(umax=1.0)
+    l = W.target_outside(gd, 0, 2.0)
+    P = orc.problem(gd, dyn)
+    V, st = orc.solve(P, l, scheme="eno2", rk=2, cfl=0.5, tol=0.0, interval=0.01,
+                      interval_tol=1e-3, max_steps=20000)
+    assert st["converged"] and st["steps"] < 20000

@@ -5,9 +5,12 @@ static device array, so two calls in a row must each give what the
 allocating entry point hji_solve gives for the same problem, and a grid too
 large for the array must be refused before any device work.
 
-Both arms march with the same tile shape: the allocating solve is given
-tile_variant=1 (shape 0, the one hji_solve_noalloc takes by default), so the
-comparison does not rest on any autotuned choice made earlier in the session.
+Both arms march with the same tile shape and the same launch form: the
+allocating solve is given tile_variant=1 (shape 0, the one hji_solve_noalloc
+takes by default) and march="per_stage" (hji_solve_noalloc launches one
+kernel per RK stage), so the comparison rests neither on an autotuned choice
+made earlier in the session nor on how the compiler fused the multi-step
+kernel's multiply-adds.
 """
 import ctypes
 
@@ -58,7 +61,7 @@ def _noalloc(hji, torch, gd, dyn, l, k, prec, resident=None, **opts):
 def _allocating(hji, gd, dyn, l, k, prec, **opts):
     g = hji.Grid(gd, prec)
     g.set_dynamics(dyn)
-    st = g.solve(l, k, tile_variant=1, **opts)
+    st = g.solve(l, k, tile_variant=1, march="per_stage", **opts)
     V = g.value()
     g.close()
     return V, st
