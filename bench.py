@@ -454,7 +454,7 @@ def run_hbm_workload(args, hji, torch, dist, rank, world, local_rank):
             "di8192": "di_8192^2"}[args.workload]
     clocks = ClockSampler(local_rank)
     res = hbm_workloads(hji, torch, steps=50, only=name, repeats=args.steps, warmup=args.warmup,
-                        clocks=clocks)[name]
+                        clocks=clocks, march=args.march)[name]
     ms, upd = res["ms_total"], res["updates_total"]
     if dist is not None:
         ms, upd = reduce_over_ranks(dist, torch, ms, upd, "cuda")
@@ -885,7 +885,8 @@ def _measured_hbm():
         return 6800.0, "fallback"
 
 
-def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=None):
+def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=None,
+                  march="auto"):
     """HBM-bound marches (working sets well above the 129 MB L2), FP32
     compensated storage, ENO2/RK2: 50 steps each from V0 = l, CUDA-event
     timed after a warm-up.  Algorithmic bytes per node per RK2 step: stage 1
@@ -907,7 +908,8 @@ def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=N
         # disturbance, l = 1 - |x1|): 67 M nodes, 268 MB per FP32 field.
         gd, dyn, l = W.di_config(8192)
         cases.append(("di_8192^2", [gd], [dyn], [l]))
-    opts = dict(scheme="eno2", rk=2, cfl=0.5, tol=0.0, max_steps=steps, check_every=steps)
+    opts = dict(scheme="eno2", rk=2, cfl=0.5, tol=0.0, max_steps=steps, check_every=steps,
+                march=march)
     stream = torch.cuda.current_stream()
     for name, gds, dyns, ls in cases:
         grids = []

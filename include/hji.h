@@ -168,10 +168,10 @@ typedef struct {
  * stage, check_every steps captured in one CUDA graph.  MULTI_STEP: one
  * cooperative launch runs every stage of check_every steps, with a
  * bounded grid-wide barrier after each stage (no launch gaps, no per-launch
- * ramp and tail); it needs every CTA resident at once and falls back to
- * PER_STAGE where that cannot be launched.  AUTO: MULTI_STEP for 1-D and
- * 2-D grids, PER_STAGE otherwise (the 3-D/4-D multi-step kernels would spill
- * registers).  Both forms run the same per-node arithmetic from the same
+ * ramp and tail); it exists for 1-D and 2-D grids (3-D/4-D ones would
+ * spill registers) and needs every CTA resident at once: elsewhere it falls
+ * back to PER_STAGE.  AUTO: MULTI_STEP for 1-D and 2-D grids, PER_STAGE
+ * otherwise.  Both forms run the same per-node arithmetic from the same
  * source; compiled as different kernels, the compiler may fuse a different
  * set of multiply-adds, so their results agree to rounding, not bit for bit.
  * Within one form, results do not depend on check_every, on the batch an

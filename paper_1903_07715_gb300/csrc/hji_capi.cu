@@ -278,16 +278,18 @@ int rk_plan(int rk, StagePlan* p) {
     return 3;
 }
 
-hji::StageLauncher launcher(bool f32, int ndim, int scheme, bool last, int variant) {
-    return f32 ? hji::stage_launcher_f32(ndim, scheme, last, variant)
-               : hji::stage_launcher_f64(ndim, scheme, last, variant);
+hji::StageLauncher launcher(bool f32, int ndim, int scheme, bool last, int variant,
+                            bool interval) {
+    return f32 ? hji::stage_launcher_f32(ndim, scheme, last, variant, interval)
+               : hji::stage_launcher_f64(ndim, scheme, last, variant, interval);
 }
 
 // CTAs of one stage launch: as many as fit on every SM at once (each stage
 // kernel has its own occupancy), at most one per tile.
-int stage_grid(bool f32, int ndim, int scheme, long long total_tiles, int variant, bool last) {
-    const int b = f32 ? hji::stage_max_blocks_f32(ndim, scheme, last, variant)
-                      : hji::stage_max_blocks_f64(ndim, scheme, last, variant);
+int stage_grid(bool f32, int ndim, int scheme, long long total_tiles, int variant, bool last,
+               bool interval) {
+    const int b = f32 ? hji::stage_max_blocks_f32(ndim, scheme, last, variant, interval)
+                      : hji::stage_max_blocks_f64(ndim, scheme, last, variant, interval);
     long long g = (long long)num_sms() * b;
     if (g > total_tiles) g = total_tiles;
     return g < 1 ? 1 : (int)g;
@@ -461,12 +463,12 @@ hji_status make_desc(hji_grid g, const hji_solve_opts* o, int* active, int varia
 // Capture `steps` steps of the march (all RK stages) into a graph.
 hji_status capture_chunk(hji_grid g, cudaStream_t cap, bool f32, int ndim, int scheme, int rk,
                          int steps, const hji::StageArgs& base, const int* grid, int variant,
-                         cudaGraphExec_t* out) {
+                         bool interval, cudaGraphExec_t* out) {
     StagePlan plan[3];
     const int ns = rk_plan(rk, plan);
     hji::StageLauncher L[3];
     for (int i = 0; i < ns; ++i) {
-        L[i] = launcher(f32, ndim, scheme, plan[i].last, variant);
+        L[i] = launcher(f32, ndim, scheme, plan[i].last, variant, interval);
         if (!L[i]) return fail(g, HJI_E_INVALID, "no kernel for this ndim/scheme");
     }
     HJI_CUDA(g, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
@@ -501,9 +503,10 @@ hji_status capture_chunk(hji_grid g, cudaStream_t cap, bool f32, int ndim, int s
 // grid-wide barriers) into a graph: the barrier counter is zeroed first.
 hji_status capture_march(hji_grid g, cudaStream_t cap, bool f32, int ndim, int scheme, int rk,
                          int steps, const hji::StageArgs& base, int grid, int variant,
-                         const int* active, unsigned* barrier, int* fault, cudaGraphExec_t* out) {
-    hji::MarchLauncher L = f32 ? hji::march_launcher_f32(ndim, scheme, variant)
-                               : hji::march_launcher_f64(ndim, scheme, variant);
+                         bool interval, const int* active, unsigned* barrier, int* fault,
+                         cudaGraphExec_t* out) {
+    hji::MarchLauncher L = f32 ? hji::march_launcher_f32(ndim, scheme, variant, interval)
+                               : hji::march_launcher_f64(ndim, scheme, variant, interval);
     if (!L) return fail(g, HJI_E_INVALID, "no march kernel for this ndim/scheme");
     StagePlan plan[3];
     const int ns = rk_plan(rk, plan);
@@ -551,7 +554,7 @@ cudaError_t timed_march(const hji_solve_opts* o, bool f32, int ndim, const hji::
     const int ns = rk_plan(o->rk_order, plan);
     hji::StageLauncher Lk[3];
     for (int i = 0; i < ns; ++i) {
-        Lk[i] = launcher(f32, ndim, o->scheme, plan[i].last, variant);
+        Lk[i] = launcher(f32, ndim, o->scheme, plan[i].last, variant, o->interval > 0.0);
         if (!Lk[i]) return cudaErrorInvalidValue;
     }
     const int steps = o->max_steps;
@@ -738,19 +741,21 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
     // Each graph is either one launch per RK stage, or one multi-step march
     // launch (every CTA resident: at most march_max_blocks per SM).
     const int chunk = o->check_every > 0 ? o->check_every : 32;
+    const bool interval = o->interval > 0.0;
     bool multi = !g_stage_timer && (o->march == HJI_MARCH_MULTI_STEP ||
                                     (o->march == HJI_MARCH_AUTO && ndim <= 2));
     int mgrid = 0;
     if (multi) {
-        const int b = f32 ? hji::march_max_blocks_f32(ndim, o->scheme, variant)
-                          : hji::march_max_blocks_f64(ndim, o->scheme, variant);
+        const int b = f32 ? hji::march_max_blocks_f32(ndim, o->scheme, variant, interval)
+                          : hji::march_max_blocks_f64(ndim, o->scheme, variant, interval);
         long long gm = (long long)num_sms() * b;
         if (gm > total_tiles) gm = total_tiles;
         mgrid = (int)gm;
         multi = mgrid >= 1;
     }
-    const int grid[2] = {multi ? mgrid : stage_grid(f32, ndim, o->scheme, total_tiles, variant, false),
-                         multi ? 0 : stage_grid(f32, ndim, o->scheme, total_tiles, variant, true)};
+    const int grid[2] = {
+        multi ? mgrid : stage_grid(f32, ndim, o->scheme, total_tiles, variant, false, interval),
+        multi ? 0 : stage_grid(f32, ndim, o->scheme, total_tiles, variant, true, interval)};
     hji::StageArgs base{d_desc, d_tiles, d_ntiles, 0, 0, 0.0, 0.0, 0.0f, 0.0f, 0};
     unsigned* d_barrier = reinterpret_cast<unsigned*>(d_active + 2);
     int* d_fault = d_active + 3;
@@ -760,7 +765,7 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
     // shape (scheme, RK order, chunk, grid, tile shape, launch mode) are
     // unchanged.
     const long long key[8] = {(long long)o->scheme, o->rk_order, chunk, grid[0], grid[1],
-                              variant + (multi ? 16 : 0), ndim, f32 ? 1 : 0};
+                              variant + (multi ? 16 : 0) + (interval ? 32 : 0), ndim, f32 ? 1 : 0};
     if (g_stage_timer) {
         // the timed march launches its stages one by one
     } else if (g0->graph && std::memcmp(key, g0->graph_key, sizeof(key)) == 0) {
@@ -768,9 +773,9 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
     } else {
         drop_graph();
         st = multi ? capture_march(g0, g0->cap_stream, f32, ndim, o->scheme, o->rk_order, chunk, base,
-                                   mgrid, variant, d_active, d_barrier, d_fault, &exec)
+                                   mgrid, variant, interval, d_active, d_barrier, d_fault, &exec)
                    : capture_chunk(g0, g0->cap_stream, f32, ndim, o->scheme, o->rk_order, chunk, base,
-                                   grid, variant, &exec);
+                                   grid, variant, interval, &exec);
         if (st != HJI_OK) return st;
         g0->graph = exec;
         std::memcpy(g0->graph_key, key, sizeof(key));
@@ -1107,7 +1112,8 @@ hji_status hji_engine_create(int ndim, hji_precision prec, const hji_solve_opts*
     }
     e->variant = pick_variant(prec, ndim, o, 1ll << 20);
     for (int last = 0; last < 2; ++last)
-        e->grid[last] = stage_grid(prec == HJI_F32, ndim, o->scheme, 1ll << 40, e->variant, last != 0);
+        e->grid[last] = stage_grid(prec == HJI_F32, ndim, o->scheme, 1ll << 40, e->variant, last != 0,
+                                   o->interval > 0.0);
     *out = e;
     return HJI_OK;
 }
@@ -1282,7 +1288,8 @@ hji_status hji_engine_step(hji_engine e, int* active, int* queued) {
         if (!e->graph) {
             hji::StageArgs base{e->d_desc, e->d_tiles, e->d_counts + 1, 0, 0, 0.0, 0.0, 0.0f, 0.0f, 0};
             hji_status st = capture_chunk(nullptr, e->cap, f32, e->ndim, e->o.scheme, e->o.rk_order,
-                                          e->chunk, base, e->grid, e->variant, &e->graph);
+                                          e->chunk, base, e->grid, e->variant,
+                                          e->o.interval > 0.0, &e->graph);
             if (st != HJI_OK) return efail(e, st, g_create_error);
         }
         ce = cudaGraphLaunch(e->graph, e->s);

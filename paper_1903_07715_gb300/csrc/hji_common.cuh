@@ -201,17 +201,21 @@ struct MarchArgs {
     int* fault;        // set to 1 when a bounded wait gave up
 };
 using MarchLauncher = cudaError_t (*)(const MarchArgs&, int grid, cudaStream_t);
-MarchLauncher march_launcher_f64(int ndim, int scheme, int variant = 0);
-MarchLauncher march_launcher_f32(int ndim, int scheme, int variant = 0);
-int march_max_blocks_f64(int ndim, int scheme, int variant = 0);
-int march_max_blocks_f32(int ndim, int scheme, int variant = 0);
+// Multi-step march kernels exist for 1-D and 2-D grids (null / 0 otherwise).
+MarchLauncher march_launcher_f64(int ndim, int scheme, int variant = 0, bool interval = false);
+MarchLauncher march_launcher_f32(int ndim, int scheme, int variant = 0, bool interval = false);
+int march_max_blocks_f64(int ndim, int scheme, int variant = 0, bool interval = false);
+int march_max_blocks_f32(int ndim, int scheme, int variant = 0, bool interval = false);
 
 // Kernel dispatch tables (one per precision); `variant` selects the tile
-// shape (only 2-D grids have more than variant 0).
-StageLauncher stage_launcher_f64(int ndim, int scheme, bool last, int variant = 0);
-StageLauncher stage_launcher_f32(int ndim, int scheme, bool last, int variant = 0);
-int stage_max_blocks_f64(int ndim, int scheme, bool last, int variant = 0);
-int stage_max_blocks_f32(int ndim, int scheme, bool last, int variant = 0);
+// shape (only 2-D grids have more than variant 0); `interval` picks the last
+// stage with Sec. V's interval test compiled in.
+StageLauncher stage_launcher_f64(int ndim, int scheme, bool last, int variant = 0,
+                                 bool interval = false);
+StageLauncher stage_launcher_f32(int ndim, int scheme, bool last, int variant = 0,
+                                 bool interval = false);
+int stage_max_blocks_f64(int ndim, int scheme, bool last, int variant = 0, bool interval = false);
+int stage_max_blocks_f32(int ndim, int scheme, bool last, int variant = 0, bool interval = false);
 
 // Arguments of the optimal-control pass (hji_control.cu): a grid's current
 // value (padded C-order fields; FP32 grids add the low word) and the input

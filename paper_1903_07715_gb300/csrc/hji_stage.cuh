@@ -375,7 +375,7 @@ __device__ __forceinline__ const CtxConst<T>& ctx_const(const InstState* st) {
 // 1-D/2-D and 4-D ENO2 ones spill none) with the context load as a call.
 static_assert(MAXD == 4 && MAXU == 4 && MAXT == 8 && kThreads > 96,
               "load_ctx hands out slices for these sizes");
-template <typename T>
+template <typename T, bool COH>
 __device__ __noinline__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict__ insts, int inst,
                                       const StageArgs& a) {
     const InstDesc& D = insts[inst];
@@ -445,11 +445,17 @@ __device__ __noinline__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict_
         C.active = D.active;
         C.history = D.history;
         C.history_len = D.history_len;
-        // steps and tau change at the end of every step (finish_step), which
-        // the multi-step march kernel runs inside the same launch.
-        C.steps0 = *reinterpret_cast<volatile long long*>(&st->steps);
+        // steps and tau change at the end of every step (finish_step); the
+        // multi-step march kernel (COH) reads them after a step of the same
+        // launch, so at L2.
+        if constexpr (COH) {
+            C.steps0 = __ldcg(&st->steps);
+            C.tau0 = __ldcg(&st->tau);
+        } else {
+            C.steps0 = st->steps;
+            C.tau0 = st->tau;
+        }
         C.max_steps = D.max_steps;
-        C.tau0 = *reinterpret_cast<volatile double*>(&st->tau);
         C.dt_d = st->dt;
         C.stop_delta = st->stop_delta;
         C.horizon = D.horizon;
@@ -629,7 +635,7 @@ struct StageSmem {
     static constexpr int DYS = 2 * BUFB;
     static constexpr int PMY = DYS + DYSB;
     static constexpr int PPY = PMY + PYB;
-    static constexpr int BYTES = PPY + PYB + 128;  // + alignment slack
+    static constexpr int BYTES = PPY + PYB;
     static __host__ __device__ constexpr int H(int b) { return b * BUFB; }
     static __host__ __device__ constexpr int LO(int b) { return b * BUFB + WINB; }
     static __host__ __device__ constexpr int DD(int b) { return b * BUFB + 2 * WINB; }
@@ -706,20 +712,27 @@ struct TileWalk {
 template <typename T, int NDIM, int SCHEME, bool LAST>
 constexpr int kMinBlocks = sizeof(T) != 4 ? 2 : NDIM > 2 ? 2 : 4;
 
+// The kernels' dynamic shared memory (the tile windows and per-tile
+// arrays; StageSmem gives the layout).  Only 16-byte alignment is needed:
+// the tensor copies use no swizzle and the widest accesses are 16 bytes.
+extern __shared__ __align__(16) unsigned char hji_smem[];
+
 // One Runge-Kutta stage of every live instance, as run by one CTA over its
 // share of the tile list (the body of a stage launch).  The caller owns the
-// shared state: the dynamic shared memory `sb` (128-byte aligned, at least
-// StageSmem<...>::BYTES - 128), the tile context C, the reduction slots
-// `red`, the two mbarriers at shared address bar0 (initialised, count 1)
-// and their phase bits, and the tile placements geo_s.  COH selects
-// coherent loads for fields that another CTA may have written earlier in
-// the same launch.  Returns false when a bounded wait gave up (the failure
-// is recorded in the instance's state; the CTA must leave).
-template <typename T, int NDIM, int SCHEME, bool LAST, int V, bool COH>
-__device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned char* sb, TileCtx<T>& C,
-                                           T* red, unsigned bar0, TileGeo* geo_s,
-                                           unsigned& phase) {
+// two mbarriers at shared address bar0 (initialised, count 1) and their
+// phase bits; the tile context, reduction slots and tile placements are
+// this function's own shared variables.  COH selects coherent loads for
+// fields that another CTA may have written earlier in the same launch.
+// INTERVAL (last stage only) compiles in Sec. V's interval test.  Returns
+// false when a bounded wait gave up (the failure is recorded in the
+// instance's state; the CTA must leave).
+template <typename T, int NDIM, int SCHEME, bool LAST, int V, bool COH, bool INTERVAL>
+__device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, unsigned& phase) {
     using L = StageSmem<T, NDIM, SCHEME, LAST, V>;
+    __shared__ TileCtx<T> C;
+    __shared__ T red[2 * (kThreads / 32)];
+    __shared__ TileGeo geo_s[2];  // where the tile in each buffer sits (written by thread 0)
+    unsigned char* sb = hji_smem;
     constexpr int G = L::G, TY = L::TY, TX = L::TX, GROUPS = L::GROUPS;
     constexpr int GY = L::GY, SWX = L::SWX, SH = L::SH, WIN = L::WIN;
     constexpr int AX = NDIM - 1;                  // fastest axis
@@ -785,6 +798,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned char* sb
     // on to another instance or runs out of tiles.
     T dmax = T(0);
     T imax = T(0);  // the same for the interval test's change, on a step that ends an interval
+    (void)imax;
     int run_tiles = 0;
     while (t >= 0) {
         const unsigned long long entry = a.tiles[t];
@@ -792,7 +806,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned char* sb
         const int local = static_cast<int>(entry & 0xFFFFFFFFFFFFull);
         if (inst != loaded) {
             __syncthreads();  // everyone is done with the previous context
-            load_ctx<T>(C, a.insts, inst, a);
+            load_ctx<T, COH>(C, a.insts, inst, a);
             __syncthreads();
             if (threadIdx.x == 0 && !C.stop) {
                 tensormap_acquire(C.tm_win);
@@ -1306,7 +1320,9 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned char* sb
                             C.vlo_out[gidx + i] = nl[i];
                         }
                     }
-                    if (C.boundary) interval_check<T, COH>(C.snap + gidx, nh, nvalid, imax);
+                    if constexpr (INTERVAL) {
+                        if (C.boundary) interval_check<T, COH>(C.snap + gidx, nh, nvalid, imax);
+                    }
                 }
             } else {
                 T vn[4], out[4];
@@ -1341,7 +1357,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned char* sb
                 if (nvalid == 4) st4(C.wout + gidx, out);
                 else
                     for (int i = 0; i < nvalid; ++i) C.wout[gidx + i] = out[i];
-                if constexpr (LAST) {
+                if constexpr (LAST && INTERVAL) {
                     if (C.boundary) interval_check<T, COH>(C.snap + gidx, out, nvalid, imax);
                 }
             }
@@ -1358,7 +1374,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned char* sb
                     const T other = __shfl_xor_sync(0xffffffffu, dmax, o);
                     dmax = (other > dmax || other != other) ? other : dmax;
                 }
-                const bool bnd = C.boundary != 0;  // uniform
+                const bool bnd = INTERVAL && C.boundary != 0;  // uniform
                 if (bnd) {
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
@@ -1368,7 +1384,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned char* sb
                 }
                 if ((threadIdx.x & 31) == 0) {
                     red[threadIdx.x >> 5] = dmax;
-                    red[kThreads / 32 + (threadIdx.x >> 5)] = imax;
+                    if (bnd) red[kThreads / 32 + (threadIdx.x >> 5)] = imax;
                 }
                 __syncthreads();
                 if (threadIdx.x == 0) {
@@ -1392,7 +1408,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned char* sb
                         finish_step(C);
                 }
                 dmax = T(0);
-                imax = T(0);
+                if constexpr (INTERVAL) imax = T(0);
                 run_tiles = 0;
             }
         }
@@ -1403,20 +1419,11 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned char* sb
     return true;
 }
 
-__device__ __forceinline__ unsigned char* align_smem(unsigned char* p) {
-    return reinterpret_cast<unsigned char*>((reinterpret_cast<unsigned long long>(p) + 127ull) &
-                                            ~127ull);
-}
-
 // One launch per Runge-Kutta stage (see stage_pass).
-template <typename T, int NDIM, int SCHEME, bool LAST, int V>
+template <typename T, int NDIM, int SCHEME, bool LAST, int V, bool INTERVAL>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
     stage_kernel(const StageArgs a) {
-    extern __shared__ unsigned char smem_raw[];
-    __shared__ TileCtx<T> C;
-    __shared__ T red[2 * (kThreads / 32)];
     __shared__ __align__(8) unsigned long long bars[2];
-    __shared__ TileGeo geo_s[2];  // where the tile in each buffer sits (written by thread 0)
     const unsigned bar0 = smem_addr(&bars[0]);
     if (threadIdx.x == 0) {
         mbar_init(bar0, 1);
@@ -1425,8 +1432,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
     }
     __syncthreads();
     unsigned phase = 0u;  // bit b: parity of the next completion of buffer b
-    stage_pass<T, NDIM, SCHEME, LAST, V, false>(a, align_smem(smem_raw), C, red, bar0, geo_s,
-                                                phase);
+    stage_pass<T, NDIM, SCHEME, LAST, V, false, INTERVAL>(a, bar0, phase);
 }
 
 // ---- the multi-step march: every stage of `steps` steps in one launch ----
@@ -1473,16 +1479,11 @@ __device__ __forceinline__ bool grid_sync(unsigned* counter, unsigned target, in
     return ok_s != 0;
 }
 
-template <typename T, int NDIM, int SCHEME, int V>
+template <typename T, int NDIM, int SCHEME, int V, bool INTERVAL>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, true>)
     march_kernel(const MarchArgs m) {
-    extern __shared__ unsigned char smem_raw[];
-    __shared__ TileCtx<T> C;
-    __shared__ T red[2 * (kThreads / 32)];
     __shared__ __align__(8) unsigned long long bars[2];
-    __shared__ TileGeo geo_s[2];
     __shared__ int go;
-    unsigned char* sb = align_smem(smem_raw);
     const unsigned bar0 = smem_addr(&bars[0]);
     if (threadIdx.x == 0) {
         mbar_init(bar0, 1);
@@ -1496,8 +1497,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, true>)
         for (int i = 0; i < m.ns; ++i) {
             const bool ok =
                 i + 1 < m.ns
-                    ? stage_pass<T, NDIM, SCHEME, false, V, true>(m.st[i], sb, C, red, bar0, geo_s, phase)
-                    : stage_pass<T, NDIM, SCHEME, true, V, true>(m.st[i], sb, C, red, bar0, geo_s, phase);
+                    ? stage_pass<T, NDIM, SCHEME, false, V, true, false>(m.st[i], bar0, phase)
+                    : stage_pass<T, NDIM, SCHEME, true, V, true, INTERVAL>(m.st[i], bar0, phase);
             if (!ok) {
                 if (threadIdx.x == 0) atomicExch(m.fault, 1);
                 return;
@@ -1513,14 +1514,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, true>)
     }
 }
 
-template <typename T, int NDIM, int SCHEME, int V>
+template <typename T, int NDIM, int SCHEME, int V, bool INTERVAL>
 cudaError_t launch_march(const MarchArgs& m, int grid, cudaStream_t s) {
     using L0 = StageSmem<T, NDIM, SCHEME, false, V>;
     using L1 = StageSmem<T, NDIM, SCHEME, true, V>;
     constexpr int BYTES = L0::BYTES > L1::BYTES ? L0::BYTES : L1::BYTES;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(march_kernel<T, NDIM, SCHEME, V>,
+        cudaError_t e = cudaFuncSetAttribute(march_kernel<T, NDIM, SCHEME, V, INTERVAL>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, BYTES);
         if (e != cudaSuccess) return e;
         configured = true;
@@ -1535,46 +1536,46 @@ cudaError_t launch_march(const MarchArgs& m, int grid, cudaStream_t s) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, march_kernel<T, NDIM, SCHEME, V>, m);
+    return cudaLaunchKernelEx(&cfg, march_kernel<T, NDIM, SCHEME, V, INTERVAL>, m);
 }
 
-template <typename T, int NDIM, int SCHEME, int V>
+template <typename T, int NDIM, int SCHEME, int V, bool INTERVAL>
 int max_blocks_march() {
     using L0 = StageSmem<T, NDIM, SCHEME, false, V>;
     using L1 = StageSmem<T, NDIM, SCHEME, true, V>;
     constexpr int BYTES = L0::BYTES > L1::BYTES ? L0::BYTES : L1::BYTES;
-    if (cudaFuncSetAttribute(march_kernel<T, NDIM, SCHEME, V>,
+    if (cudaFuncSetAttribute(march_kernel<T, NDIM, SCHEME, V, INTERVAL>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, BYTES) != cudaSuccess)
         return 0;
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, march_kernel<T, NDIM, SCHEME, V>, kThreads,
-                                                      BYTES) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, march_kernel<T, NDIM, SCHEME, V, INTERVAL>,
+                                                      kThreads, BYTES) != cudaSuccess)
         return 0;
     return b;
 }
 
-template <typename T, int NDIM, int SCHEME, bool LAST, int V>
+template <typename T, int NDIM, int SCHEME, bool LAST, int V, bool INTERVAL>
 cudaError_t launch_stage(const StageArgs& a, int grid, cudaStream_t s) {
     using L = StageSmem<T, NDIM, SCHEME, LAST, V>;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, NDIM, SCHEME, LAST, V>,
+        cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, NDIM, SCHEME, LAST, V, INTERVAL>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(L::BYTES));
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    stage_kernel<T, NDIM, SCHEME, LAST, V><<<grid, kThreads, L::BYTES, s>>>(a);
+    stage_kernel<T, NDIM, SCHEME, LAST, V, INTERVAL><<<grid, kThreads, L::BYTES, s>>>(a);
     return cudaGetLastError();
 }
 
-template <typename T, int NDIM, int SCHEME, bool LAST, int V>
+template <typename T, int NDIM, int SCHEME, bool LAST, int V, bool INTERVAL>
 int max_blocks_stage() {
     using L = StageSmem<T, NDIM, SCHEME, LAST, V>;
-    cudaFuncSetAttribute(stage_kernel<T, NDIM, SCHEME, LAST, V>,
+    cudaFuncSetAttribute(stage_kernel<T, NDIM, SCHEME, LAST, V, INTERVAL>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L::BYTES));
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stage_kernel<T, NDIM, SCHEME, LAST, V>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stage_kernel<T, NDIM, SCHEME, LAST, V, INTERVAL>,
                                                       kThreads, L::BYTES) != cudaSuccess)
         return 1;
     return b > 0 ? b : 1;

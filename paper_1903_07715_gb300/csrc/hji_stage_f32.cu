@@ -4,12 +4,18 @@
 
 namespace hji {
 
-#define HJI_ENTRY(ND, SC, V) \
-    if (ndim == ND && scheme == SC && v == V) \
-        return last ? launch_stage<float, ND, SC, true, V> : launch_stage<float, ND, SC, false, V>;
-#define HJI_OCC(ND, SC, V) \
-    if (ndim == ND && scheme == SC && v == V) \
-        return last ? max_blocks_stage<float, ND, SC, true, V>() : max_blocks_stage<float, ND, SC, false, V>();
+#define HJI_ENTRY(ND, SC, V)                                                                   \
+    if (ndim == ND && scheme == SC && v == V) {                                                 \
+        if (!last) return launch_stage<float, ND, SC, false, V, false>;                        \
+        return interval ? launch_stage<float, ND, SC, true, V, true>                           \
+                        : launch_stage<float, ND, SC, true, V, false>;                         \
+    }
+#define HJI_OCC(ND, SC, V)                                                                     \
+    if (ndim == ND && scheme == SC && v == V) {                                                 \
+        if (!last) return max_blocks_stage<float, ND, SC, false, V, false>();                  \
+        return interval ? max_blocks_stage<float, ND, SC, true, V, true>()                     \
+                        : max_blocks_stage<float, ND, SC, true, V, false>();                   \
+    }
 #define HJI_ALL(X) \
     X(1, HJI_ENO1, 0) X(1, HJI_ENO2, 0) X(1, HJI_WENO5, 0) \
     X(2, HJI_ENO1, 0) X(2, HJI_ENO2, 0) X(2, HJI_WENO5, 0) \
@@ -18,33 +24,16 @@ namespace hji {
     X(3, HJI_ENO1, 0) X(3, HJI_ENO2, 0) X(3, HJI_WENO5, 0) \
     X(4, HJI_ENO1, 0) X(4, HJI_ENO2, 0) X(4, HJI_WENO5, 0)
 
-StageLauncher stage_launcher_f32(int ndim, int scheme, bool last, int variant) {
+StageLauncher stage_launcher_f32(int ndim, int scheme, bool last, int variant, bool interval) {
     const int v = ndim == 2 ? variant : 0;
     HJI_ALL(HJI_ENTRY)
     return nullptr;
 }
 
-int stage_max_blocks_f32(int ndim, int scheme, bool last, int variant) {
+int stage_max_blocks_f32(int ndim, int scheme, bool last, int variant, bool interval) {
     const int v = ndim == 2 ? variant : 0;
     HJI_ALL(HJI_OCC)
     return 1;
-}
-
-#define HJI_MARCH(ND, SC, V) \
-    if (ndim == ND && scheme == SC && v == V) return launch_march<float, ND, SC, V>;
-#define HJI_MOCC(ND, SC, V) \
-    if (ndim == ND && scheme == SC && v == V) return max_blocks_march<float, ND, SC, V>();
-
-MarchLauncher march_launcher_f32(int ndim, int scheme, int variant) {
-    const int v = ndim == 2 ? variant : 0;
-    HJI_ALL(HJI_MARCH)
-    return nullptr;
-}
-
-int march_max_blocks_f32(int ndim, int scheme, int variant) {
-    const int v = ndim == 2 ? variant : 0;
-    HJI_ALL(HJI_MOCC)
-    return 0;
 }
 
 }  // namespace hji

@@ -6,9 +6,9 @@ contract a different set of multiply-adds into FMAs: results agree to
 rounding (FP64 1e-10, the per-step parity bar; FP32 1e-5 max|l|) rather than
 bit for bit, with the same step counts.  Covers both precisions, every scheme, RK
 orders, ragged and minimal grids, periodic axes (ghost nodes read from
-global memory), 3-D and 4-D grids (slow-axis stencil lines read from global
-memory, forced to the multi-step launch), a batch of uneven grids, and
-convergence inside a launch (steps after the stop point never run)."""
+global memory), 3-D and 4-D grids (a multi-step launch asked for there falls
+back to one launch per stage), a batch of uneven grids, and convergence
+inside a launch (steps after the stop point never run)."""
 import numpy as np
 import pytest
 
