@@ -162,6 +162,17 @@ typedef struct {
                          steps; V is compared with its copy from K steps
                          earlier after every K-th step.  0: off. */
     double interval_tol; /* >= 0, see interval */
+    int brs;          /* 0: the VI of Eq. (7), V <- min(V, l) after every step
+                         (the tube, the default); 1: the HJI PDE of Eq. (5)
+                         alone, no projection onto V <= l: the value of the
+                         backward reachable set at time tau (normally run to
+                         a horizon); a warm start k (or the resident value)
+                         is then taken as it is, not as min(k, l) */
+    int local_lf;     /* 0: Lax-Friedrichs dissipation with the grid-wide
+                         alpha_a (default); 1: with the node's own
+                         alpha_a(x) = max_{u,d} |f_a(x,u,d)| (dt stays the
+                         grid-wide CFL step).  Local dissipation marches with
+                         one launch per stage and the default tile shape. */
 } hji_solve_opts;
 
 /* hji_solve_opts.march.  PER_STAGE: one kernel launch per Runge-Kutta
@@ -170,8 +181,9 @@ typedef struct {
  * bounded grid-wide barrier after each stage (no launch gaps, no per-launch
  * ramp and tail); it exists for 1-D and 2-D grids (3-D/4-D ones would
  * spill registers) and needs every CTA resident at once: elsewhere it falls
- * back to PER_STAGE.  AUTO: MULTI_STEP for 1-D and 2-D grids, PER_STAGE
- * otherwise.  Both forms run the same per-node arithmetic from the same
+ * back to PER_STAGE.  AUTO: MULTI_STEP for 1-D and 2-D grids whose stages
+ * give every resident CTA at least 4 tiles (the barrier then costs less
+ * than a kernel boundary), PER_STAGE otherwise.  Both forms run the same per-node arithmetic from the same
  * source; compiled as different kernels, the compiler may fuse a different
  * set of multiply-adds, so their results agree to rounding, not bit for bit.
  * Within one form, results do not depend on check_every, on the batch an

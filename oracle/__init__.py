@@ -94,12 +94,13 @@ def _load():
         lib.oracle_one_sided.argtypes = [ctypes.c_int, _D, ctypes.c_double, _D, _D]
         lib.oracle_operator.argtypes = [_P, ctypes.c_int, _D, _D, _D]
         lib.oracle_step.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D,
-                                    _D, _D, _D]
+                                    _D, _D, _D, ctypes.c_int]
         lib.oracle_init.argtypes = [_P, _D, _D, _D]
         lib.oracle_solve.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int64, _D, _D,
                                      _D, ctypes.POINTER(_Stats), _D, ctypes.c_int64,
-                                     ctypes.c_double, ctypes.c_double, ctypes.c_double]
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int]
         lib.oracle_control_at.argtypes = [_P, _D, _D, _D, _D]
         lib.oracle_optimal_control.argtypes = [_P, ctypes.c_int, _D, _D, _D]
         lib.oracle_gradient.argtypes = [_P, ctypes.c_int, _D, _D]
@@ -255,21 +256,30 @@ def init(P, l, k=None):
     return V
 
 
-def step(P, scheme, rk, dt, alpha, l, V):
-    """One Runge-Kutta step + min(., l).  Returns (V_next, max|dV|)."""
+BRS, LOCAL_LF = 1, 2
+
+
+def _flags(brs, local_lf):
+    return (BRS if brs else 0) | (LOCAL_LF if local_lf else 0)
+
+
+def step(P, scheme, rk, dt, alpha, l, V, brs=False, local_lf=False):
+    """One Runge-Kutta step + min(., l) (none with brs: Eq. (5) alone).
+    Returns (V_next, max|dV|)."""
     l, V = _f64(l), _f64(V)
     out = np.empty_like(V)
     delta = ctypes.c_double()
     a = _alpha_arr(alpha)
     rc = _load().oracle_step(ctypes.byref(P), SCHEMES[scheme], int(rk), float(dt), _ptr(a),
-                             _ptr(l), _ptr(V), _ptr(out), ctypes.byref(delta))
+                             _ptr(l), _ptr(V), _ptr(out), ctypes.byref(delta),
+                             _flags(brs, local_lf))
     if rc != 0:
         raise MemoryError("oracle_step")
     return out, delta.value
 
 
 def solve(P, l, k=None, scheme="eno2", rk=2, cfl=0.5, tol=1e-6, horizon=0.0, max_steps=0,
-          history=0, tol_rate=0.0, interval=0.0, interval_tol=0.0):
+          history=0, tol_rate=0.0, interval=0.0, interval_tol=0.0, brs=False, local_lf=False):
     """March to convergence: max|dV| of one step < tol + tol_rate dt, or (with
     interval > 0) the change of V over K = round(interval / dt) steps below
     interval_tol (Sec. V).  Returns (V, stats dict[, history array])."""
@@ -282,7 +292,7 @@ def solve(P, l, k=None, scheme="eno2", rk=2, cfl=0.5, tol=1e-6, horizon=0.0, max
                               float(horizon), int(max_steps), _ptr(l),
                               None if kk is None else _ptr(kk), _ptr(V), ctypes.byref(st),
                               _ptr(hist), int(history), float(tol_rate), float(interval),
-                              float(interval_tol))
+                              float(interval_tol), _flags(brs, local_lf))
     if rc < 0:
         raise ValueError("oracle_solve rejected its input")
     stats = {"steps": st.steps, "tau": st.tau, "dt": st.dt, "last_delta": st.last_delta,

@@ -57,6 +57,16 @@
 enum { OR_FN_TAN = 0, OR_FN_SIN = 1, OR_FN_COS = 2 };
 enum { OR_ENO1 = 1, OR_ENO2 = 2, OR_WENO5 = 5 };
 
+/* Variants of the march (flags of oracle_step / oracle_solve):
+ *   OR_BRS: march the HJI PDE of Eq. (5) alone, without the projection onto
+ *     V <= l of Eq. (7): the value of the backward reachable set at time
+ *     tau (the target reached at exactly tau, Sec. II-B) instead of the
+ *     tube;
+ *   OR_LOCAL_LF: Lax-Friedrichs dissipation with the node's own
+ *     coefficients alpha_a(x) = max_{u,d} |f_a(x,u,d)| instead of their
+ *     maxima over the grid (dt stays the grid-wide CFL step). */
+enum { OR_BRS = 1, OR_LOCAL_LF = 2 };
+
 typedef struct {
     int ndim;
     int64_t n[OR_MAXD];
@@ -335,7 +345,7 @@ void oracle_one_sided(int scheme, const double* v, double dx, double* pm, double
  * of dV/dtau = H(x, grad V):
  *   L = H(x, (p+ + p-)/2) + sum_a alpha_a (p+_a - p-_a) / 2. */
 static void spatial_operator(const oracle_problem* P, int scheme, const double* alpha,
-                             const double* W, double* L) {
+                             const double* W, double* L, int flags) {
     int64_t total = oracle_num_cells(P);
     int g = ghost_width(scheme);
     double dx[OR_MAXD];
@@ -352,8 +362,12 @@ static void spatial_operator(const oracle_problem* P, int scheme, const double* 
             pbar[a] = 0.5 * (pp[a] + pm[a]);
         }
         double h = oracle_hamiltonian(P, x, pbar);
+        double al[OR_MAXD];
+        if (flags & OR_LOCAL_LF) oracle_alpha_point(P, x, al);
+        else
+            for (int a = 0; a < P->ndim; ++a) al[a] = alpha[a];
         double diss = 0.0;
-        for (int a = 0; a < P->ndim; ++a) diss += alpha[a] * 0.5 * (pp[a] - pm[a]);
+        for (int a = 0; a < P->ndim; ++a) diss += al[a] * 0.5 * (pp[a] - pm[a]);
         L[cidx] = h + diss;
     }
 }
@@ -448,7 +462,7 @@ void oracle_gradient(const oracle_problem* P, int scheme, const double* V, doubl
 /* The operator L(W) on its own, exposed for tests. */
 int oracle_operator(const oracle_problem* P, int scheme, const double* alpha, const double* W,
                     double* L) {
-    spatial_operator(P, scheme, alpha, W, L);
+    spatial_operator(P, scheme, alpha, W, L, 0);
     return 0;
 }
 
@@ -460,7 +474,7 @@ int oracle_operator(const oracle_problem* P, int scheme, const double* alpha, co
  * followed by the projection V' <- min(V', l) of Eq. (7)/(8).
  * Writes V' to Vout and returns max |V' - V| through *delta. */
 int oracle_step(const oracle_problem* P, int scheme, int rk, double dt, const double* alpha,
-                const double* l, const double* V, double* Vout, double* delta) {
+                const double* l, const double* V, double* Vout, double* delta, int flags) {
     int64_t total = oracle_num_cells(P);
     double* L = (double*)malloc(sizeof(double) * (size_t)total);
     double* W1 = (double*)malloc(sizeof(double) * (size_t)total);
@@ -471,25 +485,25 @@ int oracle_step(const oracle_problem* P, int scheme, int rk, double dt, const do
         free(W2);
         return -1;
     }
-    spatial_operator(P, scheme, alpha, V, L);
+    spatial_operator(P, scheme, alpha, V, L, flags);
     if (rk == 1) {
         for (int64_t c = 0; c < total; ++c) Vout[c] = V[c] + dt * L[c];
     } else {
         for (int64_t c = 0; c < total; ++c) W1[c] = V[c] + dt * L[c];
-        spatial_operator(P, scheme, alpha, W1, L);
+        spatial_operator(P, scheme, alpha, W1, L, flags);
         if (rk == 2) {
             for (int64_t c = 0; c < total; ++c) Vout[c] = 0.5 * V[c] + 0.5 * (W1[c] + dt * L[c]);
         } else {
             for (int64_t c = 0; c < total; ++c)
                 W2[c] = 0.75 * V[c] + 0.25 * (W1[c] + dt * L[c]);
-            spatial_operator(P, scheme, alpha, W2, L);
+            spatial_operator(P, scheme, alpha, W2, L, flags);
             for (int64_t c = 0; c < total; ++c)
                 Vout[c] = V[c] / 3.0 + 2.0 * (W2[c] + dt * L[c]) / 3.0;
         }
     }
     double dmax = 0.0;
     for (int64_t c = 0; c < total; ++c) {
-        if (l[c] < Vout[c]) Vout[c] = l[c];
+        if (!(flags & OR_BRS) && l[c] < Vout[c]) Vout[c] = l[c];
         double ch = fabs(Vout[c] - V[c]);
         if (ch > dmax) dmax = ch;
     }
@@ -517,7 +531,7 @@ void oracle_init(const oracle_problem* P, const double* l, const double* k, doub
 int oracle_solve(const oracle_problem* P, int scheme, int rk, double cfl, double tol,
                  double horizon, int64_t max_steps, const double* l, const double* k,
                  double* V, oracle_stats* st, double* history, int64_t hist_len,
-                 double tol_rate, double interval, double interval_tol) {
+                 double tol_rate, double interval, double interval_tol, int flags) {
     double alpha[OR_MAXD], dt;
     if (oracle_alpha_dt(P, cfl, alpha, &dt) != 0) return -1;
     int64_t total = oracle_num_cells(P);
@@ -539,13 +553,16 @@ int oracle_solve(const oracle_problem* P, int scheme, int rk, double cfl, double
             return -1;
         }
     }
-    oracle_init(P, l, k, V);
+    /* With the projection off (Eq. (5) alone) a given start k is taken as
+     * it is; otherwise V(x,0) = min(k, l) (Sec. III). */
+    if ((flags & OR_BRS) && k) memcpy(V, k, sizeof(double) * (size_t)total);
+    else oracle_init(P, l, k, V);
     if (snap) memcpy(snap, V, sizeof(double) * (size_t)total);
     double tau = 0.0, delta = INFINITY;
     int64_t steps = 0;
     int converged = 0;
     for (;;) {
-        if (oracle_step(P, scheme, rk, dt, alpha, l, V, Vn, &delta) != 0) {
+        if (oracle_step(P, scheme, rk, dt, alpha, l, V, Vn, &delta, flags) != 0) {
             free(Vn);
             free(snap);
             return -1;

@@ -16,6 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "_hji.so")
 SOURCES = ["hji_stage_f64.cu", "hji_stage_f32.cu", "hji_march_f64.cu", "hji_march_f32.cu",
+           "hji_llf_f64.cu", "hji_llf_f32.cu",
            "hji_setup.cu", "hji_capi.cu", "hji_noalloc.cu", "hji_peak.cu", "hji_control.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-O3",

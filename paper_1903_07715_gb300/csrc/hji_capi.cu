@@ -278,8 +278,19 @@ int rk_plan(int rk, StagePlan* p) {
     return 3;
 }
 
-hji::StageLauncher launcher(bool f32, int ndim, int scheme, bool last, int variant,
-                            bool interval) {
+// Kernel flavours beyond the default stage kernel.
+constexpr int kFlavorInterval = 1;  // last stage with Sec. V's interval test
+constexpr int kFlavorLocalLF = 2;   // local Lax-Friedrichs (interval test included)
+
+int flavor_of(const hji_solve_opts* o) {
+    return (o->interval > 0.0 ? kFlavorInterval : 0) | (o->local_lf ? kFlavorLocalLF : 0);
+}
+
+hji::StageLauncher launcher(bool f32, int ndim, int scheme, bool last, int variant, int flavor) {
+    if (flavor & kFlavorLocalLF)
+        return f32 ? hji::stage_launcher_llf_f32(ndim, scheme, last)
+                   : hji::stage_launcher_llf_f64(ndim, scheme, last);
+    const bool interval = (flavor & kFlavorInterval) != 0;
     return f32 ? hji::stage_launcher_f32(ndim, scheme, last, variant, interval)
                : hji::stage_launcher_f64(ndim, scheme, last, variant, interval);
 }
@@ -287,13 +298,21 @@ hji::StageLauncher launcher(bool f32, int ndim, int scheme, bool last, int varia
 // CTAs of one stage launch: as many as fit on every SM at once (each stage
 // kernel has its own occupancy), at most one per tile.
 int stage_grid(bool f32, int ndim, int scheme, long long total_tiles, int variant, bool last,
-               bool interval) {
-    const int b = f32 ? hji::stage_max_blocks_f32(ndim, scheme, last, variant, interval)
-                      : hji::stage_max_blocks_f64(ndim, scheme, last, variant, interval);
+               int flavor) {
+    const bool interval = (flavor & kFlavorInterval) != 0;
+    const int b = (flavor & kFlavorLocalLF)
+                      ? (f32 ? hji::stage_max_blocks_llf_f32(ndim, scheme, last)
+                             : hji::stage_max_blocks_llf_f64(ndim, scheme, last))
+                      : (f32 ? hji::stage_max_blocks_f32(ndim, scheme, last, variant, interval)
+                             : hji::stage_max_blocks_f64(ndim, scheme, last, variant, interval));
     long long g = (long long)num_sms() * b;
     if (g > total_tiles) g = total_tiles;
     return g < 1 ? 1 : (int)g;
 }
+
+// AUTO takes the multi-step launch when a stage has at least this many
+// tiles per resident CTA.
+constexpr long long kMultiStepTilesPerCta = 4;
 
 // ---- tile-shape choices made by hji_autotune, per problem class ----
 std::mutex g_tune_mu;
@@ -372,6 +391,8 @@ hji_status validate_opts(hji_grid g, const hji_solve_opts* o) {
     if (!(o->interval >= 0.0) || !std::isfinite(o->interval) || !(o->interval_tol >= 0.0) ||
         !std::isfinite(o->interval_tol))
         return fail(g, HJI_E_INVALID, "interval and interval_tol must be finite and >= 0");
+    if ((o->brs != 0 && o->brs != 1) || (o->local_lf != 0 && o->local_lf != 1))
+        return fail(g, HJI_E_INVALID, "brs and local_lf must be 0 or 1");
     return HJI_OK;
 }
 
@@ -431,6 +452,8 @@ hji_status make_desc(hji_grid g, const hji_solve_opts* o, int* active, int varia
     D.interval = o->interval;
     D.interval_tol = o->interval_tol;
     D.snap = o->interval > 0.0 ? g->snap : nullptr;
+    D.brs = o->brs;
+    D.local_lf = o->local_lf;
     D.horizon = o->horizon;
     D.max_steps = o->max_steps > 0 ? o->max_steps : 1000000;
     D.V[0] = g->V[0];
@@ -463,12 +486,12 @@ hji_status make_desc(hji_grid g, const hji_solve_opts* o, int* active, int varia
 // Capture `steps` steps of the march (all RK stages) into a graph.
 hji_status capture_chunk(hji_grid g, cudaStream_t cap, bool f32, int ndim, int scheme, int rk,
                          int steps, const hji::StageArgs& base, const int* grid, int variant,
-                         bool interval, cudaGraphExec_t* out) {
+                         int flavor, cudaGraphExec_t* out) {
     StagePlan plan[3];
     const int ns = rk_plan(rk, plan);
     hji::StageLauncher L[3];
     for (int i = 0; i < ns; ++i) {
-        L[i] = launcher(f32, ndim, scheme, plan[i].last, variant, interval);
+        L[i] = launcher(f32, ndim, scheme, plan[i].last, variant, flavor);
         if (!L[i]) return fail(g, HJI_E_INVALID, "no kernel for this ndim/scheme");
     }
     HJI_CUDA(g, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
@@ -554,7 +577,7 @@ cudaError_t timed_march(const hji_solve_opts* o, bool f32, int ndim, const hji::
     const int ns = rk_plan(o->rk_order, plan);
     hji::StageLauncher Lk[3];
     for (int i = 0; i < ns; ++i) {
-        Lk[i] = launcher(f32, ndim, o->scheme, plan[i].last, variant, o->interval > 0.0);
+        Lk[i] = launcher(f32, ndim, o->scheme, plan[i].last, variant, flavor_of(o));
         if (!Lk[i]) return cudaErrorInvalidValue;
     }
     const int steps = o->max_steps;
@@ -631,6 +654,7 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
     int variant = pick_variant(g0->prec, ndim, o, cells_all / count);
     if (o->tile_variant > 0 && g_force_variant < 0)
         variant = (ndim == 2 && o->tile_variant <= hji::kTileVariants) ? o->tile_variant - 1 : 0;
+    if (o->local_lf) variant = 0;  // the local-dissipation kernels have the default shape
     // Launch-wide device scratch (descriptors, tile list, counters) lives on
     // the first grid and is reused (grown on demand) by every solve it leads,
     // together with the captured graph of a chunk.
@@ -742,20 +766,26 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
     // launch (every CTA resident: at most march_max_blocks per SM).
     const int chunk = o->check_every > 0 ? o->check_every : 32;
     const bool interval = o->interval > 0.0;
-    bool multi = !g_stage_timer && (o->march == HJI_MARCH_MULTI_STEP ||
-                                    (o->march == HJI_MARCH_AUTO && ndim <= 2));
+    const int flavor = flavor_of(o);
+    bool multi = !g_stage_timer && o->march != HJI_MARCH_PER_STAGE && ndim <= 2 && !o->local_lf;
     int mgrid = 0;
     if (multi) {
         const int b = f32 ? hji::march_max_blocks_f32(ndim, o->scheme, variant, interval)
                           : hji::march_max_blocks_f64(ndim, o->scheme, variant, interval);
         long long gm = (long long)num_sms() * b;
+        // AUTO: the multi-step launch pays a grid-wide barrier per stage in
+        // place of a kernel boundary; that wins when every CTA has several
+        // tiles per stage, and loses on short stages of a tile or two per
+        // CTA (measured: 8192^2 and a batch of 256 grids faster, 1001^2
+        // slower).
+        if (o->march == HJI_MARCH_AUTO && total_tiles < kMultiStepTilesPerCta * gm) gm = 0;
         if (gm > total_tiles) gm = total_tiles;
         mgrid = (int)gm;
         multi = mgrid >= 1;
     }
     const int grid[2] = {
-        multi ? mgrid : stage_grid(f32, ndim, o->scheme, total_tiles, variant, false, interval),
-        multi ? 0 : stage_grid(f32, ndim, o->scheme, total_tiles, variant, true, interval)};
+        multi ? mgrid : stage_grid(f32, ndim, o->scheme, total_tiles, variant, false, flavor),
+        multi ? 0 : stage_grid(f32, ndim, o->scheme, total_tiles, variant, true, flavor)};
     hji::StageArgs base{d_desc, d_tiles, d_ntiles, 0, 0, 0.0, 0.0, 0.0f, 0.0f, 0};
     unsigned* d_barrier = reinterpret_cast<unsigned*>(d_active + 2);
     int* d_fault = d_active + 3;
@@ -765,7 +795,7 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
     // shape (scheme, RK order, chunk, grid, tile shape, launch mode) are
     // unchanged.
     const long long key[8] = {(long long)o->scheme, o->rk_order, chunk, grid[0], grid[1],
-                              variant + (multi ? 16 : 0) + (interval ? 32 : 0), ndim, f32 ? 1 : 0};
+                              variant + (multi ? 16 : 0) + 32 * flavor, ndim, f32 ? 1 : 0};
     if (g_stage_timer) {
         // the timed march launches its stages one by one
     } else if (g0->graph && std::memcmp(key, g0->graph_key, sizeof(key)) == 0) {
@@ -775,7 +805,7 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
         st = multi ? capture_march(g0, g0->cap_stream, f32, ndim, o->scheme, o->rk_order, chunk, base,
                                    mgrid, variant, interval, d_active, d_barrier, d_fault, &exec)
                    : capture_chunk(g0, g0->cap_stream, f32, ndim, o->scheme, o->rk_order, chunk, base,
-                                   grid, variant, interval, &exec);
+                                   grid, variant, flavor, &exec);
         if (st != HJI_OK) return st;
         g0->graph = exec;
         std::memcpy(g0->graph_key, key, sizeof(key));
@@ -1110,10 +1140,10 @@ hji_status hji_engine_create(int ndim, hji_precision prec, const hji_solve_opts*
         hji_engine_destroy(e);
         return efail(nullptr, HJI_E_NOMEM, "engine allocation failed");
     }
-    e->variant = pick_variant(prec, ndim, o, 1ll << 20);
+    e->variant = o->local_lf ? 0 : pick_variant(prec, ndim, o, 1ll << 20);
     for (int last = 0; last < 2; ++last)
         e->grid[last] = stage_grid(prec == HJI_F32, ndim, o->scheme, 1ll << 40, e->variant, last != 0,
-                                   o->interval > 0.0);
+                                   flavor_of(o));
     *out = e;
     return HJI_OK;
 }
@@ -1289,7 +1319,7 @@ hji_status hji_engine_step(hji_engine e, int* active, int* queued) {
             hji::StageArgs base{e->d_desc, e->d_tiles, e->d_counts + 1, 0, 0, 0.0, 0.0, 0.0f, 0.0f, 0};
             hji_status st = capture_chunk(nullptr, e->cap, f32, e->ndim, e->o.scheme, e->o.rk_order,
                                           e->chunk, base, e->grid, e->variant,
-                                          e->o.interval > 0.0, &e->graph);
+                                          flavor_of(&e->o), &e->graph);
             if (st != HJI_OK) return efail(e, st, g_create_error);
         }
         ce = cudaGraphLaunch(e->graph, e->s);

@@ -45,6 +45,7 @@ struct CtxConst {
     T cmid[MAXD];  // c + G umid + E dmid: the box centres' share of the drift
     T A[MAXD * MAXD], G[MAXD * MAXU], E[MAXD * MAXU];
     T urad[MAXU], drad[MAXU];  // half-widths of the control and disturbance boxes
+    T arad[MAXD];              // sum_j urad_j |G_aj| + sum_k drad_k |E_ak| per row a
     T dt;
 };
 
@@ -106,6 +107,8 @@ struct InstDesc {
     Dyn dyn;
     double cfl, tol, horizon, tol_rate;
     double interval, interval_tol;  // Sec. V's interval test (interval 0: off)
+    int brs;                  // 1: no projection onto V <= l (Eq. (5) alone)
+    int local_lf;             // 1: node-wise Lax-Friedrichs coefficients
     void* snap;               // its snapshot of V (the high word for FP32), or null
     long long max_steps;
     void* V[2];               // ping-pong value buffers: V[cur] = V^n
@@ -212,6 +215,12 @@ int march_max_blocks_f32(int ndim, int scheme, int variant = 0, bool interval = 
 // stage with Sec. V's interval test compiled in.
 StageLauncher stage_launcher_f64(int ndim, int scheme, bool last, int variant = 0,
                                  bool interval = false);
+// Local Lax-Friedrichs variants (default tile shape; the last stage has the
+// interval test compiled in).
+StageLauncher stage_launcher_llf_f64(int ndim, int scheme, bool last);
+StageLauncher stage_launcher_llf_f32(int ndim, int scheme, bool last);
+int stage_max_blocks_llf_f64(int ndim, int scheme, bool last);
+int stage_max_blocks_llf_f32(int ndim, int scheme, bool last);
 StageLauncher stage_launcher_f32(int ndim, int scheme, bool last, int variant = 0,
                                  bool interval = false);
 int stage_max_blocks_f64(int ndim, int scheme, bool last, int variant = 0, bool interval = false);

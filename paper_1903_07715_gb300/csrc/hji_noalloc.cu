@@ -173,6 +173,9 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
         return nfail(HJI_E_INVALID, "tile_variant must be 0..HJI_TILE_VARIANTS");
     if (o->interval != 0.0)
         return nfail(HJI_E_INVALID, "the interval test is not available without allocation");
+    if (o->local_lf != 0)
+        return nfail(HJI_E_INVALID, "local Lax-Friedrichs is not available without allocation");
+    if (o->brs != 0 && o->brs != 1) return nfail(HJI_E_INVALID, "brs must be 0 or 1");
     if (o->init == HJI_INIT_USER_K && !k) return nfail(HJI_E_INVALID, "HJI_INIT_USER_K needs k");
     if (o->init != HJI_INIT_STANDARD && o->init != HJI_INIT_USER_K && o->init != HJI_INIT_RESIDENT)
         return nfail(HJI_E_INVALID, "unknown init mode");
@@ -305,6 +308,7 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
     D.cfl = o->cfl;
     D.tol = o->tol;
     D.tol_rate = o->tol_rate;
+    D.brs = o->brs;
     D.horizon = o->horizon;
     D.max_steps = o->max_steps > 0 ? o->max_steps : 1000000;
     D.V[0] = base + o_v0;

@@ -70,6 +70,13 @@ __device__ void fill_ctx_const(const InstDesc& D, InstState* st) {
             cm += D.dyn.E[i * MAXU + j] * (0.5 * (D.dyn.dlo[j] + D.dyn.dhi[j]));
         }
         kd.cmid[i] = cm;
+        double ar = 0.0;
+        for (int j = 0; j < MAXU; ++j) {
+            ar += fabs(D.dyn.G[i * MAXU + j]) * kd.urad[j];
+            ar += fabs(D.dyn.E[i * MAXU + j]) * kd.drad[j];
+        }
+        kd.arad[i] = ar;
+        kf.arad[i] = static_cast<float>(ar);
         kf.lo[i] = static_cast<float>(kd.lo[i]);
         kf.dx[i] = static_cast<float>(kd.dx[i]);
         kf.inv_dx[i] = static_cast<float>(kd.inv_dx[i]);
@@ -277,7 +284,8 @@ __global__ void __launch_bounds__(kThreads) init_kernel(const InstDesc* __restri
             const T kv = k[c];
             const T klo = (klo_p != nullptr && Vlo != nullptr) ? klo_p[c] : T(0);
             if (!isfinite(kv)) bad = 1u;
-            if (kv < lv || (kv == lv && klo < T(0))) {
+            // With the projection off (Eq. (5) alone) the start is k as given.
+            if (D.brs || kv < lv || (kv == lv && klo < T(0))) {
                 v = kv;
                 vlo = klo;
             }

@@ -331,7 +331,9 @@ struct TileCtx {
     T lo[MAXD], dx[MAXD], inv_dx[MAXD], half_alpha[MAXD];
     T cmid[MAXD], A[MAXD * MAXD], G[MAXD * MAXU], E[MAXD * MAXU];
     T urad[MAXU], drad[MAXU];  // half-widths of the control and disturbance boxes
+    T arad[MAXD];              // per row: sum_j urad_j |G_aj| + sum_k drad_k |E_ak|
     int term_row[MAXT], term_axis[MAXT];
+    int project;               // 1: V <- min(V, l) after the step (Eq. (7)); 0: Eq. (5) alone
     T dt;
     const T* win;   // stencil input (FP64: the stage state; FP32: V^n hi word)
     const T* din;   // FP32: stage increment added to win (null for stage 1)
@@ -361,6 +363,28 @@ struct TileCtx {
     const CUtensorMap* tm_l;     // l at the tile nodes
     const CUtensorMap* tm_vn;    // FP64 V^n at the tile nodes
 };
+
+// Row a of the drift at a node, f0_a(x) = c_a + G_a umid + E_a dmid + A_a x
+// + the nonlinear terms of row a: with arad_a it gives the node's own
+// dissipation coefficient max_{u,d} |f_a(x,u,d)| = |f0_a(x)| + arad_a (local
+// Lax-Friedrichs).  idx are the node's indices; the fastest index may lie
+// past the grid's edge for the tail of a run (its table reads are clamped,
+// its result unused).
+template <typename T, int NDIM>
+__device__ __forceinline__ T row_drift(const TileCtx<T>& C, const int* idx, int a) {
+    T f = C.cmid[a];
+#pragma unroll
+    for (int j = 0; j < NDIM; ++j) f += C.A[a * MAXD + j] * (C.lo[j] + T(idx[j]) * C.dx[j]);
+    for (int tt = 0; tt < C.nterms; ++tt) {
+        if (C.term_row[tt] != a) continue;
+        const int ax = C.term_axis[tt];
+        int ia = idx[0];
+#pragma unroll
+        for (int r = 1; r < NDIM; ++r) ia = ax == r ? idx[r] : ia;
+        f += __ldg(C.table + tt * C.table_stride + min(ia, C.n[ax] - 1));
+    }
+    return f;
+}
 
 // The set-up pass's constants of an instance in precision T.
 template <typename T>
@@ -401,6 +425,7 @@ __device__ __noinline__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict_
         C.inv_dx[i] = K.inv_dx[i];
         C.half_alpha[i] = K.half_alpha[i];
         C.cmid[i] = K.cmid[i];
+        C.arad[i] = K.arad[i];
     } else if (t == 96) {
         InstState* st = D.state;
         const int cur = *((volatile int*)&st->cur);
@@ -409,6 +434,7 @@ __device__ __noinline__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict_
         C.cur = cur;
         C.m = D.dyn.m;
         C.q = D.dyn.q;
+        C.project = D.brs ? 0 : 1;
         C.nterms = D.dyn.nterms;
         C.dt = K.dt;
         C.tiles_x = static_cast<int>(D.tiles_x);
@@ -635,7 +661,7 @@ struct StageSmem {
     static constexpr int DYS = 2 * BUFB;
     static constexpr int PMY = DYS + DYSB;
     static constexpr int PPY = PMY + PYB;
-    static constexpr int BYTES = PPY + PYB;
+    static constexpr int BYTES = PPY + PYB + 128;  // + alignment slack (smem_layout_base)
     static __host__ __device__ constexpr int H(int b) { return b * BUFB; }
     static __host__ __device__ constexpr int LO(int b) { return b * BUFB + WINB; }
     static __host__ __device__ constexpr int DD(int b) { return b * BUFB + 2 * WINB; }
@@ -713,9 +739,19 @@ template <typename T, int NDIM, int SCHEME, bool LAST>
 constexpr int kMinBlocks = sizeof(T) != 4 ? 2 : NDIM > 2 ? 2 : 4;
 
 // The kernels' dynamic shared memory (the tile windows and per-tile
-// arrays; StageSmem gives the layout).  Only 16-byte alignment is needed:
-// the tensor copies use no swizzle and the widest accesses are 16 bytes.
+// arrays; StageSmem gives the layout, whose blocks sit at multiples of 128
+// bytes from its base).  A tiled tensor copy needs a 128-byte-aligned
+// shared destination, and the base of dynamic shared memory is only
+// guaranteed 16-byte alignment, so the layout starts at the first 128-byte
+// boundary (BYTES includes the 128 bytes of slack).  The offset is taken in
+// the shared window itself, so the compiler still addresses the layout as
+// shared memory.
 extern __shared__ __align__(16) unsigned char hji_smem[];
+
+__device__ __forceinline__ unsigned char* smem_layout_base() {
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(hji_smem));
+    return hji_smem + ((128u - (a & 127u)) & 127u);
+}
 
 // One Runge-Kutta stage of every live instance, as run by one CTA over its
 // share of the tile list (the body of a stage launch).  The caller owns the
@@ -723,16 +759,18 @@ extern __shared__ __align__(16) unsigned char hji_smem[];
 // phase bits; the tile context, reduction slots and tile placements are
 // this function's own shared variables.  COH selects coherent loads for
 // fields that another CTA may have written earlier in the same launch.
-// INTERVAL (last stage only) compiles in Sec. V's interval test.  Returns
+// INTERVAL (last stage only) compiles in Sec. V's interval test; LLF the
+// node-wise (local) Lax-Friedrichs coefficients.  Returns
 // false when a bounded wait gave up (the failure is recorded in the
 // instance's state; the CTA must leave).
-template <typename T, int NDIM, int SCHEME, bool LAST, int V, bool COH, bool INTERVAL>
+template <typename T, int NDIM, int SCHEME, bool LAST, int V, bool COH, bool INTERVAL,
+          bool LLF = false>
 __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, unsigned& phase) {
     using L = StageSmem<T, NDIM, SCHEME, LAST, V>;
     __shared__ TileCtx<T> C;
     __shared__ T red[2 * (kThreads / 32)];
     __shared__ TileGeo geo_s[2];  // where the tile in each buffer sits (written by thread 0)
-    unsigned char* sb = hji_smem;
+    unsigned char* sb = smem_layout_base();
     constexpr int G = L::G, TY = L::TY, TX = L::TX, GROUPS = L::GROUPS;
     constexpr int GY = L::GY, SWX = L::SWX, SH = L::SH, WIN = L::WIN;
     constexpr int AX = NDIM - 1;                  // fastest axis
@@ -1002,7 +1040,18 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
             T Lv[4] = {T(0), T(0), T(0), T(0)};
             T pb[4][NDIM];
             auto fold = [&](int ax, int i, T pm_, T pp_) {
-                Lv[i] += C.half_alpha[ax] * (pp_ - pm_);
+                T ha;
+                if constexpr (LLF) {
+                    int nid[NDIM];
+#pragma unroll
+                    for (int b = 0; b < NDIM - 2; ++b) nid[b] = tg.sidx[b];
+                    if constexpr (NDIM >= 2) nid[AY] = gy;
+                    nid[AX] = gx0 + i;
+                    ha = T(0.5) * (fabs(row_drift<T, NDIM>(C, nid, ax)) + C.arad[ax]);
+                } else {
+                    ha = C.half_alpha[ax];
+                }
+                Lv[i] += ha * (pp_ - pm_);
                 pb[i][ax] = T(0.5) * (pp_ + pm_);
             };
             const long long gidx = tg.base + (long long)gy * sy + gx0;
@@ -1300,7 +1349,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                         const T bb = vh - hi;
                         T vl = (hi - (vh - bb)) + (sl - bb);
                         const T lv = lt.v[i];
-                        if (vh > lv || (vh == lv && vl > T(0))) {
+                        if (C.project && (vh > lv || (vh == lv && vl > T(0)))) {
                             vh = lv;
                             vl = T(0);
                         }
@@ -1347,7 +1396,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                         ld4(reinterpret_cast<const T*>(sb + L::LT(buf)) + ry * TX + 4 * grp);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        out[i] = fmin(out[i], lt.v[i]);
+                        if (C.project) out[i] = fmin(out[i], lt.v[i]);
                         if (i < nvalid) {
                             const T ch = fabs(out[i] - vn[i]);
                             dmax = (ch > dmax || ch != ch) ? ch : dmax;
@@ -1420,7 +1469,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
 }
 
 // One launch per Runge-Kutta stage (see stage_pass).
-template <typename T, int NDIM, int SCHEME, bool LAST, int V, bool INTERVAL>
+template <typename T, int NDIM, int SCHEME, bool LAST, int V, bool INTERVAL, bool LLF>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
     stage_kernel(const StageArgs a) {
     __shared__ __align__(8) unsigned long long bars[2];
@@ -1432,7 +1481,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, NDIM, SCHEME, LAST>)
     }
     __syncthreads();
     unsigned phase = 0u;  // bit b: parity of the next completion of buffer b
-    stage_pass<T, NDIM, SCHEME, LAST, V, false, INTERVAL>(a, bar0, phase);
+    stage_pass<T, NDIM, SCHEME, LAST, V, false, INTERVAL, LLF>(a, bar0, phase);
 }
 
 // ---- the multi-step march: every stage of `steps` steps in one launch ----
@@ -1554,28 +1603,28 @@ int max_blocks_march() {
     return b;
 }
 
-template <typename T, int NDIM, int SCHEME, bool LAST, int V, bool INTERVAL>
+template <typename T, int NDIM, int SCHEME, bool LAST, int V, bool INTERVAL, bool LLF = false>
 cudaError_t launch_stage(const StageArgs& a, int grid, cudaStream_t s) {
     using L = StageSmem<T, NDIM, SCHEME, LAST, V>;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, NDIM, SCHEME, LAST, V, INTERVAL>,
+        cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, NDIM, SCHEME, LAST, V, INTERVAL, LLF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(L::BYTES));
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    stage_kernel<T, NDIM, SCHEME, LAST, V, INTERVAL><<<grid, kThreads, L::BYTES, s>>>(a);
+    stage_kernel<T, NDIM, SCHEME, LAST, V, INTERVAL, LLF><<<grid, kThreads, L::BYTES, s>>>(a);
     return cudaGetLastError();
 }
 
-template <typename T, int NDIM, int SCHEME, bool LAST, int V, bool INTERVAL>
+template <typename T, int NDIM, int SCHEME, bool LAST, int V, bool INTERVAL, bool LLF = false>
 int max_blocks_stage() {
     using L = StageSmem<T, NDIM, SCHEME, LAST, V>;
-    cudaFuncSetAttribute(stage_kernel<T, NDIM, SCHEME, LAST, V, INTERVAL>,
+    cudaFuncSetAttribute(stage_kernel<T, NDIM, SCHEME, LAST, V, INTERVAL, LLF>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L::BYTES));
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stage_kernel<T, NDIM, SCHEME, LAST, V, INTERVAL>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stage_kernel<T, NDIM, SCHEME, LAST, V, INTERVAL, LLF>,
                                                       kThreads, L::BYTES) != cudaSuccess)
         return 1;
     return b > 0 ? b : 1;

@@ -377,3 +377,121 @@ def test_interval_rule_stops_the_running_example_limit_cycle(orc):
     V, st = orc.solve(P, l, scheme="eno2", rk=2, cfl=0.5, tol=0.0, interval=0.01,
                       interval_tol=1e-3, max_steps=20000)
     assert st["converged"] and st["steps"] < 20000
+
+
+def _semi_lagrangian_di(n, umax=1.0, iters=20000):
+    """An independent discretisation of the dynamic-programming recursion of
+    Eq. (8): V(x) <- min( l(x), max_u V(x + f(x,u) h) ) with bilinear
+    interpolation, controls at the box vertices {-umax, 0, umax}, and h the
+    grid spacing, iterated to a fixed point.  No derivative, Hamiltonian or
+    Runge-Kutta step of the oracle is involved."""
+    from scipy.interpolate import RegularGridInterpolator
+    gd, dyn, l = W.di_config(n, umax=umax)
+    x1, x2 = W.node_coords(gd)
+    X1, X2 = W.mesh(gd)
+    h = x1[1] - x1[0]
+    V = l.copy()
+    for _ in range(iters):
+        interp = RegularGridInterpolator((x1, x2), V, bounds_error=False, fill_value=None)
+        best = np.full_like(V, -np.inf)
+        for u in (-umax, 0.0, umax):
+            p1 = np.clip(X1 + X2 * h, -2.0, 2.0)
+            p2 = np.clip(X2 + u * h, -2.0, 2.0)
+            best = np.maximum(best, interp(np.stack([p1, p2], -1)))
+        Vn = np.minimum(l, best)
+        if np.abs(Vn - V).max() < 1e-10:
+            return gd, Vn
+        V = Vn
+    return gd, V
+
+
+def test_semi_lagrangian_cross_check(orc):
+    """P12: the oracle's converged value and the semi-Lagrangian fixed point
+    of Eq. (8) approach each other as the grid is refined (first order),
+    on the region where the braking trajectories stay on the grid."""
+    gaps = []
+    for n in (21, 41, 81):
+        gd, Vsl = _semi_lagrangian_di(n)
+        P = orc.problem(gd, W.double_integrator(umax=1.0))
+        l = W.target_strip(gd, 0, 1.0)
+        Vo, st = orc.solve(P, l, scheme="eno2", rk=2, cfl=0.5, tol=1e-8, max_steps=200000)
+        assert st["converged"]
+        X1, X2 = W.mesh(gd)
+        z = X1 + X2 * np.abs(X2) / 2.0
+        inner = (np.abs(z) <= 1.2) & (np.abs(X2) <= 1.2)
+        gaps.append(float(np.abs(Vo - Vsl)[inner].max()))
+    h = 4.0 / 20
+    assert gaps[0] <= 2.0 * h  # O(dx) at the coarsest grid
+    assert gaps[1] < 0.75 * gaps[0] and gaps[2] < 0.75 * gaps[1], gaps
+
+
+# ------------------------------------------- BRS and local Lax-Friedrichs
+
+def test_brs_advection_closed_form(orc):
+    """Eq. (5) alone (no projection onto V <= l) carries l along the flow:
+    for x' = c, V(x, tau) = l(x + c tau), the target value at exactly tau,
+    away from the grid edges where the extrapolated ghost nodes feed in.  The
+    kink of l is smeared by the scheme's dissipation, so the error there
+    shrinks like dx^(1/2) rather than dx."""
+    c, tau = 1.0, 0.5
+    l_fn = lambda x: np.abs(x) - 0.5  # noqa: E731
+    errs = []
+    for n in (101, 201, 401):
+        gd = W.grid([n], [-2.0], [2.0])
+        x = W.node_coords(gd)[0]
+        V, st = _solve(orc, gd, {"c": [c], "G": np.zeros((1, 0))}, l_fn(x), horizon=tau,
+                       tol=0.0, scheme="eno2", rk=2, brs=True)
+        inner = np.abs(x) <= 1.2
+        want = l_fn(x + c * st["tau"])
+        errs.append(np.abs(V - want)[inner].max())
+        # the tube value min_s l(x + c s) is below it, strictly somewhere
+        assert (advection_value(x, st["tau"], c, l_fn) < want - 0.1)[inner].any()
+        assert errs[-1] <= 0.6 * np.sqrt(4.0 / (n - 1))
+    assert errs[2] < errs[1] < errs[0]
+
+
+def test_brs_iterates_lie_above_the_tube(orc, mono):
+    """With the order-preserving ENO1/Euler update, the march without the
+    projection stays above the VI march step by step (the projection only
+    lowers values and the update preserves order)."""
+    P, l = mono["P"], mono["l"]
+    V = orc.init(P, l)
+    for n in range(1, 200):
+        V, _ = orc.step(P, "eno1", 1, mono["dt"], mono["alpha"], l, V, brs=True)
+        assert np.all(mono["std"][n] <= V + 1e-12), n
+    assert (V - mono["std"][199]).max() > 0.05
+
+
+def test_local_lf_equals_global_when_alpha_is_uniform(orc):
+    """x' = G u + E d (no state dependence): alpha_a(x) is the same at every
+    node, so the local and the grid-wide dissipation are the same numbers."""
+    gd = W.grid([41, 37], [-2.0, -1.0], [2.0, 1.0])
+    dyn = {"c": [0.3, -0.1], "G": [[1.0], [0.5]], "ulo": [-1.0], "uhi": [0.5],
+           "E": [[0.0], [1.0]], "dlo": [-0.2], "dhi": [0.1]}
+    X1, X2 = W.mesh(gd)
+    l = np.sqrt(X1 ** 2 + X2 ** 2) - 0.5
+    P = orc.problem(gd, dyn)
+    alpha, dt = orc.alpha_dt(P, 0.5)
+    for scheme, rk in (("eno2", 2), ("weno5", 3)):
+        a, _ = orc.step(P, scheme, rk, dt, alpha, l, l)
+        b, _ = orc.step(P, scheme, rk, dt, alpha, l, l, local_lf=True)
+        assert np.array_equal(a, b)
+
+
+def test_local_lf_converges_to_the_closed_form(orc):
+    """The double integrator's alpha_1(x) = |x2| varies over the grid; with
+    local coefficients the converged value still meets the closed form of
+    Eq. (3)-(4) (same O(dx) bound and zero level within 2 cells as the
+    grid-wide form), and the two forms differ by O(dx)."""
+    n = 101
+    gd, dyn, l = W.di_config(n)
+    X1, X2 = W.mesh(gd)
+    want = di_strip_value(X1, X2, 1.0)
+    mask = _di_mask(X1, X2, 1.0)
+    Vg, sg = _solve(orc, gd, dyn, l)
+    Vl, sl = _solve(orc, gd, dyn, l, local_lf=True)
+    assert sg["converged"] and sl["converged"]
+    dx = 4.0 / (n - 1)
+    assert np.abs(Vl - want)[mask].max() <= 3 * dx
+    assert brt_hausdorff(np.where(mask, Vl, 1.0), np.where(mask, want, 1.0)) <= 2.0
+    assert 0 < np.abs(Vl - Vg).max() <= 3 * dx
