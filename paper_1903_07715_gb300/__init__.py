@@ -350,7 +350,9 @@ def solve_opts(scheme="eno2", rk=2, cfl=0.5, tol=1e-6, horizon=0.0, max_steps=0,
 
 class Grid:
     """One grid handle.  `gd` is a grid dict ({"n","lo","hi","periodic"});
-    precision "f64" or "f32"; allocator: "torch" (default), "cuda" or None."""
+    precision "f64" or "f32"; allocator: "torch" (default), "cuda" or None
+    (the library's own cudaMallocAsync), or an hji_allocator structure (kept
+    alive by the caller for the grid's lifetime)."""
 
     def __init__(self, gd, precision="f64", allocator="torch"):
         self._h = ctypes.c_void_p()
@@ -361,7 +363,10 @@ class Grid:
         self.prec = HJI_F64 if precision == "f64" else HJI_F32
         n = (ctypes.c_int64 * nd)(*self.shape)
         per = _iarr(gd.get("periodic", [0] * nd))
-        alloc = torch_allocator() if allocator == "torch" else None
+        if isinstance(allocator, hji_allocator):
+            alloc = allocator
+        else:
+            alloc = torch_allocator() if allocator == "torch" else None
         _check(hji_grid_create(nd, n, _darr(gd["lo"]), _darr(gd["hi"]), per, self.prec,
                                ctypes.byref(alloc) if alloc is not None else None,
                                ctypes.byref(self._h)))
