@@ -350,7 +350,9 @@ def main():
         line["time_to_converge"] = time_to_converge(hji, torch, gd, dyn, l, l_dev, k_dev)
         line["hbm_workloads"] = hbm_workloads(hji, torch)
         line["config_rows"] = config_rows(hji, torch)
-        line["north_star_batch"] = north_star_batch(hji, torch)
+        line["north_star_batch"] = {
+            "paper_interval_test_0.001": north_star_batch(hji, torch, 1e-3),
+            "tight_interval_test_1e-5": north_star_batch(hji, torch, 1e-5)}
         line["serving"] = serving_both(hji, torch)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(budget_s=12.0)
@@ -678,21 +680,22 @@ def c2_analysis(hji, torch):
     return out
 
 
-def north_star_batch(hji, torch, budget_s=40.0):
+def north_star_batch(hji, torch, interval_tol, budget_s=40.0):
     """The 256-instance batch (config 4) solved as the batched FP32 warm
     form (one hji_batch_solve, each instance warm-started from its d = 0
     solution) against the plain per-instance FP64 standard solve (V0 = l,
     one hji_solve per instance, one after another) on the same GPU: time to
     converge and the FP32 results' distance to the FP64 ones.  ENO2/RK2,
     cfl 0.5, Sec. V's interval test (largest change over 0.01 of time below
-    0.001; the per-step test max|dV| < 1e-6 is never met by some of these
-    instances, whose ENO2 marches settle into small limit cycles).  The FP64
+    interval_tol: the paper's 0.001, or a tighter one for the accuracy bar;
+    the per-step test max|dV| < 1e-6 is never met by some of these instances,
+    whose ENO2 marches settle into small limit cycles).  The FP64
     solves run in instance order until
     budget_s of wall time is spent; the comparison covers those instances
     (their count is reported) and the batched time is scaled by their share
     of the batch's cell-updates."""
     insts = W.batch_instances(count=256, seed=1903)
-    o = dict(scheme="eno2", rk=2, cfl=0.5, tol=0.0, interval=0.01, interval_tol=1e-3,
+    o = dict(scheme="eno2", rk=2, cfl=0.5, tol=0.0, interval=0.01, interval_tol=interval_tol,
              max_steps=100000, check_every=32)
     ls = [W.instance_target(i) for i in insts]
     l32 = [torch.from_numpy(x.astype(np.float32)).cuda() for x in ls]
@@ -746,8 +749,8 @@ def north_star_batch(hji, torch, budget_s=40.0):
             "batched_ms_for_those_instances": ms_batch * share,
             "speedup": ms64 / max(1e-9, ms_batch * share),
             "worst_max_abs_over_max_l": worst_abs, "worst_brt_hausdorff_cells": worst_h,
-            "rule": "ENO2/RK2, cfl 0.5, Sec. V's interval test (change below 0.001 over "
-                    "0.01 of time)"}
+            "rule": "ENO2/RK2, cfl 0.5, Sec. V's interval test (change below %g over 0.01 "
+                    "of time)" % interval_tol}
 
 
 def serving_both(hji, torch):

@@ -39,6 +39,10 @@ struct Dyn {
 // at a small fraction of the FP32 rate on this GPU, and a few dozen dependent
 // FP64 operations per CTA at the start of every launch were on its critical
 // path.
+//
+// The stage kernels carry p- + p+ = 2 pbar per axis instead of pbar, so the
+// Hamiltonian's constants (cmid, A, G, E, and the term table) are stored
+// halved: every term of H is linear in pbar, and halving is exact.
 template <typename T>
 struct CtxConst {
     T lo[MAXD], dx[MAXD], inv_dx[MAXD], half_alpha[MAXD];
@@ -116,7 +120,8 @@ struct InstDesc {
     void* W2;                 // states (FP64) or stage increments (FP32)
     void* Vlo[2];             // FP32 only: low words, ping-pong with V: V^n = V[cur] + Vlo[cur]
     void* l;                  // target function l(x)
-    void* table;              // per-term tables: table[t*n_max + i] = w_t phi_t(x_axis(i))
+    void* table;              // per-term tables: table[t*n_max + i] = w_t phi_t(x_axis(i)) / 2
+                              // (halved like the stage kernels' other drift constants)
     long long table_stride;
     double* history;          // optional max|dV| per step (FP64), may be null
     long long history_len;

@@ -1,5 +1,5 @@
 // Per-solve set-up passes, run once before the march:
-//   * term tables: w_t phi_t(x_axis) per node of the term's axis, so the
+//   * term tables: w_t phi_t(x_axis) / 2 per node of the term's axis, so the
 //     stage kernel evaluates tan/sin/cos terms by a table read;
 //   * dissipation coefficients and CFL step: alpha_a = max over nodes of
 //     max_{u,d} |f_a(x,u,d)| and dt = cfl / max over nodes of
@@ -29,7 +29,8 @@ __global__ void __launch_bounds__(kThreads) table_kernel(const InstDesc* __restr
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.n[ax];
              i += gridDim.x * blockDim.x) {
             const double x = D.lo[ax] + (double)i * D.dx[ax];
-            table[t * D.table_stride + i] = T(D.dyn.term_w[t] * apply_fn(D.dyn.term_fn[t], x));
+            // halved, like the other drift constants of the stage kernels
+            table[t * D.table_stride + i] = T(0.5 * D.dyn.term_w[t] * apply_fn(D.dyn.term_fn[t], x));
         }
     }
 }
@@ -43,15 +44,16 @@ constexpr int kAlphaChunk = 16;  // consecutive nodes per alpha thread
 __device__ void fill_ctx_const(const InstDesc& D, InstState* st) {
     CtxConst<double>& kd = st->kd;
     CtxConst<float>& kf = st->kf;
+    // cmid, A, G, E halved: the stage kernels multiply them by 2 pbar.
     for (int i = 0; i < MAXD * MAXD; ++i) {
-        kd.A[i] = D.dyn.A[i];
-        kf.A[i] = static_cast<float>(D.dyn.A[i]);
+        kd.A[i] = 0.5 * D.dyn.A[i];
+        kf.A[i] = static_cast<float>(kd.A[i]);
     }
     for (int i = 0; i < MAXD * MAXU; ++i) {
-        kd.G[i] = D.dyn.G[i];
-        kf.G[i] = static_cast<float>(D.dyn.G[i]);
-        kd.E[i] = D.dyn.E[i];
-        kf.E[i] = static_cast<float>(D.dyn.E[i]);
+        kd.G[i] = 0.5 * D.dyn.G[i];
+        kf.G[i] = static_cast<float>(kd.G[i]);
+        kd.E[i] = 0.5 * D.dyn.E[i];
+        kf.E[i] = static_cast<float>(kd.E[i]);
     }
     for (int j = 0; j < MAXU; ++j) {
         kd.urad[j] = 0.5 * (D.dyn.uhi[j] - D.dyn.ulo[j]);
@@ -69,7 +71,7 @@ __device__ void fill_ctx_const(const InstDesc& D, InstState* st) {
             cm += D.dyn.G[i * MAXU + j] * (0.5 * (D.dyn.ulo[j] + D.dyn.uhi[j]));
             cm += D.dyn.E[i * MAXU + j] * (0.5 * (D.dyn.dlo[j] + D.dyn.dhi[j]));
         }
-        kd.cmid[i] = cm;
+        kd.cmid[i] = 0.5 * cm;
         double ar = 0.0;
         for (int j = 0; j < MAXU; ++j) {
             ar += fabs(D.dyn.G[i * MAXU + j]) * kd.urad[j];
@@ -81,7 +83,7 @@ __device__ void fill_ctx_const(const InstDesc& D, InstState* st) {
         kf.dx[i] = static_cast<float>(kd.dx[i]);
         kf.inv_dx[i] = static_cast<float>(kd.inv_dx[i]);
         kf.half_alpha[i] = static_cast<float>(kd.half_alpha[i]);
-        kf.cmid[i] = static_cast<float>(cm);
+        kf.cmid[i] = static_cast<float>(kd.cmid[i]);
     }
     kd.dt = st->dt;
     kf.dt = static_cast<float>(st->dt);

@@ -70,48 +70,66 @@ __device__ __forceinline__ T smaller_mag(T a, T b) {
 // reversing its triple) and third differences (-t3, -t1), so one set of
 // five differences serves p+ of one node and p- of its neighbour.
 //
-// WenoZ holds z1..z3 with forward weights (0.1 z1, 0.6 z2, 0.3 z3) and
-// reversed weights (0.1 z3, 0.6 z2, 0.3 z1), normalised by their sum:
-//   FP64: z = ((b_B b_C)^2, (b_A b_C)^2, (b_A b_B)^2), b = S + eps: the
-//         weights d_k / b_k^2 times the common factor (b_A b_B b_C)^2, one
-//         division (tiny = 1e-60 keeps the fourth powers above the FP64
-//         range floor);
+// Two exact rescalings shape the arithmetic into fused multiply-adds:
+//   * the normalised weights do not change when every S_k and eps are
+//     multiplied by one factor, so the indicators are formed as
+//     S'_k = S_k / (13/12) = p_k^2 + (3/13) q_k^2 with eps' = (12/13) eps;
+//   * numerator and denominator of the weighted correction are multiplied
+//     by 30:  forward  (z1 t1 + 1.5 z3 t3) / (3 z1 + 18 z2 + 9 z3),
+//             reversed (z3 t3 + 1.5 z1 t1) / (9 z1 + 18 z2 + 3 z3),
+//     so a set's products A = z1 t1, B = z3 t3 and u = 18 z2 serve both of
+//     its derivatives.
+//
+// WenoSet holds z1, z3, A, B, u of a set, where (z1, z2, z3) are the
+// weights d_k / b_k^2 up to a common factor (b = S' + eps'):
+//   FP64: z = ((b_B b_C)^2, (b_A b_C)^2, (b_A b_B)^2), the common factor
+//         (b_A b_B b_C)^2, one division (tiny = 1e-60 keeps the fourth
+//         powers above the FP64 range floor);
 //   FP32: z = (r_A^2, r_B^2, r_C^2), r = 1/b by the fast reciprocal; tiny =
 //         1e-18 keeps the sums below 2^126 (the range of the fast division)
 //         while exceeding 1e-6 max(v^2) only where every |v| < 1e-6 (flat
 //         data, where the weights do not matter).
 template <typename T>
-struct WenoZ {
-    T z1, z2, z3;
+struct WenoSet {
+    T z1, z3, A, B, u;
 };
 
-// Weights of a set from its first differences e1..e4 and m = max |v_k|.
+// A set from its first differences e1..e4, m = max |v_k| and its third
+// differences t1, t3.
 template <typename T>
-__device__ __forceinline__ WenoZ<T> weno_z(T e1, T e2, T e3, T e4, T m) {
+__device__ __forceinline__ WenoSet<T> weno_set(T e1, T e2, T e3, T e4, T m, T t1, T t3) {
+    constexpr T kq = T(3.0 / 13.0);           // (1/4) / (13/12)
+    constexpr T keps = T(1e-6 * 12.0 / 13.0);  // eps' = eps / (13/12)
     const T pA = e1 - e2, qA = e1 - T(3) * e2;
     const T pB = e2 - e3, qB = e2 + e3;
     const T pC = e3 - e4, qC = T(3) * e3 - e4;
-    const T sA = T(13.0 / 12.0) * pA * pA + T(0.25) * qA * qA;
-    const T sB = T(13.0 / 12.0) * pB * pB + T(0.25) * qB * qB;
-    const T sC = T(13.0 / 12.0) * pC * pC + T(0.25) * qC * qC;
-    WenoZ<T> z;
+    const T sA = fma(pA, pA, (kq * qA) * qA);
+    const T sB = fma(pB, pB, (kq * qB) * qB);
+    const T sC = fma(pC, pC, (kq * qC) * qC);
+    T z1, z2, z3;
     if constexpr (sizeof(T) == 4) {
-        const float eps = 1e-6f * (m * m) + 1e-18f;
+        const float eps = fmaf(keps * m, m, 1e-18f * (12.0f / 13.0f));
         const float rA = __fdividef(1.0f, sA + eps);
         const float rB = __fdividef(1.0f, sB + eps);
         const float rC = __fdividef(1.0f, sC + eps);
-        z.z1 = rA * rA;
-        z.z2 = rB * rB;
-        z.z3 = rC * rC;
+        z1 = rA * rA;
+        z2 = rB * rB;
+        z3 = rC * rC;
     } else {
-        const T eps = T(1e-6) * (m * m) + Num<T>::weno_tiny();
+        const T eps = fma(keps * m, m, Num<T>::weno_tiny() * T(12.0 / 13.0));
         const T bA = sA + eps, bB = sB + eps, bC = sC + eps;
         const T pBC = bB * bC, pAC = bA * bC, pAB = bA * bB;
-        z.z1 = pBC * pBC;
-        z.z2 = pAC * pAC;
-        z.z3 = pAB * pAB;
+        z1 = pBC * pBC;
+        z2 = pAC * pAC;
+        z3 = pAB * pAB;
     }
-    return z;
+    WenoSet<T> w;
+    w.z1 = z1;
+    w.z3 = z3;
+    w.A = z1 * t1;
+    w.B = z3 * t3;
+    w.u = T(18) * z2;
+    return w;
 }
 
 template <typename T>
@@ -122,18 +140,18 @@ __device__ __forceinline__ T ratio(T num, T den) {
 
 // p- on the forward set v1..v5 (phi_2 = -v2/6 + 5 v3/6 + v4/3).
 template <typename T>
-__device__ __forceinline__ T weno_fwd(T v2, T v3, T v4, T t1, T t3, const WenoZ<T>& z) {
+__device__ __forceinline__ T weno_fwd(T v2, T v3, T v4, const WenoSet<T>& w) {
     const T phi2 = v3 * T(5.0 / 6.0) - v2 * T(1.0 / 6.0) + v4 * T(1.0 / 3.0);
-    const T num = z.z1 * T(0.1 / 3.0) * t1 + z.z3 * T(0.3 / 6.0) * t3;
-    const T den = T(0.1) * z.z1 + T(0.6) * z.z2 + T(0.3) * z.z3;
+    const T num = fma(T(1.5), w.B, w.A);
+    const T den = fma(T(3), w.z1, fma(T(9), w.z3, w.u));
     return phi2 + ratio(num, den);
 }
 // p+ on the same set read in reverse (v5..v1).
 template <typename T>
-__device__ __forceinline__ T weno_rev(T v2, T v3, T v4, T t1, T t3, const WenoZ<T>& z) {
+__device__ __forceinline__ T weno_rev(T v2, T v3, T v4, const WenoSet<T>& w) {
     const T phi2 = v3 * T(5.0 / 6.0) - v4 * T(1.0 / 6.0) + v2 * T(1.0 / 3.0);
-    const T num = z.z3 * T(0.1 / 3.0) * t3 + z.z1 * T(0.3 / 6.0) * t1;
-    const T den = T(0.1) * z.z3 + T(0.6) * z.z2 + T(0.3) * z.z1;
+    const T num = fma(T(1.5), w.A, w.B);
+    const T den = fma(T(9), w.z1, fma(T(3), w.z3, w.u));
     return phi2 - ratio(num, den);
 }
 
@@ -146,10 +164,10 @@ __device__ __forceinline__ void weno5_pair(const T* D, T inv_dx, T& pm, T& pp) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) Tt[k] = E[k] - T(2) * E[k + 1] + E[k + 2];
     const T m14 = fmax(fmax(fabs(D[1]), fabs(D[2])), fmax(fabs(D[3]), fabs(D[4])));
-    const WenoZ<T> za = weno_z(E[0], E[1], E[2], E[3], fmax(m14, fabs(D[0])));
-    const WenoZ<T> zb = weno_z(E[1], E[2], E[3], E[4], fmax(m14, fabs(D[5])));
-    pm = weno_fwd(D[1], D[2], D[3], Tt[0], Tt[1], za) * inv_dx;
-    pp = weno_rev(D[2], D[3], D[4], Tt[1], Tt[2], zb) * inv_dx;
+    const WenoSet<T> wa = weno_set(E[0], E[1], E[2], E[3], fmax(m14, fabs(D[0])), Tt[0], Tt[1]);
+    const WenoSet<T> wb = weno_set(E[1], E[2], E[3], E[4], fmax(m14, fabs(D[5])), Tt[1], Tt[2]);
+    pm = weno_fwd(D[1], D[2], D[3], wa) * inv_dx;
+    pp = weno_rev(D[2], D[3], D[4], wb) * inv_dx;
 }
 
 // (p-, p+) at node c from the 2G undivided differences D[k] = W[k+1] - W[k]
@@ -364,9 +382,11 @@ struct TileCtx {
     const CUtensorMap* tm_vn;    // FP64 V^n at the tile nodes
 };
 
-// Row a of the drift at a node, f0_a(x) = c_a + G_a umid + E_a dmid + A_a x
-// + the nonlinear terms of row a: with arad_a it gives the node's own
-// dissipation coefficient max_{u,d} |f_a(x,u,d)| = |f0_a(x)| + arad_a (local
+// Half of row a of the drift at a node, f0_a(x)/2 with f0_a(x) = c_a +
+// G_a umid + E_a dmid + A_a x + the nonlinear terms of row a (the context's
+// drift constants and the term table are stored halved): with arad_a it
+// gives half the node's own dissipation coefficient,
+// max_{u,d} |f_a(x,u,d)| / 2 = |f0_a(x)/2| + arad_a / 2 (local
 // Lax-Friedrichs).  idx are the node's indices; the fastest index may lie
 // past the grid's edge for the tail of a run (its table reads are clamped,
 // its result unused).
@@ -1021,9 +1041,9 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                 const T t1 = e[0] - T(2) * e[1] + e[2], t3 = e[1] - T(2) * e[2] + e[3];
                 const T m = fmax(fmax(fmax(fabs(q[0][c]), fabs(q[1][c])), fmax(fabs(q[2][c]), fabs(q[3][c]))),
                                  fabs(q[4][c]));
-                const WenoZ<T> z = weno_z(e[0], e[1], e[2], e[3], m);
-                pmv[c] = weno_fwd(q[1][c], q[2][c], q[3][c], t1, t3, z) * iy;
-                ppv[c] = weno_rev(q[1][c], q[2][c], q[3][c], t1, t3, z) * iy;
+                const WenoSet<T> w = weno_set(e[0], e[1], e[2], e[3], m, t1, t3);
+                pmv[c] = weno_fwd(q[1][c], q[2][c], q[3][c], w) * iy;
+                ppv[c] = weno_rev(q[1][c], q[2][c], q[3][c], w) * iy;
             }
             if (j < TY) st4(reinterpret_cast<T*>(sb + L::PMY) + j * TX + 4 * g4, pmv);
             if (j > 0) st4(reinterpret_cast<T*>(sb + L::PPY) + (j - 1) * TX + 4 * g4, ppv);
@@ -1047,12 +1067,12 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                     for (int b = 0; b < NDIM - 2; ++b) nid[b] = tg.sidx[b];
                     if constexpr (NDIM >= 2) nid[AY] = gy;
                     nid[AX] = gx0 + i;
-                    ha = T(0.5) * (fabs(row_drift<T, NDIM>(C, nid, ax)) + C.arad[ax]);
+                    ha = fabs(row_drift<T, NDIM>(C, nid, ax)) + T(0.5) * C.arad[ax];
                 } else {
                     ha = C.half_alpha[ax];
                 }
                 Lv[i] += ha * (pp_ - pm_);
-                pb[i][ax] = T(0.5) * (pp_ + pm_);
+                pb[i][ax] = pp_ + pm_;  // 2 pbar: the Hamiltonian's constants are halved
             };
             const long long gidx = tg.base + (long long)gy * sy + gx0;
             // Slower axes first (their stencil lines are the largest live
@@ -1164,17 +1184,17 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                     for (int j = 1; j <= 7; ++j) Tt[j] = E[j] - T(2) * E[j + 1] + E[j + 2];
 #pragma unroll
                     for (int j = 1; j <= 9; ++j) a[j] = fabs(d[j]);
-                    auto set_z = [&](int j) {
+                    auto set_w = [&](int j) {
                         const T m = fmax(fmax(fmax(a[j], a[j + 1]), fmax(a[j + 2], a[j + 3])), a[j + 4]);
-                        return weno_z(E[j], E[j + 1], E[j + 2], E[j + 3], m);
+                        return weno_set(E[j], E[j + 1], E[j + 2], E[j + 3], m, Tt[j], Tt[j + 1]);
                     };
-                    WenoZ<T> zl = set_z(1);
+                    WenoSet<T> wl = set_w(1);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const WenoZ<T> zr = set_z(i + 2);
-                        fold(AX, i, weno_fwd(d[i + 2], d[i + 3], d[i + 4], Tt[i + 1], Tt[i + 2], zl) * ix,
-                             weno_rev(d[i + 3], d[i + 4], d[i + 5], Tt[i + 2], Tt[i + 3], zr) * ix);
-                        zl = zr;
+                        const WenoSet<T> wr = set_w(i + 2);
+                        fold(AX, i, weno_fwd(d[i + 2], d[i + 3], d[i + 4], wl) * ix,
+                             weno_rev(d[i + 3], d[i + 4], d[i + 5], wr) * ix);
+                        wl = wr;
                     }
                 } else if constexpr (SCHEME == HJI_ENO2) {
                     // Node i: second differences S[i+2..i+4]; the choice
