@@ -311,10 +311,13 @@ hji_status hji_value_transfer(hji_grid dst, hji_grid src, void* cuda_stream);
 typedef struct hji_engine_s* hji_engine;
 
 /* max_slots: 1..65535 concurrent requests; budget_bytes: device bytes the
- * admitted grids may hold together (0 = no limit).  Errors: HJI_E_INVALID,
- * HJI_E_NOMEM, HJI_E_CUDA. */
+ * admitted grids may hold together (0 = no limit).  alloc (may be NULL:
+ * cudaMallocAsync) supplies the engine's own device buffers (descriptors,
+ * counters, tile list); it is copied and must stay callable until
+ * hji_engine_destroy.  Errors: HJI_E_INVALID, HJI_E_NOMEM, HJI_E_CUDA. */
 hji_status hji_engine_create(int ndim, hji_precision prec, const hji_solve_opts* o, int max_slots,
-                             size_t budget_bytes, void* cuda_stream, hji_engine* out);
+                             size_t budget_bytes, void* cuda_stream, const hji_allocator* alloc,
+                             hji_engine* out);
 
 /* Queue a request.  l (grid-shaped, host or device) is copied into the grid
  * now, on the engine's stream; k likewise for HJI_INIT_USER_K.  A grid may
@@ -344,7 +347,8 @@ const char* hji_engine_last_error(hji_engine e);
 /* Tile-shape autotuner (the paper has no counterpart).  2-D grids can be
  * marched with HJI_TILE_VARIANTS tile shapes (31x32, 15x64 and 63x16 nodes,
  * rows x columns); this times `steps` steps of a
- * standard march of grid g (dynamics set, target l) with each and remembers
+ * standard march of grid g (dynamics set, target l) with each (one warm-up
+ * march, then the median of three timed ones) and remembers
  * the fastest for this precision, ndim, scheme, RK order and grid-size class
  * (log2 of the node count).  Later hji_solve, hji_batch_solve and engines
  * of that class use it (the nearest tuned size class; untuned: variant 0).

@@ -123,7 +123,8 @@ def load(build_if_missing=False):
     lib.hji_noalloc_last_error.restype = ctypes.c_char_p
     ip = ctypes.POINTER(ctypes.c_int)
     lib.hji_engine_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(hji_solve_opts),
-                                      ctypes.c_int, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+                                      ctypes.c_int, ctypes.c_size_t, vp,
+                                      ctypes.POINTER(hji_allocator), ctypes.POINTER(vp)]
     lib.hji_engine_submit.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64]
     lib.hji_engine_step.argtypes = [vp, ip, ip]
     lib.hji_engine_poll.argtypes = [vp, i64p, ctypes.POINTER(hji_solve_stats), ip, ctypes.c_int, ip]
@@ -227,8 +228,8 @@ def peak_fma(precision="f32", target_ms=20.0, stream=None):
     return tf.value, ms.value
 
 
-def hji_engine_create(ndim, prec, opts, max_slots, budget_bytes, stream, out):
-    return load().hji_engine_create(ndim, prec, opts, max_slots, budget_bytes, stream, out)
+def hji_engine_create(ndim, prec, opts, max_slots, budget_bytes, stream, alloc, out):
+    return load().hji_engine_create(ndim, prec, opts, max_slots, budget_bytes, stream, alloc, out)
 
 
 def hji_engine_submit(e, g, l, k, ptr_is_device, init, tag):
@@ -519,12 +520,18 @@ class Engine:
     slots while others march; see include/hji.h."""
 
     def __init__(self, ndim, precision="f32", max_slots=64, budget_bytes=0, stream=None,
-                 **opts):
+                 allocator="torch", **opts):
         self._h = ctypes.c_void_p()
         self.prec = HJI_F64 if precision == "f64" else HJI_F32
         o = solve_opts(**opts)
+        if isinstance(allocator, hji_allocator):
+            alloc = allocator
+        else:
+            alloc = torch_allocator() if allocator == "torch" else None
         rc = hji_engine_create(ndim, self.prec, ctypes.byref(o), max_slots, budget_bytes,
-                               Grid._stream(stream), ctypes.byref(self._h))
+                               Grid._stream(stream),
+                               ctypes.byref(alloc) if alloc is not None else None,
+                               ctypes.byref(self._h))
         if rc != HJI_OK:
             raise HJIError(rc, hji_engine_last_error(None))
         self._keep = {}

@@ -6,6 +6,7 @@
 // tile list).  Kernels skip the tiles of grids that have stopped, so the host
 // keeps one graph in flight ahead of the one it checks; it reads a single
 // device counter of still-marching grids per graph and never syncs per step.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -134,6 +135,8 @@ struct hji_grid_s {
 
 struct hji_engine_s {
     int ndim = 0;
+    bool has_alloc = false;
+    hji_allocator alloc{};            // device allocations of the engine's own buffers
     hji_precision prec = HJI_F64;
     hji_solve_opts o{};
     int chunk = 32;
@@ -1095,6 +1098,26 @@ hji_status hji_value_transfer(hji_grid dst, hji_grid src, void* cuda_stream) {
     return HJI_OK;
 }
 
+// The engine's device buffers come from its allocator (if one was given,
+// e.g. a framework's caching allocator), else from cudaMallocAsync, on the
+// engine's stream.
+static void* engine_alloc(hji_engine e, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (e->has_alloc) return e->alloc.alloc(bytes, e->s, e->alloc.ctx);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, e->s) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+static void engine_free(hji_engine e, void* p) {
+    if (!p) return;
+    if (e->has_alloc) e->alloc.free(p, e->s, e->alloc.ctx);
+    else cudaFreeAsync(p, e->s);
+}
+
 static hji_status efail(hji_engine e, hji_status st, const std::string& msg) {
     if (e) e->err = msg;
     else g_create_error = msg;
@@ -1110,7 +1133,8 @@ static size_t grid_bytes(hji_grid g, int rk) {
 const char* hji_engine_last_error(hji_engine e) { return e ? e->err.c_str() : g_create_error.c_str(); }
 
 hji_status hji_engine_create(int ndim, hji_precision prec, const hji_solve_opts* o, int max_slots,
-                             size_t budget_bytes, void* cuda_stream, hji_engine* out) {
+                             size_t budget_bytes, void* cuda_stream, const hji_allocator* alloc,
+                             hji_engine* out) {
     if (!out) return efail(nullptr, HJI_E_INVALID, "out is NULL");
     *out = nullptr;
     if (ndim < 1 || ndim > HJI_MAX_DIM) return efail(nullptr, HJI_E_INVALID, "ndim must be 1..4");
@@ -1129,8 +1153,13 @@ hji_status hji_engine_create(int ndim, hji_precision prec, const hji_solve_opts*
     e->s = (cudaStream_t)cuda_stream;
     e->slots.resize(max_slots);
     e->h_desc.resize(max_slots);
-    bool ok = cudaMalloc(&e->d_desc, sizeof(InstDesc) * max_slots) == cudaSuccess &&
-              cudaMalloc(&e->d_counts, sizeof(int) * 2) == cudaSuccess &&
+    if (alloc) {
+        e->alloc = *alloc;
+        e->has_alloc = true;
+    }
+    e->d_desc = (InstDesc*)engine_alloc(e, sizeof(InstDesc) * max_slots);
+    e->d_counts = (int*)engine_alloc(e, sizeof(int) * 2);
+    bool ok = e->d_desc && e->d_counts &&
               cudaMallocHost(&e->h_counts, sizeof(int) * 2) == cudaSuccess &&
               cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&e->ev, cudaEventDisableTiming) == cudaSuccess &&
@@ -1152,9 +1181,10 @@ hji_status hji_engine_destroy(hji_engine e) {
     if (!e) return HJI_OK;
     cudaStreamSynchronize(e->s);
     if (e->graph) cudaGraphExecDestroy(e->graph);
-    if (e->d_desc) cudaFree(e->d_desc);
-    if (e->d_counts) cudaFree(e->d_counts);
-    if (e->d_tiles) cudaFree(e->d_tiles);
+    engine_free(e, e->d_desc);
+    engine_free(e, e->d_counts);
+    engine_free(e, e->d_tiles);
+    cudaStreamSynchronize(e->s);
     if (e->h_counts) cudaFreeHost(e->h_counts);
     if (e->cap) cudaStreamDestroy(e->cap);
     if (e->ev) cudaEventDestroy(e->ev);
@@ -1280,11 +1310,10 @@ hji_status hji_engine_step(hji_engine e, int* active, int* queued) {
             if (e->slots[i].used)
                 for (long long t = 0; t < e->h_desc[i].ntiles; ++t) tiles.push_back(hji::make_tile(i, t));
         if (tiles.size() > e->tiles_cap) {
-            if (e->d_tiles) cudaFreeAsync(e->d_tiles, e->s);
+            engine_free(e, e->d_tiles);
             size_t cap = tiles.size() * 2;
-            if (cudaMallocAsync(&e->d_tiles, cap * sizeof(unsigned long long), e->s) != cudaSuccess) {
-                cudaGetLastError();
-                e->d_tiles = nullptr;
+            e->d_tiles = (unsigned long long*)engine_alloc(e, cap * sizeof(unsigned long long));
+            if (!e->d_tiles) {
                 e->tiles_cap = 0;
                 return efail(e, HJI_E_NOMEM, "tile list allocation failed");
             }
@@ -1368,13 +1397,20 @@ hji_status hji_autotune(hji_grid g, const void* l, int ptr_is_device, const hji_
         if (ms_per_step) ms_per_step[v] = -1.0;
         if (v >= nvar) continue;
         g_force_variant = v;
-        hji_solve_stats s1, s2;
+        // One warm-up solve, then the median of three timed solves (a single
+        // host-timed solve of a small grid is too noisy to rank shapes).
+        hji_solve_stats s1;
         hji_status r = hji_solve(g, l, nullptr, ptr_is_device, &t, cuda_stream, &s1);  // warm-up
-        if (r == HJI_OK || r == HJI_E_NOT_CONVERGED)
+        double rep[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < 3 && (r == HJI_OK || r == HJI_E_NOT_CONVERGED); ++k) {
+            hji_solve_stats s2;
             r = hji_solve(g, l, nullptr, ptr_is_device, &t, cuda_stream, &s2);
+            rep[k] = s2.wall_ms / (double)(s2.steps > 0 ? s2.steps : 1);
+        }
         g_force_variant = -1;
         if (r != HJI_OK && r != HJI_E_NOT_CONVERGED) return r;
-        const double ms = s2.wall_ms / (double)(s2.steps > 0 ? s2.steps : 1);
+        std::sort(rep, rep + 3);
+        const double ms = rep[1];
         if (ms_per_step) ms_per_step[v] = ms;
         if (ms < best_ms) {
             best_ms = ms;

@@ -99,3 +99,29 @@ def test_no_kernel_writes_outside_its_buffers(hji_lib, prec):
     assert not ga.live
     assert ga.checked > 50
     assert not ga.violations, ga.violations
+
+
+def test_engine_buffers_and_its_grids_stay_inside_their_bands(hji_lib):
+    """The serving engine's own buffers (descriptors, counters, tile list)
+    come from its allocator too; requests arriving while others march."""
+    import torch
+    assert torch.cuda.is_available()
+    hji = hji_lib
+    ga = GuardedAllocator(hji, torch)
+    insts = W.batch_instances(count=5, seed=8, side=(31, 90))
+    grids = []
+    for i in insts:
+        g = hji.Grid(i["grid"], "f32", allocator=ga.struct)
+        g.set_dynamics(i["dyn"])
+        grids.append(g)
+    eng = hji.Engine(2, "f32", max_slots=2, allocator=ga.struct, scheme="eno2", rk=2,
+                     tol=0.0, max_steps=20, check_every=4)
+    for t, (g, i) in enumerate(zip(grids, insts)):
+        eng.submit(g, W.instance_target(i).astype(np.float32), tag=t)
+    done = eng.drain()
+    eng.close()
+    for g in grids:
+        g.close()
+    assert sorted(t for t, _, _ in done) == list(range(len(insts)))
+    assert not ga.live and ga.checked > 10
+    assert not ga.violations, ga.violations
