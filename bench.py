@@ -932,8 +932,10 @@ def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=N
 
         for _ in range(max(1, warmup)):
             run()
-        if clocks is not None:
-            clocks.start()
+        # clocks sampled during this case's timed marches (a sampler of its own
+        # unless the caller passed one)
+        sampler = clocks if clocks is not None else ClockSampler(_env_int("LOCAL_RANK", 0))
+        sampler.start()
         ms, upd, launches = 0.0, 0, 0
         for _ in range(repeats):
             e0 = torch.cuda.Event(enable_timing=True)
@@ -945,7 +947,7 @@ def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=N
             ms += e0.elapsed_time(e1)
             upd += sum(int(np.prod(gd["n"])) * s["steps"] for gd, s in zip(gds, sts))
             launches += max(s["kernel_launches"] for s in sts)
-        clk = clocks.stop() if clocks is not None else None
+        clk = sampler.stop()
         stage = None
         if len(grids) == 1:
             # Each of the two stage kernels alone between two CUDA events
