@@ -868,16 +868,30 @@ def _served_vs_f64(hji, torch, srv, reqs, records, opts, budget_s):
 # --profile-steps 2 --workload W` of the current stage kernels (mean of the
 # two launches of each stage; summaries under profiles/).
 DRAM_BYTES_PER_LAUNCH = {
-    ("di_8192^2", "first_stage"): (545649664 + 237907200 + 547152128 + 238781952) / 2,
-    ("di_8192^2", "fused_last_stage"): (1198846208 + 506711040 + 1201185280 + 505523456) / 2,
-    ("quad4d_61^4", "first_stage"): (121092352 + 36559616 + 121172992 + 36836352) / 2,
-    ("quad4d_61^4", "fused_last_stage"): (254417408 + 94041088 + 254025728 + 94262784) / 2,
+    ("di_8192^2", "first_stage"): (540748800 + 238147840 + 541717248 + 238302464) / 2,
+    ("di_8192^2", "fused_last_stage"): (1202743040 + 506452480 + 1205676288 + 505219328) / 2,
+    ("quad4d_61^4", "first_stage"): (121117440 + 36525568 + 121155328 + 36753920) / 2,
+    ("quad4d_61^4", "fused_last_stage"): (256818944 + 93993984 + 257107200 + 94154752) / 2,
 }
+# The multi-step march kernel on 8192^2 (one launch of 20 steps, read +
+# written, from `ncu ... -k regex:march_kernel -s 2 -c 2 python bench.py
+# --workload di8192 --steps 1 --warmup 1 --march multi_step`), per RK2 step.
+DRAM_BYTES_MARCH_8192_PER_STEP = (34933350144 + 16078156032) / 20
 # The same capture of the 1001^2 WENO5 stage kernels (first touch of each
 # field per launch: ncu flushes the caches between launches, so these are
 # upper bounds of what a launch inside a solve moves).
-DRAM_BYTES_DI1001 = [(8122112 + 8122368) / 2, (12158720 + 12157952) / 2,
-                     (16206080 + 16199936) / 2]
+DRAM_BYTES_DI1001 = [(8122880 + 8122624) / 2, (12158976 + 12161536) / 2,
+                     (16200448 + 16201216) / 2]
+
+
+def march_traffic(name, multi_step):
+    """Captured DRAM bytes per RK2 step of a workload's march in the launch
+    form it ran (None where no capture of that form exists)."""
+    if multi_step:
+        return DRAM_BYTES_MARCH_8192_PER_STEP if name == "di_8192^2" else None
+    b = (DRAM_BYTES_PER_LAUNCH.get((name, "first_stage"), 0) +
+         DRAM_BYTES_PER_LAUNCH.get((name, "fused_last_stage"), 0))
+    return b or None
 
 
 def _measured_hbm():
@@ -980,10 +994,11 @@ def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=N
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                                   "frac": gbs / peak, "peak_source": src,
                                   "bytes_per_node_step": bytes_per_update,
-                                  "traffic": (DRAM_BYTES_PER_LAUNCH.get((name, "first_stage"), 0) +
-                                              DRAM_BYTES_PER_LAUNCH.get((name, "fused_last_stage"), 0))
-                                  or None,
-                                  "traffic_unit": "DRAM bytes per RK2 step (both stage launches, ncu)",
+                                  "traffic": march_traffic(name, launches / max(1, repeats) < steps),
+                                  "traffic_unit": "DRAM bytes per RK2 step of the launch form that "
+                                                  "ran (ncu)",
+                                  "launch_form": "multi_step" if launches / max(1, repeats) < steps
+                                                 else "per_stage",
                                   "method_per_stage": {"bytes_per_node_step": 24,
                                                        "achieved": gbs_stage,
                                                        "frac": gbs_stage / peak},
