@@ -10,7 +10,8 @@ Functions follow arXiv:1903.07715: the dynamics of Sec. II-A Eq. (1), the
 Hamiltonian of Eq. (6), the HJI variational inequality of Eq. (7) marched
 backwards in time with min(., l) after every step (Eq. (8)), standard or warm
 initialisation (Sec. II-B, Sec. III), and the max-change convergence test
-(Sec. IV).  Parity status of each function is listed in ``PINS`` below.
+(Sec. IV), and the discounted variant of Sec. II-C.  Parity status of each
+function is listed in ``PINS`` below.
 """
 import ctypes
 import os
@@ -33,6 +34,9 @@ PINS = {
     "step/solve": "closed-form double-integrator value (Sec. II-B cost, Eq. (3)-(4)); "
                   "1-D advection closed form; stationary case; refinement order; "
                   "Thm. 1 / Lemma 1 / Thm. 2 / Props. 1-2 / Remarks 1-2 orderings",
+    "step/solve, discounted": "closed form of the discounted one-cell shift (Courant number 1, "
+                              "periodic); contraction from two starts (Sec. II-C); "
+                              "gamma 0 or 1 equals the plain march",
 }
 
 
@@ -94,13 +98,13 @@ def _load():
         lib.oracle_one_sided.argtypes = [ctypes.c_int, _D, ctypes.c_double, _D, _D]
         lib.oracle_operator.argtypes = [_P, ctypes.c_int, _D, _D, _D]
         lib.oracle_step.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D,
-                                    _D, _D, _D, ctypes.c_int]
+                                    _D, _D, _D, ctypes.c_int, ctypes.c_double]
         lib.oracle_init.argtypes = [_P, _D, _D, _D]
         lib.oracle_solve.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int64, _D, _D,
                                      _D, ctypes.POINTER(_Stats), _D, ctypes.c_int64,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                     ctypes.c_int]
+                                     ctypes.c_int, ctypes.c_double]
         lib.oracle_control_at.argtypes = [_P, _D, _D, _D, _D]
         lib.oracle_optimal_control.argtypes = [_P, ctypes.c_int, _D, _D, _D]
         lib.oracle_gradient.argtypes = [_P, ctypes.c_int, _D, _D]
@@ -263,8 +267,9 @@ def _flags(brs, local_lf):
     return (BRS if brs else 0) | (LOCAL_LF if local_lf else 0)
 
 
-def step(P, scheme, rk, dt, alpha, l, V, brs=False, local_lf=False):
-    """One Runge-Kutta step + min(., l) (none with brs: Eq. (5) alone).
+def step(P, scheme, rk, dt, alpha, l, V, brs=False, local_lf=False, discount=0.0):
+    """One Runge-Kutta step + min(., l) (none with brs: Eq. (5) alone); with
+    0 < discount < 1, min(l, discount * step) (Sec. II-C).
     Returns (V_next, max|dV|)."""
     l, V = _f64(l), _f64(V)
     out = np.empty_like(V)
@@ -272,17 +277,19 @@ def step(P, scheme, rk, dt, alpha, l, V, brs=False, local_lf=False):
     a = _alpha_arr(alpha)
     rc = _load().oracle_step(ctypes.byref(P), SCHEMES[scheme], int(rk), float(dt), _ptr(a),
                              _ptr(l), _ptr(V), _ptr(out), ctypes.byref(delta),
-                             _flags(brs, local_lf))
+                             _flags(brs, local_lf), float(discount))
     if rc != 0:
         raise MemoryError("oracle_step")
     return out, delta.value
 
 
 def solve(P, l, k=None, scheme="eno2", rk=2, cfl=0.5, tol=1e-6, horizon=0.0, max_steps=0,
-          history=0, tol_rate=0.0, interval=0.0, interval_tol=0.0, brs=False, local_lf=False):
+          history=0, tol_rate=0.0, interval=0.0, interval_tol=0.0, brs=False, local_lf=False,
+          discount=0.0):
     """March to convergence: max|dV| of one step < tol + tol_rate dt, or (with
     interval > 0) the change of V over K = round(interval / dt) steps below
-    interval_tol (Sec. V).  Returns (V, stats dict[, history array])."""
+    interval_tol (Sec. V); every step discounted by 0 < discount < 1
+    (Sec. II-C).  Returns (V, stats dict[, history array])."""
     l = _f64(l)
     V = np.empty_like(l)
     kk = None if k is None else _f64(k)
@@ -292,7 +299,7 @@ def solve(P, l, k=None, scheme="eno2", rk=2, cfl=0.5, tol=1e-6, horizon=0.0, max
                               float(horizon), int(max_steps), _ptr(l),
                               None if kk is None else _ptr(kk), _ptr(V), ctypes.byref(st),
                               _ptr(hist), int(history), float(tol_rate), float(interval),
-                              float(interval_tol), _flags(brs, local_lf))
+                              float(interval_tol), _flags(brs, local_lf), float(discount))
     if rc < 0:
         raise ValueError("oracle_solve rejected its input")
     stats = {"steps": st.steps, "tau": st.tau, "dt": st.dt, "last_delta": st.last_delta,

@@ -472,9 +472,13 @@ int oracle_operator(const oracle_problem* P, int scheme, const double* alpha, co
  *   rk 2: V1 = E(V);  V' = V/2 + E(V1)/2                       (Heun)
  *   rk 3: V1 = E(V);  V2 = 3V/4 + E(V1)/4;  V' = V/3 + 2E(V2)/3 (Shu-Osher)
  * followed by the projection V' <- min(V', l) of Eq. (7)/(8).
+ * Discounted reachability (Sec. II-C): with 0 < gamma < 1 the projection
+ * becomes V' <- min(l, gamma V'), the discounted dynamic-programming step
+ * with gamma = exp(-lambda dt) the factor of one step (gamma 0 or 1: off).
  * Writes V' to Vout and returns max |V' - V| through *delta. */
 int oracle_step(const oracle_problem* P, int scheme, int rk, double dt, const double* alpha,
-                const double* l, const double* V, double* Vout, double* delta, int flags) {
+                const double* l, const double* V, double* Vout, double* delta, int flags,
+                double gamma) {
     int64_t total = oracle_num_cells(P);
     double* L = (double*)malloc(sizeof(double) * (size_t)total);
     double* W1 = (double*)malloc(sizeof(double) * (size_t)total);
@@ -501,8 +505,10 @@ int oracle_step(const oracle_problem* P, int scheme, int rk, double dt, const do
                 Vout[c] = V[c] / 3.0 + 2.0 * (W2[c] + dt * L[c]) / 3.0;
         }
     }
+    const int discounted = gamma > 0.0 && gamma < 1.0;
     double dmax = 0.0;
     for (int64_t c = 0; c < total; ++c) {
+        if (discounted) Vout[c] = gamma * Vout[c];
         if (!(flags & OR_BRS) && l[c] < Vout[c]) Vout[c] = l[c];
         double ch = fabs(Vout[c] - V[c]);
         if (ch > dmax) dmax = ch;
@@ -526,12 +532,14 @@ void oracle_init(const oracle_problem* P, const double* l, const double* k, doub
  * (max_steps > 0).  tol is a bound on the change per step; tol_rate bounds
  * the change per unit of time, which is how Sec. IV states its rule (a
  * change below 0.001 over a time step of 0.01: tol_rate = 0.1).
+ * gamma (0 or 1: off) discounts every step as oracle_step says.
  * If `history` is not NULL it receives max|dV| of the first hist_len steps.
  * Returns 0 converged, 1 stopped without converging, -1 bad input. */
 int oracle_solve(const oracle_problem* P, int scheme, int rk, double cfl, double tol,
                  double horizon, int64_t max_steps, const double* l, const double* k,
                  double* V, oracle_stats* st, double* history, int64_t hist_len,
-                 double tol_rate, double interval, double interval_tol, int flags) {
+                 double tol_rate, double interval, double interval_tol, int flags,
+                 double gamma) {
     double alpha[OR_MAXD], dt;
     if (oracle_alpha_dt(P, cfl, alpha, &dt) != 0) return -1;
     int64_t total = oracle_num_cells(P);
@@ -562,7 +570,7 @@ int oracle_solve(const oracle_problem* P, int scheme, int rk, double cfl, double
     int64_t steps = 0;
     int converged = 0;
     for (;;) {
-        if (oracle_step(P, scheme, rk, dt, alpha, l, V, Vn, &delta, flags) != 0) {
+        if (oracle_step(P, scheme, rk, dt, alpha, l, V, Vn, &delta, flags, gamma) != 0) {
             free(Vn);
             free(snap);
             return -1;
