@@ -512,7 +512,9 @@ def config_rows(hji, torch):
     solve each on device-resident inputs (wall time of the C-ABI call):
       c1: 101^2 double integrator, FP64 ENO2/RK2, tol 1e-6, warm start from
           the umax = 1.2 solution (control authority shrinks: Sec. V-B,
-          Table 1's control-authority rows);
+          Table 1's control-authority rows), and discounted reachability
+          from the same start (Sec. II-C; 0.999 per step, then 1 once
+          converged, as Sec. V describes its comparison);
       c2: the benchmark's 1001^2 problem (FP32 WENO5/RK3, d 0 -> 0.2), under
           the per-step rule (max|dV| < 1e-6) and Sec. IV's rate rule
           (max|dV| < 0.001 per 0.01 of time), with where the last step's
@@ -542,10 +544,23 @@ def config_rows(hji, torch):
     warm = _solve_timed(torch, g, l64, k, **o1)
     vw = torch.empty_like(l64)
     g.value(vw)
+    # Sec. V's third column: discounted reachability from the same start,
+    # 0.999 per step until converged, then 1 from the converged value
+    disc = _solve_timed(torch, g, l64, k, discount=0.999, **o1)
+    vd = torch.empty_like(l64)
+    g.value(vd)
+    ann = _solve_timed(torch, g, l64, init=hji.HJI_INIT_RESIDENT, **o1)
+    va = torch.empty_like(l64)
+    g.value(va)
     g.close()
     out["c1_di101_f64_umax_1.2_to_1.0"] = {
         "standard": std, "warm": warm, "step_ratio": std["steps"] / max(1, warm["steps"]),
-        "time_ratio": std["ms"] / warm["ms"], "warm_vs_standard": _errs(torch, vw, vs, 1.0)}
+        "time_ratio": std["ms"] / warm["ms"], "warm_vs_standard": _errs(torch, vw, vs, 1.0),
+        "discounted_0.999": disc, "then_annealed_to_1": ann,
+        "discounted_total_steps": disc["steps"] + ann["steps"],
+        "discounted_vs_warm_steps": (disc["steps"] + ann["steps"]) / max(1, warm["steps"]),
+        "discounted_vs_standard": _errs(torch, vd, vs, 1.0),
+        "annealed_vs_standard": _errs(torch, va, vs, 1.0)}
     # ---- c2
     out["c2_di1001_f32_weno5"] = c2_analysis(hji, torch)
     # ---- c3

@@ -173,6 +173,16 @@ typedef struct {
                          alpha_a(x) = max_{u,d} |f_a(x,u,d)| (dt stays the
                          grid-wide CFL step).  Local dissipation marches with
                          one launch per stage and the default tile shape. */
+    double discount;  /* 0 (or 1): off.  gamma in (0, 1): discounted
+                         reachability (Sec. II-C): each step ends with
+                         V <- min(l, gamma * V~), V~ the Runge-Kutta step's
+                         result, instead of min(l, V~); gamma = exp(-lambda dt)
+                         is the factor of one CFL step.  The map is then a
+                         contraction, so any start converges, to a value with
+                         the same sign as the undiscounted one.  Sec. V's
+                         schedule (0.999, then 1 once converged) is two
+                         calls: a discounted solve, then an undiscounted one
+                         from the resident value.  Not with brs. */
 } hji_solve_opts;
 
 /* hji_solve_opts.march.  PER_STAGE: one kernel launch per Runge-Kutta

@@ -65,7 +65,8 @@ class hji_solve_opts(ctypes.Structure):
                 ("init", ctypes.c_int), ("tile_variant", ctypes.c_int),
                 ("tol_rate", ctypes.c_double), ("march", ctypes.c_int),
                 ("interval", ctypes.c_double), ("interval_tol", ctypes.c_double),
-                ("brs", ctypes.c_int), ("local_lf", ctypes.c_int)]
+                ("brs", ctypes.c_int), ("local_lf", ctypes.c_int),
+                ("discount", ctypes.c_double)]
 
 
 class hji_solve_stats(ctypes.Structure):
@@ -342,11 +343,12 @@ MARCH = {"auto": 0, "per_stage": 1, "multi_step": 2}
 
 def solve_opts(scheme="eno2", rk=2, cfl=0.5, tol=1e-6, horizon=0.0, max_steps=0,
                check_every=32, init=HJI_INIT_STANDARD, tile_variant=0, tol_rate=0.0,
-               march="auto", interval=0.0, interval_tol=0.0, brs=False, local_lf=False):
+               march="auto", interval=0.0, interval_tol=0.0, brs=False, local_lf=False,
+               discount=0.0):
     return hji_solve_opts(SCHEMES[scheme] if isinstance(scheme, str) else scheme, rk, cfl, tol,
                           horizon, check_every, max_steps, init, tile_variant, tol_rate,
                           MARCH[march] if isinstance(march, str) else march, interval,
-                          interval_tol, int(brs), int(local_lf))
+                          interval_tol, int(brs), int(local_lf), float(discount))
 
 
 class Grid:

@@ -396,6 +396,10 @@ hji_status validate_opts(hji_grid g, const hji_solve_opts* o) {
         return fail(g, HJI_E_INVALID, "interval and interval_tol must be finite and >= 0");
     if ((o->brs != 0 && o->brs != 1) || (o->local_lf != 0 && o->local_lf != 1))
         return fail(g, HJI_E_INVALID, "brs and local_lf must be 0 or 1");
+    if (!(o->discount >= 0.0 && o->discount <= 1.0))
+        return fail(g, HJI_E_INVALID, "discount must be in [0, 1] (0 and 1: off)");
+    if (o->brs && o->discount > 0.0 && o->discount < 1.0)
+        return fail(g, HJI_E_INVALID, "discount applies to the projected march, not to brs");
     return HJI_OK;
 }
 
@@ -457,6 +461,7 @@ hji_status make_desc(hji_grid g, const hji_solve_opts* o, int* active, int varia
     D.snap = o->interval > 0.0 ? g->snap : nullptr;
     D.brs = o->brs;
     D.local_lf = o->local_lf;
+    D.discount = o->discount;
     D.horizon = o->horizon;
     D.max_steps = o->max_steps > 0 ? o->max_steps : 1000000;
     D.V[0] = g->V[0];

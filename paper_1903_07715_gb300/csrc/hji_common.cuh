@@ -113,6 +113,7 @@ struct InstDesc {
     double interval, interval_tol;  // Sec. V's interval test (interval 0: off)
     int brs;                  // 1: no projection onto V <= l (Eq. (5) alone)
     int local_lf;             // 1: node-wise Lax-Friedrichs coefficients
+    double discount;          // gamma of discounted reachability (Sec. II-C); 0 or 1: off
     void* snap;               // its snapshot of V (the high word for FP32), or null
     long long max_steps;
     void* V[2];               // ping-pong value buffers: V[cur] = V^n

@@ -176,6 +176,10 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
     if (o->local_lf != 0)
         return nfail(HJI_E_INVALID, "local Lax-Friedrichs is not available without allocation");
     if (o->brs != 0 && o->brs != 1) return nfail(HJI_E_INVALID, "brs must be 0 or 1");
+    if (!(o->discount >= 0.0 && o->discount <= 1.0))
+        return nfail(HJI_E_INVALID, "discount must be in [0, 1] (0 and 1: off)");
+    if (o->brs && o->discount > 0.0 && o->discount < 1.0)
+        return nfail(HJI_E_INVALID, "discount applies to the projected march, not to brs");
     if (o->init == HJI_INIT_USER_K && !k) return nfail(HJI_E_INVALID, "HJI_INIT_USER_K needs k");
     if (o->init != HJI_INIT_STANDARD && o->init != HJI_INIT_USER_K && o->init != HJI_INIT_RESIDENT)
         return nfail(HJI_E_INVALID, "unknown init mode");
@@ -309,6 +313,7 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
     D.tol = o->tol;
     D.tol_rate = o->tol_rate;
     D.brs = o->brs;
+    D.discount = o->discount;
     D.horizon = o->horizon;
     D.max_steps = o->max_steps > 0 ? o->max_steps : 1000000;
     D.V[0] = base + o_v0;

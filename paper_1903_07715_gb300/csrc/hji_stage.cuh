@@ -352,6 +352,11 @@ struct TileCtx {
     T arad[MAXD];              // per row: sum_j urad_j |G_aj| + sum_k drad_k |E_ak|
     int term_row[MAXT], term_axis[MAXT];
     int project;               // 1: V <- min(V, l) after the step (Eq. (7)); 0: Eq. (5) alone
+    // Discounted reachability (Sec. II-C): the step's result is scaled by
+    // gamma before the projection.  FP64 keeps gamma; the FP32 compensated
+    // form keeps 1 - gamma and subtracts (1 - gamma) V~ from the increment.
+    int discounted;
+    T disc;
     T dt;
     const T* win;   // stencil input (FP64: the stage state; FP32: V^n hi word)
     const T* din;   // FP32: stage increment added to win (null for stage 1)
@@ -455,6 +460,8 @@ __device__ __noinline__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict_
         C.m = D.dyn.m;
         C.q = D.dyn.q;
         C.project = D.brs ? 0 : 1;
+        C.discounted = (D.discount > 0.0 && D.discount < 1.0) ? 1 : 0;
+        C.disc = sizeof(T) == 4 ? T(1.0 - D.discount) : T(D.discount);
         C.nterms = D.dyn.nterms;
         C.dt = K.dt;
         C.tiles_x = static_cast<int>(D.tiles_x);
@@ -1360,6 +1367,13 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                         lt = ld4(reinterpret_cast<const T*>(sb + L::LT(buf)) + ry * TX + 4 * grp);
                     else
                         lt = ldg4(C.l + gidx);  // (its pad columns are never used)
+                    if (C.discounted) {
+                        // gamma V~ = V~ - (1 - gamma) V~ with V~ = hi + lo +
+                        // inc; the low word's share of (1 - gamma) V~ is below
+                        // the pair's rounding and is left out.
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) inc[i] = fma(-C.disc, wc[i] + inc[i], inc[i]);
+                    }
                     T nh[4], nl[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
@@ -1414,6 +1428,10 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                 if constexpr (LAST) {
                     const Q4<T> lt =
                         ld4(reinterpret_cast<const T*>(sb + L::LT(buf)) + ry * TX + 4 * grp);
+                    if (C.discounted) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) out[i] *= C.disc;
+                    }
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         if (C.project) out[i] = fmin(out[i], lt.v[i]);
