@@ -738,7 +738,7 @@ def north_star_batch(hji, torch, interval_tol, budget_s=40.0):
     upd_batch = [W.num_cells(i["grid"]) * s["steps"] for i, s in zip(insts, sts)]
     # per-instance FP64 standard solves
     t0 = time.perf_counter()
-    done, ms64, worst_abs, worst_h, upd64 = 0, 0.0, 0.0, 0.0, 0
+    done, ms64, worst_abs, worst_h, upd64, conv64, both = 0, 0.0, 0.0, 0.0, 0, 0, 0
     for i, inst in enumerate(insts):
         if time.perf_counter() - t0 > budget_s:
             break
@@ -749,6 +749,8 @@ def north_star_batch(hji, torch, interval_tol, budget_s=40.0):
         v = torch.empty_like(l64)
         g.value(v)
         g.close()
+        conv64 += int(st["converged"])
+        both += int(st["converged"] and sts[i]["converged"])
         ms64 += ms
         upd64 += W.num_cells(inst["grid"]) * st["steps"]
         scale = float(l64.abs().max().item())
@@ -757,10 +759,13 @@ def north_star_batch(hji, torch, interval_tol, budget_s=40.0):
         worst_h = max(worst_h, e["brt_hausdorff_cells"])
         done += 1
     share = sum(upd_batch[:done]) / max(1, sum(upd_batch))
-    return {"instances": len(insts), "batched_f32_warm": {"ms": ms_batch, "all_converged": rc == 0,
-                                                         "cell_updates": sum(upd_batch)},
-            "per_instance_f64_standard": {"instances_solved": done, "ms": ms64,
-                                          "cell_updates": upd64},
+    return {"instances": len(insts), "batched_f32_warm": {
+                "ms": ms_batch, "all_converged": rc == 0,
+                "converged": sum(int(s["converged"]) for s in sts),
+                "cell_updates": sum(upd_batch)},
+            "per_instance_f64_standard": {"instances_solved": done, "converged": conv64,
+                                          "ms": ms64, "cell_updates": upd64},
+            "compared_instances_converged_in_both": both,
             "batched_ms_for_those_instances": ms_batch * share,
             "speedup": ms64 / max(1e-9, ms_batch * share),
             "worst_max_abs_over_max_l": worst_abs, "worst_brt_hausdorff_cells": worst_h,

@@ -60,9 +60,13 @@ typedef enum {
     HJI_E_NOMEM = 2,         /* device allocation failed                               */
     HJI_E_CUDA = 3,          /* a CUDA runtime call failed (see hji_last_error)        */
     HJI_E_NOT_CONVERGED = 4, /* horizon or step cap reached first; value still valid   */
-    HJI_E_TIMEOUT = 5,       /* reserved: a bounded device wait gave up                */
+    HJI_E_TIMEOUT = 5,       /* a bounded device wait gave up                          */
     HJI_E_STATE = 6,         /* call out of order (no dynamics set, no value yet, ...) */
-    HJI_E_NONFINITE = 7      /* the march produced NaN/Inf (e.g. cfl too large)         */
+    HJI_E_NONFINITE = 7,     /* the march produced NaN/Inf (e.g. cfl too large)         */
+    HJI_E_CHECK = 8          /* bounds-checked debug build only: an index check of the
+                                tile/halo code failed (hji_last_error names the site,
+                                the index and the extent); the access was redirected
+                                to element 0, so the value is not meaningful          */
 } hji_status;
 
 typedef enum { HJI_F64 = 0, HJI_F32 = 1 } hji_precision;
@@ -395,6 +399,25 @@ hji_status hji_stage_times(hji_grid g, const void* l, int ptr_is_device, const h
  * for a limit out of range, HJI_E_NOMEM / HJI_E_CUDA on runtime failures.
  * Synchronous on cuda_stream; the message is in hji_last_error(NULL). */
 hji_status hji_selftest_bounded_wait(int64_t limit_ns, void* cuda_stream);
+
+/* Which build this library is, and a self-test of its index-check recorder
+ * (the paper has no counterpart).  The library also comes as a
+ * bounds-checked debug build (_hji_checked.so, the same sources compiled
+ * with HJI_CHECKED): there every index the stage kernels' tile and halo code
+ * forms is tested against its array's extent before the access; a failed
+ * check is recorded for the instance, the access goes to element 0 instead,
+ * and the solve returns HJI_E_CHECK with the first failure in
+ * hji_last_error.  *checked (may be NULL) is 1 in that build, 0 in the
+ * product build.  The self-test runs the recorder on fixed indices that are
+ * compared, never used as addresses (one inside a 10-element extent, a
+ * 4-wide range past its end, one before its start, a failed condition) and
+ * returns how many failures it recorded (*count: 3 in the checked build, 0
+ * in the product build, whose checks compile to nothing) and the first one
+ * (*site, *index, *extent; may be NULL).  Synchronous on cuda_stream.
+ * Errors: HJI_E_NOMEM, HJI_E_CUDA (message in hji_last_error(NULL)), and
+ * HJI_E_STATE if the recorder returned other indices than it should. */
+hji_status hji_selftest_index_check(void* cuda_stream, int* checked, int* count, int* site,
+                                    int64_t* index, int64_t* extent);
 
 /* The instantaneous optimal control of Sec. II-B, Eq. (9),
  *     u*(x) = argmax_u min_d <grad V(x), f(x,u,d)>,

@@ -23,7 +23,7 @@ HJI_MAX_DIM, HJI_MAX_INPUTS, HJI_MAX_TERMS = 4, 4, 8
 HJI_TILE_VARIANTS = 3
 
 HJI_OK, HJI_E_INVALID, HJI_E_NOMEM, HJI_E_CUDA = 0, 1, 2, 3
-HJI_E_NOT_CONVERGED, HJI_E_TIMEOUT, HJI_E_STATE, HJI_E_NONFINITE = 4, 5, 6, 7
+HJI_E_NOT_CONVERGED, HJI_E_TIMEOUT, HJI_E_STATE, HJI_E_NONFINITE, HJI_E_CHECK = 4, 5, 6, 7, 8
 HJI_F64, HJI_F32 = 0, 1
 HJI_ENO1, HJI_ENO2, HJI_WENO5 = 1, 2, 5
 HJI_INIT_STANDARD, HJI_INIT_USER_K, HJI_INIT_RESIDENT = 0, 1, 2
@@ -36,7 +36,7 @@ EXPORTS = ["hji_grid_create", "hji_grid_destroy", "hji_dynamics_set", "hji_solve
            "hji_engine_create", "hji_engine_submit", "hji_engine_step", "hji_engine_poll",
            "hji_engine_destroy", "hji_engine_last_error", "hji_autotune",
            "hji_stage_times", "hji_selftest_bounded_wait", "hji_peak_fma",
-           "hji_peak_last_error", "hji_optimal_control"]
+           "hji_peak_last_error", "hji_optimal_control", "hji_selftest_index_check"]
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -80,18 +80,21 @@ _lib = None
 
 
 def library_path():
-    return _build.LIB
+    """_hji.so, or the bounds-checked debug build _hji_checked.so when the
+    environment variable HJI_CHECKED_BUILD is "1"."""
+    return _build.CHECKED_LIB if os.environ.get("HJI_CHECKED_BUILD") == "1" else _build.LIB
 
 
 def load(build_if_missing=False):
-    """Load _hji.so.  Raises if it is missing (no fallback path exists)."""
+    """Load the library (library_path()).  Raises if it is missing (no
+    fallback path exists)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = library_path()
     if not os.path.exists(path):
         if build_if_missing:
-            _build.build()
+            _build.build(checked=path == _build.CHECKED_LIB)
         else:
             raise RuntimeError("CUDA library %s is missing: run "
                                "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
@@ -136,6 +139,7 @@ def load(build_if_missing=False):
     lib.hji_engine_last_error.argtypes = [vp]
     lib.hji_engine_last_error.restype = ctypes.c_char_p
     lib.hji_selftest_bounded_wait.argtypes = [ctypes.c_int64, vp]
+    lib.hji_selftest_index_check.argtypes = [vp, ip, ip, ip, i64p, i64p]
     lib.hji_stage_times.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(hji_solve_opts),
                                     ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double)]
     lib.hji_peak_fma.argtypes = [ctypes.c_int, ctypes.c_double, vp, dp, dp]
@@ -186,6 +190,10 @@ def hji_grid_info(g, ndim, n, num_nodes):
 
 def hji_selftest_bounded_wait(limit_ns, stream):
     return load().hji_selftest_bounded_wait(limit_ns, stream)
+
+
+def hji_selftest_index_check(stream, checked, count, site, index, extent):
+    return load().hji_selftest_index_check(stream, checked, count, site, index, extent)
 
 
 def hji_solve_noalloc(ndim, n, lo, hi, periodic, prec, dyn, l, k, v_out, opts, stream, stats):

@@ -875,7 +875,9 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
         g->cur = S.cur;
         g->has_value = true;
         hji_status si = HJI_OK;
-        if (S.status == 1) {
+        if (S.check_count) {
+            si = fail(g, HJI_E_CHECK, check_message(S));
+        } else if (S.status == 1) {
             si = fail(g, HJI_E_NONFINITE, "the march produced NaN or Inf");
         } else if (S.status == 4) {
             si = fail(g, HJI_E_TIMEOUT, "a bounded device wait gave up (a tile copy never arrived)");
@@ -916,6 +918,7 @@ const char* hji_status_string(hji_status s) {
         case HJI_E_TIMEOUT: return "timeout";
         case HJI_E_STATE: return "call out of order";
         case HJI_E_NONFINITE: return "non-finite value";
+        case HJI_E_CHECK: return "index check failed";
     }
     return "unknown status";
 }
@@ -1252,7 +1255,8 @@ static hji_status engine_retire(hji_engine e) {
         d.st.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - sl.t0).count();
         for (int a = 0; a < HJI_MAX_DIM; ++a) d.st.alpha[a] = a < sl.g->ndim ? S.alpha[a] : 0.0;
         d.st.converged = S.converged;
-        if (S.nonfinite) d.status = HJI_E_INVALID;
+        if (S.check_count) d.status = HJI_E_CHECK;
+        else if (S.nonfinite) d.status = HJI_E_INVALID;
         else if (S.status == 2) d.status = HJI_E_INVALID;
         else if (S.status == 1) d.status = HJI_E_NONFINITE;
         else if (S.status == 4) d.status = HJI_E_TIMEOUT;
@@ -1473,6 +1477,42 @@ hji_status hji_selftest_bounded_wait(int64_t limit_ns, void* cuda_stream) {
     if (h == 4) return fail(nullptr, HJI_E_TIMEOUT, "the bounded wait gave up, as it should");
     if (h == 0) return fail(nullptr, HJI_E_STATE, "a barrier that nothing completes completed");
     return fail(nullptr, HJI_E_CUDA, "self-test kernel wrote no result");
+}
+
+hji_status hji_selftest_index_check(void* cuda_stream, int* checked, int* count, int* site,
+                                    int64_t* index, int64_t* extent) {
+#ifdef HJI_CHECKED
+    const int is_checked = 1;
+#else
+    const int is_checked = 0;
+#endif
+    if (checked) *checked = is_checked;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    void* d = nullptr;
+    const size_t bytes = sizeof(InstState) + 4 * sizeof(long long);
+    if (cudaMallocAsync(&d, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, HJI_E_NOMEM, "device allocation failed");
+    }
+    InstState* d_st = static_cast<InstState*>(d);
+    long long* d_out = reinterpret_cast<long long*>(static_cast<char*>(d) + sizeof(InstState));
+    InstState h;
+    long long out[4] = {-1, -1, -1, -1};
+    cudaError_t e = cudaMemsetAsync(d, 0, bytes, s);
+    if (e == cudaSuccess) e = hji::launch_check_selftest(d_st, d_out, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_st, sizeof(InstState), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, sizeof(out), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(nullptr, HJI_E_CUDA, std::string("self-test: ") + cudaGetErrorString(e));
+    if (count) *count = h.check_count;
+    if (site) *site = h.check_site;
+    if (index) *index = h.check_index;
+    if (extent) *extent = h.check_limit;
+    const bool want = is_checked ? (out[0] == 7 && out[1] == 0 && out[2] == 0 && out[3] == 0)
+                                 : (out[0] == 0 && out[1] == 0 && out[2] == 0 && out[3] == 0);
+    if (!want) return fail(nullptr, HJI_E_STATE, "the index-check recorder returned wrong indices");
+    return HJI_OK;
 }
 
 hji_status hji_optimal_control(hji_grid g, hji_scheme scheme, void* u_out, void* d_out,

@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -79,7 +80,66 @@ struct InstState {
     long long interval_K;
     unsigned long long interval_bits;  // max|V - snapshot| of the step in flight (bits of a double)
     double last_interval_change;       // of the last finished interval
+    // Bounds-checked debug build only (HJI_CHECKED): index checks that
+    // failed, and the first one's site (CheckSite), index and extent.
+    int check_count;
+    int check_site;
+    long long check_index;
+    long long check_limit;
 };
+
+// Sites of the debug build's index checks (the message of a failed check
+// names them).
+enum CheckSite {
+    CK_TILE = 1,     // tile index within the instance's tile count
+    CK_TILE_GEO,     // tile origin and slow-axis indices inside the grid
+    CK_TMA_X,        // tensor-copy x coordinate on a 16-byte boundary
+    CK_TMA_DST,      // tensor-copy destination on a 128-byte boundary
+    CK_GHOST_WRITE,  // ghost node slot inside the staged window
+    CK_GHOST_READ,   // edge nodes an extrapolated ghost reads, inside the window
+    CK_GHOST_LINE,   // periodic ghost line inside the field
+    CK_DIFF_READ,    // window rows the y-differences read
+    CK_DIFF_WRITE,   // slot of a y-difference
+    CK_YSET_READ,    // y-differences a WENO5 set reads
+    CK_YSET_WRITE,   // slot of a set's y-derivatives
+    CK_PLANE,        // slow-axis stencil plane inside the field
+    CK_XWINDOW,      // window row segment of a run's x-stencil
+    CK_DIFF_Y,       // y-differences an ENO y-stencil reads
+    CK_TABLE,        // per-term table entry
+    CK_NODE_SMEM,    // staged l / V^n at the run's nodes
+    CK_NODE_GLOBAL,  // the run's nodes in the fields it reads and writes
+    CK_NUM_SITES
+};
+
+// The text of a failed check (host side).
+std::string check_message(const InstState& S);
+
+#ifdef HJI_CHECKED
+// Record a failed index check: the first one's site, index and extent, and
+// how many failed.
+static __device__ __noinline__ void check_miss(InstState* st, int site, long long i, long long n) {
+    if (atomicAdd(&st->check_count, 1) == 0) {
+        st->check_site = site;
+        st->check_index = i;
+        st->check_limit = n;
+    }
+}
+// [i, i + w) inside [0, n): i, else 0 after recording the miss.
+__device__ __forceinline__ long long checked_index(InstState* st, int site, long long i, long long w,
+                                                   long long n) {
+    if (i < 0 || i + w > n) {
+        check_miss(st, site, i, n);
+        return 0;
+    }
+    return i;
+}
+// A condition that must hold; false after recording the miss.
+__device__ __forceinline__ bool checked_cond(InstState* st, int site, bool ok, long long v,
+                                             long long n) {
+    if (!ok) check_miss(st, site, v, n);
+    return ok;
+}
+#endif
 
 // Tensor maps of one instance (TMA descriptors, encoded on the host):
 // "window" maps copy a tile with its ghost halo (TX + 8 columns starting 4
@@ -264,6 +324,10 @@ cudaError_t launch_init(const InstDesc* d_insts, const InstDesc* h_insts, int co
 bool encode_maps(InstDesc& D, bool f32, int scheme, int variant, const char** why);
 // Bounded-wait self-test (hji_setup.cu): *d_result = 4 when the wait gave up.
 cudaError_t launch_wait_selftest(unsigned long long limit_ns, int* d_result, cudaStream_t s);
+// The debug build's check recorder on fixed indices (none of them is used to
+// address memory): out[0..3] and the record in *st.  A no-op in the product
+// build.
+cudaError_t launch_check_selftest(InstState* st, long long* out, cudaStream_t s);
 cudaError_t launch_convert(long long n, const void* src_hi, const void* src_lo, bool src_f32,
                            void* dst_hi, void* dst_lo, bool dst_f32, cudaStream_t s);
 

@@ -434,6 +434,7 @@ extern "C" hji_status hji_solve_noalloc(int ndim, const int64_t* n, const double
         stats->converged = hs.converged;
         stats->kernel_launches = launches;
     }
+    if (hs.check_count) return nfail(HJI_E_CHECK, hji::check_message(hs).c_str());
     if (hs.status == 1) return nfail(HJI_E_NONFINITE, "the march produced NaN or Inf");
     if (hs.status == 4) return nfail(HJI_E_TIMEOUT, "a bounded device wait gave up");
     if (!hs.converged) return nfail(HJI_E_NOT_CONVERGED, "stopped by the horizon or the step cap");

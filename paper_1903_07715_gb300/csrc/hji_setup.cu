@@ -348,6 +348,55 @@ cudaError_t launch_wait_selftest(unsigned long long limit_ns, int* d_result, cud
     return cudaGetLastError();
 }
 
+// The debug build's recorder on a 10-element extent: one index inside, a
+// 4-wide range past the end, one index before the start, and a failed
+// condition.  The indices are only compared, never used as addresses.
+__global__ void check_selftest_kernel(InstState* st, long long* out) {
+#ifdef HJI_CHECKED
+    out[0] = checked_index(st, CK_TILE, 7, 1, 10);
+    out[1] = checked_index(st, CK_PLANE, 8, 4, 10);
+    out[2] = checked_index(st, CK_XWINDOW, -1, 1, 10);
+    out[3] = checked_cond(st, CK_TMA_X, false, 3, 4) ? 1 : 0;
+#else
+    (void)st;
+    (void)out;
+#endif
+}
+
+cudaError_t launch_check_selftest(InstState* st, long long* out, cudaStream_t s) {
+    check_selftest_kernel<<<1, 1, 0, s>>>(st, out);
+    return cudaGetLastError();
+}
+
+static const char* const kCheckSiteNames[CK_NUM_SITES] = {
+    "",
+    "tile index",
+    "tile origin",
+    "tensor-copy x coordinate (16-byte boundary)",
+    "tensor-copy destination (128-byte boundary)",
+    "ghost node slot",
+    "extrapolation source in the window",
+    "periodic ghost line",
+    "y-difference source rows",
+    "y-difference slot",
+    "WENO5 set source",
+    "WENO5 set result slot",
+    "slow-axis stencil plane",
+    "x-stencil window segment",
+    "ENO y-stencil differences",
+    "term table entry",
+    "staged node values",
+    "node fields",
+};
+
+std::string check_message(const InstState& S) {
+    const int site = S.check_site;
+    const char* name = site > 0 && site < CK_NUM_SITES ? kCheckSiteNames[site] : "unknown site";
+    return "index check failed " + std::to_string(S.check_count) + " time(s); first: " + name +
+           " (site " + std::to_string(site) + "), index " + std::to_string(S.check_index) +
+           " against extent " + std::to_string(S.check_limit);
+}
+
 static int grid_for(long long work, int cap);
 
 cudaError_t launch_convert(long long n, const void* src_hi, const void* src_lo, bool src_f32,

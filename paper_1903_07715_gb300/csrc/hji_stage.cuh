@@ -335,6 +335,28 @@ __device__ __forceinline__ void interval_check(T* snap, const T* v, int nvalid, 
     }
 }
 
+// ---- The bounds-checked debug build ----
+// Compiled with -DHJI_CHECKED (a second library from the same sources),
+// every index the tile and halo code forms is tested against the extent of
+// the array it addresses before the access.  A miss is recorded in the
+// instance's state (the first site, index and extent, and a count; the
+// solve then fails with HJI_E_CHECK) and the access goes to element 0
+// instead, so the march never touches memory outside its arrays.  In the
+// product build the checks compile to nothing.
+#ifdef HJI_CHECKED
+#define HJI_CHK(site, i, w, n) \
+    static_cast<decltype(i)>(::hji::checked_index(C.state, (site), (i), (w), (n)))
+#define HJI_CHK_COND(site, ok, v, n) ::hji::checked_cond(C.state, (site), (ok), (v), (n))
+// An offset `off` from element `base` of a field: the offset, or -base (the
+// field's element 0) after a miss.
+#define HJI_CHK_REL(site, base, off, w, n) \
+    static_cast<decltype(off)>(::hji::checked_index(C.state, (site), (base) + (off), (w), (n)) - (base))
+#else
+#define HJI_CHK(site, i, w, n) (i)
+#define HJI_CHK_COND(site, ok, v, n) true
+#define HJI_CHK_REL(site, base, off, w, n) (off)
+#endif
+
 // Shared-memory copy of what a tile needs from its instance, in precision T.
 template <typename T>
 struct TileCtx {
@@ -379,6 +401,9 @@ struct TileCtx {
     T* snap;
     int boundary;
     double interval_tol;
+    // Extents the debug build's index checks test against: elements of one
+    // field, and of the term table.
+    long long nalloc, table_elems;
     // TMA descriptors of the fields this stage copies.
     const CUtensorMap* tm_win;   // stencil input (high word)
     const CUtensorMap* tm_lo;    // FP32 low word of V^n
@@ -406,7 +431,9 @@ __device__ __forceinline__ T row_drift(const TileCtx<T>& C, const int* idx, int 
         int ia = idx[0];
 #pragma unroll
         for (int r = 1; r < NDIM; ++r) ia = ax == r ? idx[r] : ia;
-        f += __ldg(C.table + tt * C.table_stride + min(ia, C.n[ax] - 1));
+        f += __ldg(C.table + tt * C.table_stride +
+                   HJI_CHK_REL(CK_TABLE, (long long)tt * C.table_stride, min(ia, C.n[ax] - 1), 1,
+                               C.table_elems));
     }
     return f;
 }
@@ -494,6 +521,8 @@ __device__ __noinline__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict_
         C.l = static_cast<const T*>(D.l);
         C.table = static_cast<const T*>(D.table);
         C.table_stride = D.table_stride;
+        C.nalloc = D.nalloc;
+        C.table_elems = (long long)D.dyn.nterms * D.table_stride;
         C.state = st;
         C.active = D.active;
         C.history = D.history;
@@ -689,6 +718,8 @@ struct StageSmem {
     static constexpr int PMY = DYS + DYSB;
     static constexpr int PPY = PMY + PYB;
     static constexpr int BYTES = PPY + PYB + 128;  // + alignment slack (smem_layout_base)
+    static_assert(WINB % 128 == 0 && NODEB % 128 == 0 && DYSB % 128 == 0 && PYB % 128 == 0,
+                  "tensor-copy destinations sit on 128-byte boundaries");
     static __host__ __device__ constexpr int H(int b) { return b * BUFB; }
     static __host__ __device__ constexpr int LO(int b) { return b * BUFB + WINB; }
     static __host__ __device__ constexpr int DD(int b) { return b * BUFB + 2 * WINB; }
@@ -832,6 +863,10 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
     // Thread 0: start the tensor copies of a tile into buffer b.
     auto issue = [&](const TileGeo& tg, int b) {
         const unsigned bar = bar0 + 8u * b;
+        const unsigned base = smem_addr(sb);
+        // (A destination off its 128-byte boundary issues no copy: the
+        // bounded wait then gives up and the CTA leaves.)
+        if (!HJI_CHK_COND(CK_TMA_DST, (base & 127u) == 0u, base, 128)) return;
         mbar_expect_tx(bar, tile_bytes);
         int cw[4] = {tg.x0 - 4, tg.y0 - GY, 0, 0};
         int cn[4] = {tg.x0, tg.y0, 0, 0};
@@ -839,7 +874,17 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
             cw[2] = cn[2] = tg.sidx[NDIM - 3];
             if constexpr (NDIM == 4) cw[3] = cn[3] = tg.sidx[0];
         }
-        const unsigned base = smem_addr(sb);
+#ifdef HJI_CHECKED
+        {
+            constexpr int k = 16 / (int)sizeof(T);  // elements per 16 bytes
+            bool in = tg.x0 >= 0 && tg.x0 < C.n[AX] && (NDIM < 2 || (tg.y0 >= 0 && tg.y0 < C.n[AY]));
+            for (int ax = 0; ax < NDIM - 2; ++ax) in = in && tg.sidx[ax] >= 0 && tg.sidx[ax] < C.n[ax];
+            HJI_CHK_COND(CK_TILE_GEO, in, tg.x0, C.n[AX]);
+            // an unaligned x would be an illegal copy: round it down
+            if (!HJI_CHK_COND(CK_TMA_X, cw[0] % k == 0, cw[0], k)) cw[0] -= ((cw[0] % k) + k) % k;
+            if (!HJI_CHK_COND(CK_TMA_X, cn[0] % k == 0, cn[0], k)) cn[0] -= ((cn[0] % k) + k) % k;
+        }
+#endif
         tma_load<NDIM>(base + L::H(b), C.tm_win, cw, bar);
         if constexpr (INCR) {
             tma_load<NDIM>(base + L::LO(b), C.tm_lo, cw, bar);
@@ -893,7 +938,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
         // finished before the barrier below of the previous tile.  Thread 0
         // places the tiles (one integer division each) for everyone.
         if (threadIdx.x == 0 && !issued) {
-            geo_s[buf] = tile_geo<T, NDIM, TY, TX>(C, local);
+            geo_s[buf] = tile_geo<T, NDIM, TY, TX>(C, HJI_CHK(CK_TILE, local, 1, C.ntiles));
             issue(geo_s[buf], buf);
         }
         const bool ok = mbar_wait_bounded(bar0 + 8u * buf, (phase >> buf) & 1u);
@@ -912,7 +957,8 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
         const TileGeo& tg = geo_s[buf];  // read from shared memory where used
         // Prefetch the next tile of the walk while this one is computed.
         if (threadIdx.x == 0 && pref) {
-            geo_s[buf ^ 1] = tile_geo<T, NDIM, TY, TX>(C, static_cast<int>(a.tiles[tn] & 0xFFFFFFFFFFFFull));
+            geo_s[buf ^ 1] = tile_geo<T, NDIM, TY, TX>(
+                C, HJI_CHK(CK_TILE, static_cast<int>(a.tiles[tn] & 0xFFFFFFFFFFFFull), 1, C.ntiles));
             issue(geo_s[buf ^ 1], buf ^ 1);
         }
 
@@ -930,12 +976,13 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
         // adds the stage increment to the low word itself.  Ghost slots lie
         // outside the tensor, so their increments read as zero.
         auto pair_at = [&](int r, int c) {
+            const int i = HJI_CHK(CK_GHOST_READ, r * SWX + c, 1, WIN);
             Pair<T> p;
-            p.h = wh[r * SWX + c];
+            p.h = wh[i];
             p.l = T(0);
             if constexpr (INCR) {
-                p.l = wl[r * SWX + c];
-                if (has_d) p.l += wd[r * SWX + c];
+                p.l = wl[i];
+                if (has_d) p.l += wd[i];
             }
             return p;
         };
@@ -961,7 +1008,8 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                     c = gx - x0 + 4;
                     if ((NDIM >= 2 && gy >= ny) || c < 4 - G || c >= 4 + TX + G) continue;
                     if (C.periodic[AX]) {
-                        const long long r0 = (long long)gy * sy;
+                        const long long r0 =
+                            HJI_CHK_REL(CK_GHOST_LINE, tg.base, (long long)gy * sy, nx, C.nalloc);
                         v = line_pair<T, COH>(hp + r0, lp ? lp + r0 : nullptr, dp ? dp + r0 : nullptr,
                                          gx, nx, 1, 1);
                     } else {
@@ -979,7 +1027,9 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                     r = gy - y0 + GY;
                     if (gx >= nx || r < 0 || r >= SH) continue;
                     if (C.periodic[AY]) {
-                        v = line_pair<T, COH>(hp + gx, lp ? lp + gx : nullptr, dp ? dp + gx : nullptr,
+                        const long long c0 = HJI_CHK_REL(CK_GHOST_LINE, tg.base, (long long)gx,
+                                                         (long long)(ny - 1) * sy + 1, C.nalloc);
+                        v = line_pair<T, COH>(hp + c0, lp ? lp + c0 : nullptr, dp ? dp + c0 : nullptr,
                                          gy, ny, sy, 1);
                     } else {
                         const bool low = gy < 0;
@@ -990,8 +1040,9 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                 }
                 // Written after every read of this pass: ghost nodes only
                 // read in-grid nodes, and no thread writes an in-grid node.
-                wh[r * SWX + c] = v.h;
-                if constexpr (INCR) wl[r * SWX + c] = v.l;
+                const int gs = HJI_CHK(CK_GHOST_WRITE, r * SWX + c, 1, WIN);
+                wh[gs] = v.h;
+                if constexpr (INCR) wl[gs] = v.l;
             }
             __syncthreads();
         }
@@ -1002,7 +1053,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
         if constexpr (NDIM >= 2) {
             for (int i = kThreads - 1 - threadIdx.x; i < (SH - 1) * GROUPS; i += kThreads) {
                 const int r = i / GROUPS, g4 = i - r * GROUPS;
-                const int s0 = r * SWX + 4 + 4 * g4;
+                const int s0 = HJI_CHK(CK_DIFF_READ, r * SWX + 4 + 4 * g4, SWX + 4, WIN);
                 const Q4<T> h0 = ld4(wh + s0), h1 = ld4(wh + s0 + SWX);
                 T dv[4];
                 if constexpr (INCR) {
@@ -1021,7 +1072,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
 #pragma unroll
                     for (int q = 0; q < 4; ++q) dv[q] = h1.v[q] - h0.v[q];
                 }
-                st4(dys + r * TX + 4 * g4, dv);
+                st4(dys + HJI_CHK(CK_DIFF_WRITE, r * TX + 4 * g4, 4, (SH - 1) * TX), dv);
             }
             __syncthreads();
         }
@@ -1031,10 +1082,11 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
         //     (j, g4) takes set j of columns 4 g4 .. 4 g4 + 3.
         if constexpr (L::YSETS) {
             const int j = threadIdx.x / GROUPS, g4 = threadIdx.x - j * GROUPS;
+            const int q0 = HJI_CHK(CK_YSET_READ, j * TX + 4 * g4, 4 * TX + 4, (SH - 1) * TX);
             T q[5][4];
 #pragma unroll
             for (int o = 0; o < 5; ++o) {
-                const Q4<T> v = ld4(dys + (j + o) * TX + 4 * g4);
+                const Q4<T> v = ld4(dys + q0 + o * TX);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) q[o][c] = v.v[c];
             }
@@ -1052,8 +1104,13 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                 pmv[c] = weno_fwd(q[1][c], q[2][c], q[3][c], w) * iy;
                 ppv[c] = weno_rev(q[1][c], q[2][c], q[3][c], w) * iy;
             }
-            if (j < TY) st4(reinterpret_cast<T*>(sb + L::PMY) + j * TX + 4 * g4, pmv);
-            if (j > 0) st4(reinterpret_cast<T*>(sb + L::PPY) + (j - 1) * TX + 4 * g4, ppv);
+            if (j < TY)
+                st4(reinterpret_cast<T*>(sb + L::PMY) + HJI_CHK(CK_YSET_WRITE, j * TX + 4 * g4, 4, TY * TX),
+                    pmv);
+            if (j > 0)
+                st4(reinterpret_cast<T*>(sb + L::PPY) +
+                        HJI_CHK(CK_YSET_WRITE, (j - 1) * TX + 4 * g4, 4, TY * TX),
+                    ppv);
             __syncthreads();
         }
 
@@ -1081,7 +1138,8 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                 Lv[i] += ha * (pp_ - pm_);
                 pb[i][ax] = pp_ + pm_;  // 2 pbar: the Hamiltonian's constants are halved
             };
-            const long long gidx = tg.base + (long long)gy * sy + gx0;
+            const long long gidx =
+                HJI_CHK(CK_NODE_GLOBAL, tg.base + (long long)gy * sy + gx0, 4, C.nalloc);
             // Slower axes first (their stencil lines are the largest live
             // set): the lines straight from global memory
             // (L1/L2), four nodes per load, differenced plane by plane.  The
@@ -1093,7 +1151,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                 const int si = tg.sidx[ax], ns = C.n[ax];
                 const long long l0 = gidx - (long long)si * st;  // node 0 of these lines
                 auto plane = [&](int j, Pair<T>* out) {
-                    const long long o = l0 + (long long)j * st;
+                    const long long o = HJI_CHK(CK_PLANE, l0 + (long long)j * st, 4, C.nalloc);
                     const Q4<T> h = ldg4<T, COH>(C.win + o);
                     Q4<T> lo, dd;
                     if constexpr (INCR) {
@@ -1154,7 +1212,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                 }
             }
             // x: the window row of this run, columns 4 grp .. 4 grp + 11.
-            const int s0 = (ry + GY) * SWX + 4 * grp;
+            const int s0 = HJI_CHK(CK_XWINDOW, (ry + GY) * SWX + 4 * grp, 12, WIN);
             {
                 T d[11];
                 const Q4<T> h0 = ld4(wh + s0), h1 = ld4(wh + s0 + 4), h2 = ld4(wh + s0 + 8);
@@ -1228,15 +1286,17 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
             // y: WENO5 from the set pass; ENO from rows ry .. ry + 2G - 1 of
             // the difference array.
             if constexpr (L::YSETS) {
-                const Q4<T> m4 = ld4(reinterpret_cast<const T*>(sb + L::PMY) + ry * TX + 4 * grp);
-                const Q4<T> p4 = ld4(reinterpret_cast<const T*>(sb + L::PPY) + ry * TX + 4 * grp);
+                const int ni = HJI_CHK(CK_NODE_SMEM, ry * TX + 4 * grp, 4, TY * TX);
+                const Q4<T> m4 = ld4(reinterpret_cast<const T*>(sb + L::PMY) + ni);
+                const Q4<T> p4 = ld4(reinterpret_cast<const T*>(sb + L::PPY) + ni);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) fold(AY, i, m4.v[i], p4.v[i]);
             } else if constexpr (NDIM >= 2) {
                 T dy[2 * G][4];
+                const int y0i = HJI_CHK(CK_DIFF_Y, ry * TX + 4 * grp, (2 * G - 1) * TX + 4, (SH - 1) * TX);
 #pragma unroll
                 for (int o = 0; o < 2 * G; ++o) {
-                    const Q4<T> q = ld4(dys + (ry + o) * TX + 4 * grp);
+                    const Q4<T> q = ld4(dys + y0i + o * TX);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) dy[o][i] = q.v[i];
                 }
@@ -1290,11 +1350,14 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
 #pragma unroll
                     for (int r = 1; r < NDIM; ++r) ia = ax == r ? idx[r] : ia;
                     if (ax == AX) {
+                        const int xa = HJI_CHK_REL(CK_TABLE, (long long)tt * C.table_stride, gx0,
+                                                   min(4, nx - gx0), C.table_elems);
 #pragma unroll
                         for (int i = 0; i < 4; ++i)  // runs may reach past the edge
-                            Lv[i] += pr[i] * __ldg(tab + min(gx0 + i, nx - 1));
+                            Lv[i] += pr[i] * __ldg(tab + min(xa + i, nx - 1));
                     } else {
-                        const T w = __ldg(tab + ia);
+                        const T w = __ldg(
+                            tab + HJI_CHK_REL(CK_TABLE, (long long)tt * C.table_stride, ia, 1, C.table_elems));
 #pragma unroll
                         for (int i = 0; i < 4; ++i) Lv[i] += pr[i] * w;
                     }
@@ -1364,7 +1427,8 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                     }
                     Q4<T> lt;  // l at the run's nodes
                     if constexpr (L::STAGE_L)
-                        lt = ld4(reinterpret_cast<const T*>(sb + L::LT(buf)) + ry * TX + 4 * grp);
+                        lt = ld4(reinterpret_cast<const T*>(sb + L::LT(buf)) +
+                                 HJI_CHK(CK_NODE_SMEM, ry * TX + 4 * grp, 4, TY * TX));
                     else
                         lt = ldg4(C.l + gidx);  // (its pad columns are never used)
                     if (C.discounted) {
@@ -1414,7 +1478,8 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                 if (reads_v) {
                     Q4<T> q;
                     if constexpr (LAST)
-                        q = ld4(reinterpret_cast<const T*>(sb + L::VN(buf)) + ry * TX + 4 * grp);
+                        q = ld4(reinterpret_cast<const T*>(sb + L::VN(buf)) +
+                                HJI_CHK(CK_NODE_SMEM, ry * TX + 4 * grp, 4, TY * TX));
                     else
                         q = ldg4<T, COH>(C.vcur + gidx);
 #pragma unroll
@@ -1426,8 +1491,8 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                     out[i] = reads_v ? cV * vn[i] + cE * eul : eul;
                 }
                 if constexpr (LAST) {
-                    const Q4<T> lt =
-                        ld4(reinterpret_cast<const T*>(sb + L::LT(buf)) + ry * TX + 4 * grp);
+                    const Q4<T> lt = ld4(reinterpret_cast<const T*>(sb + L::LT(buf)) +
+                                         HJI_CHK(CK_NODE_SMEM, ry * TX + 4 * grp, 4, TY * TX));
                     if (C.discounted) {
 #pragma unroll
                         for (int i = 0; i < 4; ++i) out[i] *= C.disc;

@@ -35,6 +35,16 @@ def test_library_exports_every_declared_symbol(hji_lib):
         assert getattr(lib, n) is not None
 
 
+def test_checked_build_exports_every_declared_symbol():
+    """The bounds-checked debug build has the same boundary."""
+    from paper_1903_07715_gb300 import build as B
+    path = B.build(checked=True)  # no-op when up to date
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(l.split()[-1] for l in out.splitlines() if l.strip())
+    assert not [n for n in _declared() if n not in exported]
+
+
 def test_binding_names_match_header(hji_lib):
     assert sorted(hji_lib.EXPORTS) == sorted(n for n in _declared())
     for n in _declared():
@@ -44,6 +54,7 @@ def test_binding_names_match_header(hji_lib):
 def test_status_strings(hji_lib):
     assert hji_lib.hji_status_string(0) == "ok"
     assert hji_lib.hji_status_string(4) == "not converged"
+    assert hji_lib.hji_status_string(8) == "index check failed"
     assert hji_lib.hji_status_string(99) == "unknown status"
 
 
