@@ -91,7 +91,7 @@ def grid_cases():
                                        gd, dyn, l, prec, scheme=scheme, rk=rk, march=march,
                                        check_every=2)
             if nd == 2:
-                # ragged multi-tile grids in every tile shape (31x32, 15x64, 7x128)
+                # ragged multi-tile grids in every tile shape (31x32, 15x64, 63x16)
                 for scheme, rk in SCHEMES:
                     for tv in (1, 2, 3):
                         gd = W.grid([70, 135], [-1.0, -1.5], [1.1, 1.2], periodic=[0, 1])
