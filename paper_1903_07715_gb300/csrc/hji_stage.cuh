@@ -89,6 +89,17 @@ __device__ __forceinline__ T smaller_mag(T a, T b) {
 //         1e-18 keeps the sums below 2^126 (the range of the fast division)
 //         while exceeding 1e-6 max(v^2) only where every |v| < 1e-6 (flat
 //         data, where the weights do not matter).
+// The hardware's approximate reciprocal (PTX rcp.approx.ftz.f32, one
+// special-function instruction).  The WENO5 weights' denominators lie far
+// inside the normal range (at least 1e-18 and below 2^126), where it is
+// what a fast division by them computes, without that division's checks
+// for the range ends.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <typename T>
 struct WenoSet {
     T z1, z3, A, B, u;
@@ -109,9 +120,9 @@ __device__ __forceinline__ WenoSet<T> weno_set(T e1, T e2, T e3, T e4, T m, T t1
     T z1, z2, z3;
     if constexpr (sizeof(T) == 4) {
         const float eps = fmaf(keps * m, m, 1e-18f * (12.0f / 13.0f));
-        const float rA = __fdividef(1.0f, sA + eps);
-        const float rB = __fdividef(1.0f, sB + eps);
-        const float rC = __fdividef(1.0f, sC + eps);
+        const float rA = rcp_approx(sA + eps);
+        const float rB = rcp_approx(sB + eps);
+        const float rC = rcp_approx(sC + eps);
         z1 = rA * rA;
         z2 = rB * rB;
         z3 = rC * rC;
@@ -134,7 +145,7 @@ __device__ __forceinline__ WenoSet<T> weno_set(T e1, T e2, T e3, T e4, T m, T t1
 
 template <typename T>
 __device__ __forceinline__ T ratio(T num, T den) {
-    if constexpr (sizeof(T) == 4) return __fdividef(num, den);
+    if constexpr (sizeof(T) == 4) return num * rcp_approx(den);
     else return num / den;
 }
 
@@ -153,6 +164,55 @@ __device__ __forceinline__ T weno_rev(T v2, T v3, T v4, const WenoSet<T>& w) {
     const T num = fma(T(1.5), w.A, w.B);
     const T den = fma(T(9), w.z1, fma(T(3), w.z3, w.u));
     return phi2 - ratio(num, den);
+}
+
+// ---- Two FP32 lanes per instruction ----
+// Blackwell's packed FP32 instructions (add / mul / fma on .f32x2) do two
+// lanes in one issue slot, each lane rounded as the scalar instruction
+// would be.  The WENO5 y-set pass evaluates four independent tile columns
+// per thread, which pair up as (0, 1) and (2, 3).
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 rcp2(float2 a) {  // the scalar path's reciprocal, per lane
+    return make_float2(rcp_approx(a.x), rcp_approx(a.y));
+}
+
+// weno_set on two lanes (FP32): the same arithmetic; 3 e3 - e4 enters only
+// squared, so its negation e4 - 3 e3 (one fused operation) is used.
+__device__ __forceinline__ WenoSet<float2> weno_set2(float2 e1, float2 e2, float2 e3, float2 e4, float2 m,
+                                                    float2 t1, float2 t3) {
+    const float2 kq = f2(3.0f / 13.0f);
+    const float2 pA = sub2(e1, e2), qA = fma2(e2, f2(-3.0f), e1);
+    const float2 pB = sub2(e2, e3), qB = add2(e2, e3);
+    const float2 pC = sub2(e3, e4), qCn = fma2(e3, f2(-3.0f), e4);
+    const float2 sA = fma2(pA, pA, mul2(mul2(kq, qA), qA));
+    const float2 sB = fma2(pB, pB, mul2(mul2(kq, qB), qB));
+    const float2 sC = fma2(pC, pC, mul2(mul2(kq, qCn), qCn));
+    const float2 eps = fma2(mul2(f2(float(1e-6 * 12.0 / 13.0)), m), m, f2(1e-18f * (12.0f / 13.0f)));
+    const float2 rA = rcp2(add2(sA, eps)), rB = rcp2(add2(sB, eps)), rC = rcp2(add2(sC, eps));
+    WenoSet<float2> w;
+    w.z1 = mul2(rA, rA);
+    w.z3 = mul2(rC, rC);
+    w.A = mul2(w.z1, t1);
+    w.B = mul2(w.z3, t3);
+    w.u = mul2(f2(18.0f), mul2(rB, rB));
+    return w;
+}
+__device__ __forceinline__ float2 ratio2(float2 num, float2 den) { return mul2(num, rcp2(den)); }
+__device__ __forceinline__ float2 weno_fwd2(float2 v2, float2 v3, float2 v4, const WenoSet<float2>& w) {
+    const float2 phi2 = fma2(v4, f2(1.0f / 3.0f), fma2(v2, f2(-1.0f / 6.0f), mul2(v3, f2(5.0f / 6.0f))));
+    const float2 num = fma2(f2(1.5f), w.B, w.A);
+    const float2 den = fma2(f2(3.0f), w.z1, fma2(f2(9.0f), w.z3, w.u));
+    return add2(phi2, ratio2(num, den));
+}
+__device__ __forceinline__ float2 weno_rev2(float2 v2, float2 v3, float2 v4, const WenoSet<float2>& w) {
+    const float2 phi2 = fma2(v2, f2(1.0f / 3.0f), fma2(v4, f2(-1.0f / 6.0f), mul2(v3, f2(5.0f / 6.0f))));
+    const float2 num = fma2(f2(1.5f), w.A, w.B);
+    const float2 den = fma2(f2(9.0f), w.z1, fma2(f2(3.0f), w.z3, w.u));
+    return sub2(phi2, ratio2(num, den));
 }
 
 // WENO5 (p-, p+) from the six differences D[0..5] of one node.
@@ -1092,17 +1152,42 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
             }
             const T iy = C.inv_dx[AY];
             T pmv[4], ppv[4];
+            T mc[4];  // the sets' scales m (no packed max)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                T e[4];
+            for (int c = 0; c < 4; ++c)
+                mc[c] = fmax(fmax(fmax(fabs(q[0][c]), fabs(q[1][c])), fmax(fabs(q[2][c]), fabs(q[3][c]))),
+                             fabs(q[4][c]));
+            if constexpr (sizeof(T) == 4) {
+                // columns (0, 1) and (2, 3) as two lanes
 #pragma unroll
-                for (int o = 0; o < 4; ++o) e[o] = q[o][c] - q[o + 1][c];
-                const T t1 = e[0] - T(2) * e[1] + e[2], t3 = e[1] - T(2) * e[2] + e[3];
-                const T m = fmax(fmax(fmax(fabs(q[0][c]), fabs(q[1][c])), fmax(fabs(q[2][c]), fabs(q[3][c]))),
-                                 fabs(q[4][c]));
-                const WenoSet<T> w = weno_set(e[0], e[1], e[2], e[3], m, t1, t3);
-                pmv[c] = weno_fwd(q[1][c], q[2][c], q[3][c], w) * iy;
-                ppv[c] = weno_rev(q[1][c], q[2][c], q[3][c], w) * iy;
+                for (int c = 0; c < 4; c += 2) {
+                    float2 v[5], e[4];
+#pragma unroll
+                    for (int o = 0; o < 5; ++o) v[o] = make_float2(q[o][c], q[o][c + 1]);
+#pragma unroll
+                    for (int o = 0; o < 4; ++o) e[o] = sub2(v[o], v[o + 1]);
+                    const float2 t1 = add2(fma2(e[1], f2(-2.0f), e[0]), e[2]);
+                    const float2 t3 = add2(fma2(e[2], f2(-2.0f), e[1]), e[3]);
+                    const WenoSet<float2> w =
+                        weno_set2(e[0], e[1], e[2], e[3], make_float2(mc[c], mc[c + 1]), t1, t3);
+                    const float2 pm = mul2(weno_fwd2(v[1], v[2], v[3], w), f2(iy));
+                    const float2 pp = mul2(weno_rev2(v[1], v[2], v[3], w), f2(iy));
+                    pmv[c] = pm.x;
+                    pmv[c + 1] = pm.y;
+                    ppv[c] = pp.x;
+                    ppv[c + 1] = pp.y;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    T e[4];
+#pragma unroll
+                    for (int o = 0; o < 4; ++o) e[o] = q[o][c] - q[o + 1][c];
+                    const T t1 = e[0] - T(2) * e[1] + e[2], t3 = e[1] - T(2) * e[2] + e[3];
+                    const WenoSet<T> w = weno_set(e[0], e[1], e[2], e[3], mc[c], t1, t3);
+                    pmv[c] = weno_fwd(q[1][c], q[2][c], q[3][c], w) * iy;
+                    ppv[c] = weno_rev(q[1][c], q[2][c], q[3][c], w) * iy;
+                }
             }
             if (j < TY)
                 st4(reinterpret_cast<T*>(sb + L::PMY) + HJI_CHK(CK_YSET_WRITE, j * TX + 4 * g4, 4, TY * TX),
