@@ -901,20 +901,21 @@ def _served_vs_f64(hji, torch, srv, reqs, records, opts, budget_s):
 # --profile-steps 2 --workload W` of the current stage kernels (mean of the
 # two launches of each stage; summaries under profiles/).
 DRAM_BYTES_PER_LAUNCH = {
-    ("di_8192^2", "first_stage"): (540748800 + 238147840 + 541717248 + 238302464) / 2,
-    ("di_8192^2", "fused_last_stage"): (1202743040 + 506452480 + 1205676288 + 505219328) / 2,
-    ("quad4d_61^4", "first_stage"): (121117440 + 36525568 + 121155328 + 36753920) / 2,
-    ("quad4d_61^4", "fused_last_stage"): (256818944 + 93993984 + 257107200 + 94154752) / 2,
+    ("di_8192^2", "first_stage"): (541499648 + 237979904 + 542182400 + 238619136) / 2,
+    ("di_8192^2", "fused_last_stage"): (1203697664 + 506604032 + 1205700352 + 505386240) / 2,
+    ("quad4d_61^4", "first_stage"): (121092096 + 36517120 + 121197824 + 36704000) / 2,
+    ("quad4d_61^4", "fused_last_stage"): (258368768 + 94071808 + 258445056 + 94155264) / 2,
 }
 # The multi-step march kernel on 8192^2 (one launch of 20 steps, read +
 # written, from `ncu ... -k regex:march_kernel -s 2 -c 2 python bench.py
 # --workload di8192 --steps 1 --warmup 1 --march multi_step`), per RK2 step.
-DRAM_BYTES_MARCH_8192_PER_STEP = (34933350144 + 16078156032) / 20
-# The same capture of the 1001^2 WENO5 stage kernels (first touch of each
-# field per launch: ncu flushes the caches between launches, so these are
-# upper bounds of what a launch inside a solve moves).
-DRAM_BYTES_DI1001 = [(8122880 + 8122624) / 2, (12158976 + 12161536) / 2,
-                     (16200448 + 16201216) / 2]
+DRAM_BYTES_MARCH_8192_PER_STEP = (34917801216 + 16077754880) / 20
+# The 1001^2 WENO5 stage kernels, one launch of each stage from the
+# `ncu --set full ... -k regex:stage_kernel -c 3 python bench.py
+# --profile-steps 4 --workload di1001` capture (first touch of each field per
+# launch: ncu flushes the caches between launches, so these are upper bounds
+# of what a launch inside a solve moves; no DRAM writes were counted).
+DRAM_BYTES_DI1001 = [8118016, 12154368, 16196608]
 
 
 def march_traffic(name, multi_step):
