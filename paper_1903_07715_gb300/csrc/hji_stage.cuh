@@ -85,10 +85,16 @@ __device__ __forceinline__ T smaller_mag(T a, T b) {
 //   FP64: z = ((b_B b_C)^2, (b_A b_C)^2, (b_A b_B)^2), the common factor
 //         (b_A b_B b_C)^2, one division (tiny = 1e-60 keeps the fourth
 //         powers above the FP64 range floor);
-//   FP32: z = (r_A^2, r_B^2, r_C^2), r = 1/b by the fast reciprocal; tiny =
-//         1e-18 keeps the sums below 2^126 (the range of the fast division)
-//         while exceeding 1e-6 max(v^2) only where every |v| < 1e-6 (flat
-//         data, where the weights do not matter).
+//   FP32: z = (r_A^2, r_B^2, r_C^2), r = 1/b by the hardware's approximate
+//         reciprocal; tiny = 1e-18 keeps r^2 and the weighted sums below
+//         2^126, inside the normal range, while exceeding 1e-6 max(v^2)
+//         only where every |v| < 1e-6 (flat data, where the weights do not
+//         matter).
+template <typename T>
+struct WenoSet {
+    T z1, z3, A, B, u;
+};
+
 // The hardware's approximate reciprocal (PTX rcp.approx.ftz.f32, one
 // special-function instruction).  The WENO5 weights' denominators lie far
 // inside the normal range (at least 1e-18 and below 2^126), where it is
@@ -99,11 +105,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
-
-template <typename T>
-struct WenoSet {
-    T z1, z3, A, B, u;
-};
 
 // A set from its first differences e1..e4, m = max |v_k| and its third
 // differences t1, t3.
