@@ -231,6 +231,43 @@ __device__ __forceinline__ void weno5_pair(const T* D, T inv_dx, T& pm, T& pp) {
     pp = weno_rev(D[2], D[3], D[4], wb) * inv_dx;
 }
 
+// The same on two lanes (FP32; two nodes' stencil lines, lane by lane the
+// scalar arithmetic): WENO5 from six differences per lane, and the
+// smaller-magnitude choice of ENO2 per lane (no packed compare).
+__device__ __forceinline__ void weno5_pair2(const float2* D, float2 inv_dx, float2& pm, float2& pp) {
+    float2 E[5], Tt[3];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) E[k] = sub2(D[k], D[k + 1]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Tt[k] = add2(fma2(E[k + 1], f2(-2.0f), E[k]), E[k + 2]);
+    const float m14x = fmaxf(fmaxf(fabsf(D[1].x), fabsf(D[2].x)), fmaxf(fabsf(D[3].x), fabsf(D[4].x)));
+    const float m14y = fmaxf(fmaxf(fabsf(D[1].y), fabsf(D[2].y)), fmaxf(fabsf(D[3].y), fabsf(D[4].y)));
+    const WenoSet<float2> wa =
+        weno_set2(E[0], E[1], E[2], E[3],
+                  make_float2(fmaxf(m14x, fabsf(D[0].x)), fmaxf(m14y, fabsf(D[0].y))), Tt[0], Tt[1]);
+    const WenoSet<float2> wb =
+        weno_set2(E[1], E[2], E[3], E[4],
+                  make_float2(fmaxf(m14x, fabsf(D[5].x)), fmaxf(m14y, fabsf(D[5].y))), Tt[1], Tt[2]);
+    pm = mul2(weno_fwd2(D[1], D[2], D[3], wa), inv_dx);
+    pp = mul2(weno_rev2(D[2], D[3], D[4], wb), inv_dx);
+}
+__device__ __forceinline__ float2 smaller_mag2(float2 a, float2 b) {
+    return make_float2(fabsf(a.x) <= fabsf(b.x) ? a.x : b.x, fabsf(a.y) <= fabsf(b.y) ? a.y : b.y);
+}
+template <int SCHEME>
+__device__ __forceinline__ void one_sided_diffs2(const float2* D, float2 inv_dx, float2& pm, float2& pp) {
+    if constexpr (SCHEME == HJI_ENO1) {
+        pm = mul2(D[0], inv_dx);
+        pp = mul2(D[1], inv_dx);
+    } else if constexpr (SCHEME == HJI_ENO2) {
+        const float2 Sm = sub2(D[1], D[0]), S0 = sub2(D[2], D[1]), Sp = sub2(D[3], D[2]);
+        pm = mul2(fma2(f2(0.5f), smaller_mag2(Sm, S0), D[1]), inv_dx);
+        pp = mul2(fma2(f2(-0.5f), smaller_mag2(S0, Sp), D[2]), inv_dx);
+    } else {
+        weno5_pair2(D, inv_dx, pm, pp);
+    }
+}
+
 // (p-, p+) at node c from the 2G undivided differences D[k] = W[k+1] - W[k]
 // of its stencil line W[0..2G] (node c = W[G]; D[G-1] is the backward and
 // D[G] the forward difference).
@@ -1272,29 +1309,81 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                     }
                 };
                 const bool inner = si >= G && si < ns - G;
-                T D[2 * G][4];
-                Pair<T> prev[4], cur[4];
-                if (inner) plane(si - G, prev);
-                else plane_any(si - G, prev);
+                const T is = C.inv_dx[ax];
+                if constexpr (INCR) {
+                    // FP32: nodes (0, 1) and (2, 3) of the run as two lanes of
+                    // packed instructions (the plane loads give them as
+                    // aligned pairs); the same arithmetic lane by lane.
+                    struct P2 {
+                        float2 h[2], l[2];
+                    };
+                    auto plane2 = [&](int j) {
+                        P2 r;
+                        if (inner || (j >= 0 && j < ns)) {
+                            const long long o = HJI_CHK(CK_PLANE, l0 + (long long)j * st, 4, C.nalloc);
+                            const Q4<T> h = ldg4<T, COH>(C.win + o);
+                            const Q4<T> lo = ldg4<T, COH>(C.vlo + o);
+                            r.h[0] = make_float2(h.v[0], h.v[1]);
+                            r.h[1] = make_float2(h.v[2], h.v[3]);
+                            r.l[0] = make_float2(lo.v[0], lo.v[1]);
+                            r.l[1] = make_float2(lo.v[2], lo.v[3]);
+                            if (C.din) {
+                                const Q4<T> dd = ldg4<T, COH>(C.din + o);
+                                r.l[0] = add2(r.l[0], make_float2(dd.v[0], dd.v[1]));
+                                r.l[1] = add2(r.l[1], make_float2(dd.v[2], dd.v[3]));
+                            }
+                        } else {  // a ghost plane (periodic wrap or extrapolation)
+                            Pair<T> out[4];
+                            plane_any(j, out);
 #pragma unroll
-                for (int o = 1 - G; o <= G; ++o) {
-                    if (inner) plane(si + o, cur);
-                    else plane_any(si + o, cur);
+                            for (int k = 0; k < 2; ++k) {
+                                r.h[k] = make_float2(out[2 * k].h, out[2 * k + 1].h);
+                                r.l[k] = make_float2(out[2 * k].l, out[2 * k + 1].l);
+                            }
+                        }
+                        return r;
+                    };
+                    float2 D2[2][2 * G];
+                    P2 prev = plane2(si - G);
+#pragma unroll
+                    for (int o = 1 - G; o <= G; ++o) {
+                        const P2 cur = plane2(si + o);
+#pragma unroll
+                        for (int k = 0; k < 2; ++k)
+                            D2[k][o + G - 1] = add2(sub2(cur.h[k], prev.h[k]), sub2(cur.l[k], prev.l[k]));
+                        prev = cur;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        float2 pm2, pp2;
+                        one_sided_diffs2<SCHEME>(D2[k], f2(is), pm2, pp2);
+                        fold(ax, 2 * k, pm2.x, pp2.x);
+                        fold(ax, 2 * k + 1, pm2.y, pp2.y);
+                    }
+                } else {
+                    T D[2 * G][4];
+                    Pair<T> prev[4], cur[4];
+                    if (inner) plane(si - G, prev);
+                    else plane_any(si - G, prev);
+#pragma unroll
+                    for (int o = 1 - G; o <= G; ++o) {
+                        if (inner) plane(si + o, cur);
+                        else plane_any(si + o, cur);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            D[o + G - 1][i] = pair_diff(cur[i], prev[i]);
+                            prev[i] = cur[i];
+                        }
+                    }
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        D[o + G - 1][i] = pair_diff(cur[i], prev[i]);
-                        prev[i] = cur[i];
+                        T Di[2 * G];
+#pragma unroll
+                        for (int o = 0; o < 2 * G; ++o) Di[o] = D[o][i];
+                        T pm_, pp_;
+                        one_sided_diffs<T, SCHEME>(Di, is, pm_, pp_);
+                        fold(ax, i, pm_, pp_);
                     }
-                }
-                const T is = C.inv_dx[ax];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    T Di[2 * G];
-#pragma unroll
-                    for (int o = 0; o < 2 * G; ++o) Di[o] = D[o][i];
-                    T pm_, pp_;
-                    one_sided_diffs<T, SCHEME>(Di, is, pm_, pp_);
-                    fold(ax, i, pm_, pp_);
                 }
             }
             // x: the window row of this run, columns 4 grp .. 4 grp + 11.
