@@ -1263,6 +1263,10 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
             };
             const long long gidx =
                 HJI_CHK(CK_NODE_GLOBAL, tg.base + (long long)gy * sy + gx0, 4, C.nalloc);
+            // FP32 last stage without staged l: its load from L2 is issued
+            // here, so that its latency overlaps the derivatives.
+            Q4<T> lt_early;
+            if constexpr (LAST && INCR && !L::STAGE_L) lt_early = ldg4(C.l + gidx);
             // Slower axes first (their stencil lines are the largest live
             // set): the lines straight from global memory
             // (L1/L2), four nodes per load, differenced plane by plane.  The
@@ -1605,7 +1609,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                         lt = ld4(reinterpret_cast<const T*>(sb + L::LT(buf)) +
                                  HJI_CHK(CK_NODE_SMEM, ry * TX + 4 * grp, 4, TY * TX));
                     else
-                        lt = ldg4(C.l + gidx);  // (its pad columns are never used)
+                        lt = lt_early;  // (its pad columns are never used)
                     if (C.discounted) {
                         // gamma V~ = V~ - (1 - gamma) V~ with V~ = hi + lo +
                         // inc; the low word's share of (1 - gamma) V~ is below
