@@ -1347,15 +1347,17 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
                         }
                         return r;
                     };
-                    float2 D2[2][2 * G];
-                    P2 prev = plane2(si - G);
+                    // every plane of the line first (their loads in flight
+                    // together), then the differences
+                    P2 pl[2 * G + 1];
 #pragma unroll
-                    for (int o = 1 - G; o <= G; ++o) {
-                        const P2 cur = plane2(si + o);
+                    for (int o = 0; o <= 2 * G; ++o) pl[o] = plane2(si - G + o);
+                    float2 D2[2][2 * G];
+#pragma unroll
+                    for (int o = 0; o < 2 * G; ++o) {
 #pragma unroll
                         for (int k = 0; k < 2; ++k)
-                            D2[k][o + G - 1] = add2(sub2(cur.h[k], prev.h[k]), sub2(cur.l[k], prev.l[k]));
-                        prev = cur;
+                            D2[k][o] = add2(sub2(pl[o + 1].h[k], pl[o].h[k]), sub2(pl[o + 1].l[k], pl[o].l[k]));
                     }
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
