@@ -901,10 +901,10 @@ def _served_vs_f64(hji, torch, srv, reqs, records, opts, budget_s):
 # --profile-steps 2 --workload W` of the current stage kernels (mean of the
 # two launches of each stage; summaries under profiles/).
 DRAM_BYTES_PER_LAUNCH = {
-    ("di_8192^2", "first_stage"): (541499648 + 237979904 + 542182400 + 238619136) / 2,
-    ("di_8192^2", "fused_last_stage"): (1203697664 + 506604032 + 1205700352 + 505386240) / 2,
-    ("quad4d_61^4", "first_stage"): (121092096 + 36517120 + 121197824 + 36704000) / 2,
-    ("quad4d_61^4", "fused_last_stage"): (258368768 + 94071808 + 258445056 + 94155264) / 2,
+    ("di_8192^2", "first_stage"): (541506304 + 237935872 + 542315264 + 238590208) / 2,
+    ("di_8192^2", "fused_last_stage"): (1204115456 + 506545920 + 1207416576 + 505442816) / 2,
+    ("quad4d_61^4", "first_stage"): (121088512 + 36569344 + 121139968 + 36809984) / 2,
+    ("quad4d_61^4", "fused_last_stage"): (254387456 + 93981952 + 253672704 + 94644736) / 2,
 }
 # The multi-step march kernel on 8192^2 (one launch of 20 steps, read +
 # written, from `ncu ... -k regex:march_kernel -s 2 -c 2 python bench.py
@@ -915,7 +915,7 @@ DRAM_BYTES_MARCH_8192_PER_STEP = (34917801216 + 16077754880) / 20
 # --profile-steps 4 --workload di1001` capture (first touch of each field per
 # launch: ncu flushes the caches between launches, so these are upper bounds
 # of what a launch inside a solve moves; no DRAM writes were counted).
-DRAM_BYTES_DI1001 = [8118016, 12154368, 16196608]
+DRAM_BYTES_DI1001 = [8118528, 12154880, 16197120]
 
 
 def march_traffic(name, multi_step):
