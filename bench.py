@@ -1017,6 +1017,11 @@ def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=N
                               "method_frac": am / peak,
                               "traffic": DRAM_BYTES_PER_LAUNCH.get((name, key))}
         gbs = upd * bytes_per_update / (ms * 1e-3) / 1e9
+        # The launch form that ran: the solve's launch count less the set-up
+        # launches (two per grid, three with a term table) is below the step
+        # count only for the multi-step launch.
+        setup = sum(2 + (1 if d.get("terms") else 0) for d in dyns)
+        multi_step = launches / max(1, repeats) - setup < steps
         # The method's counts per node-step: per-stage kernels of RK2 move 6
         # words (24 B in FP32); a march fused in time needs 3 (read V^n and l,
         # write V^{n+1}: 12 B).
@@ -1028,11 +1033,10 @@ def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=N
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                                   "frac": gbs / peak, "peak_source": src,
                                   "bytes_per_node_step": bytes_per_update,
-                                  "traffic": march_traffic(name, launches / max(1, repeats) < steps),
+                                  "traffic": march_traffic(name, multi_step),
                                   "traffic_unit": "DRAM bytes per RK2 step of the launch form that "
                                                   "ran (ncu)",
-                                  "launch_form": "multi_step" if launches / max(1, repeats) < steps
-                                                 else "per_stage",
+                                  "launch_form": "multi_step" if multi_step else "per_stage",
                                   "method_per_stage": {"bytes_per_node_step": 24,
                                                        "achieved": gbs_stage,
                                                        "frac": gbs_stage / peak},
