@@ -910,6 +910,10 @@ DRAM_BYTES_PER_LAUNCH = {
 # written, from `ncu ... -k regex:march_kernel -s 2 -c 2 python bench.py
 # --workload di8192 --steps 1 --warmup 1 --march multi_step`), per RK2 step.
 DRAM_BYTES_MARCH_8192_PER_STEP = (34917801216 + 16077754880) / 20
+# The same for the 256-grid batch (`ncu ... -k regex:march_kernel python
+# bench.py --workload batch256 --steps 1 --warmup 1 --march multi_step
+# --no-cpu-baseline`: two launches of 50 steps, tile shape 63x16), per RK2 step.
+DRAM_BYTES_MARCH_BATCH_PER_STEP = (33359375616 + 15277051136 + 33355850752 + 15273392640) / 100
 # The 1001^2 WENO5 stage kernels, one launch of each stage from the
 # `ncu --set full ... -k regex:stage_kernel -c 3 python bench.py
 # --profile-steps 4 --workload di1001` capture (first touch of each field per
@@ -922,7 +926,8 @@ def march_traffic(name, multi_step):
     """Captured DRAM bytes per RK2 step of a workload's march in the launch
     form it ran (None where no capture of that form exists)."""
     if multi_step:
-        return DRAM_BYTES_MARCH_8192_PER_STEP if name == "di_8192^2" else None
+        return {"di_8192^2": DRAM_BYTES_MARCH_8192_PER_STEP,
+                "batch256_di_101..501": DRAM_BYTES_MARCH_BATCH_PER_STEP}.get(name)
     b = (DRAM_BYTES_PER_LAUNCH.get((name, "first_stage"), 0) +
          DRAM_BYTES_PER_LAUNCH.get((name, "fused_last_stage"), 0))
     return b or None
