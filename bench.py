@@ -350,9 +350,9 @@ def main():
         line["time_to_converge"] = time_to_converge(hji, torch, gd, dyn, l, l_dev, k_dev)
         line["hbm_workloads"] = hbm_workloads(hji, torch)
         line["config_rows"] = config_rows(hji, torch)
-        line["north_star_batch"] = {
-            "paper_interval_test_0.001": north_star_batch(hji, torch, 1e-3),
-            "tight_interval_test_1e-4": north_star_batch(hji, torch, 1e-4, max_steps=20000)}
+        line["batch_vs_f64_standard"] = {
+            "paper_interval_test_0.001": batch_vs_f64_standard(hji, torch, 1e-3),
+            "tight_interval_test_1e-4": batch_vs_f64_standard(hji, torch, 1e-4, max_steps=20000)}
         line["serving"] = serving_both(hji, torch)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(budget_s=12.0)
@@ -695,7 +695,7 @@ def c2_analysis(hji, torch):
     return out
 
 
-def north_star_batch(hji, torch, interval_tol, budget_s=40.0, max_steps=100000):
+def batch_vs_f64_standard(hji, torch, interval_tol, budget_s=40.0, max_steps=100000):
     """The 256-instance batch (config 4) solved as the batched FP32 warm
     form (one hji_batch_solve, each instance warm-started from its d = 0
     solution) against the plain per-instance FP64 standard solve (V0 = l,
