@@ -88,9 +88,7 @@ def _quad_case(n):
     return gd, dyn, l
 
 
-@pytest.mark.parametrize("ndim", [1, 3, 4])
-@pytest.mark.parametrize("scheme,rk", [("eno2", 2), ("weno5", 3), ("eno1", 1)])
-def test_one_step_fp64_nd(orc, hji_lib, torch_cuda, ndim, scheme, rk):
+def _nd_case(ndim):
     rng = np.random.Generator(np.random.PCG64(ndim))
     if ndim == 1:
         gd = W.grid([263], [-2.0], [2.0])
@@ -107,12 +105,36 @@ def test_one_step_fp64_nd(orc, hji_lib, torch_cuda, ndim, scheme, rk):
         l = np.sqrt(X[0] ** 2 + X[1] ** 2 + X[2] ** 2) - 0.8
     else:
         gd, dyn, l = _quad_case(15)
+    return gd, dyn, l
+
+
+@pytest.mark.parametrize("ndim", [1, 3, 4])
+@pytest.mark.parametrize("scheme,rk", [("eno2", 2), ("weno5", 3), ("eno1", 1)])
+def test_one_step_fp64_nd(orc, hji_lib, torch_cuda, ndim, scheme, rk):
+    gd, dyn, l = _nd_case(ndim)
     P, alpha, dt, traj = oracle_traj(orc, gd, dyn, l, scheme, rk, 12)
     for n in (0, 3, 12):
         want, _ = orc.step(P, scheme, rk, dt, alpha, l, traj[n])
         got, _ = gpu_one_step(hji_lib, gd, dyn, l, traj[n], scheme, rk)
         err = np.abs(got - want).max()
         assert err <= TOL_STEP_F64, (n, err)
+
+
+@pytest.mark.parametrize("ndim", [1, 3, 4])
+@pytest.mark.parametrize("scheme,rk", [("eno2", 2), ("weno5", 3), ("eno1", 1)])
+def test_fp32_steps_nd(orc, hji_lib, torch_cuda, ndim, scheme, rk):
+    """FP32 compensated storage in 1-D, 3-D and 4-D (the FP32 kernels evaluate
+    the slow axes' derivatives two nodes per packed instruction): twelve
+    steps from V0 = l against twelve FP64 oracle steps, within the FP32
+    rounding of the values."""
+    gd, dyn, l = _nd_case(ndim)
+    _, _, _, traj = oracle_traj(orc, gd, dyn, l, scheme, rk, 12)
+    g = _grid(hji_lib, gd, dyn, "f32")
+    st = g.solve(l.astype(np.float32), scheme=scheme, rk=rk, cfl=0.5, tol=0.0, max_steps=12)
+    got = g.value().astype(np.float64)
+    g.close()
+    assert st["steps"] == 12
+    assert np.abs(got - traj[12]).max() <= 1e-5 * np.abs(l).max()
 
 
 @pytest.mark.parametrize("scheme,rk", [("eno2", 2), ("weno5", 3), ("eno1", 1)])
