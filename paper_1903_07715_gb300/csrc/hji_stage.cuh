@@ -577,6 +577,13 @@ __device__ __noinline__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict_
         C.cmid[i] = K.cmid[i];
         C.arad[i] = K.arad[i];
     } else if (t == 96) {
+        // Both buffers' pointers are read beside the state pointer, so that
+        // only the choice between them waits for the buffer index (two
+        // dependent loads before the first tile copy, not three).
+        void* const v0 = D.V[0];
+        void* const v1 = D.V[1];
+        void* const lo0 = D.Vlo[0];
+        void* const lo1 = D.Vlo[1];
         InstState* st = D.state;
         const int cur = *((volatile int*)&st->cur);
         C.inst = inst;
@@ -592,7 +599,7 @@ __device__ __noinline__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict_
         C.tiles_x = static_cast<int>(D.tiles_x);
         C.tiles_per_plane = static_cast<int>(D.tiles_per_plane);
         C.ntiles = static_cast<int>(D.ntiles);
-        const T* vc = static_cast<const T*>(D.V[cur]);
+        const T* vc = static_cast<const T*>(cur ? v1 : v0);
         const T* stage =
             a.stage_in == 0 ? nullptr : static_cast<const T*>(a.stage_in == 1 ? D.W1 : D.W2);
         const int tm_v = cur ? TM_WIN_V1 : TM_WIN_V0;
@@ -612,9 +619,9 @@ __device__ __noinline__ void load_ctx(TileCtx<T>& C, const InstDesc* __restrict_
         C.tm_lo = &D.tm[cur ? TM_WIN_LO1 : TM_WIN_LO0];
         C.tm_l = &D.tm[TM_NODE_L];
         C.tm_vn = &D.tm[cur ? TM_NODE_V1 : TM_NODE_V0];
-        C.vlo = static_cast<const T*>(D.Vlo[cur]);
-        C.vlo_out = static_cast<T*>(D.Vlo[cur ^ 1]);
-        C.wout = a.stage_out == 3 ? static_cast<T*>(D.V[cur ^ 1])
+        C.vlo = static_cast<const T*>(cur ? lo1 : lo0);
+        C.vlo_out = static_cast<T*>(cur ? lo0 : lo1);
+        C.wout = a.stage_out == 3 ? static_cast<T*>(cur ? v0 : v1)
                                   : static_cast<T*>(a.stage_out == 1 ? D.W1 : D.W2);
         C.l = static_cast<const T*>(D.l);
         C.table = static_cast<const T*>(D.table);
