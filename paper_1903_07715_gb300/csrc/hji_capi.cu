@@ -129,7 +129,7 @@ struct hji_grid_s {
     std::string err;
     // Graph cache for single-grid solves.
     cudaGraphExec_t graph = nullptr;
-    long long graph_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long graph_key[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     cudaStream_t cap_stream = nullptr;
 };
 
@@ -795,15 +795,20 @@ hji_status run(int count, hji_grid* grids, const void* const* l, const void* con
         multi ? mgrid : stage_grid(f32, ndim, o->scheme, total_tiles, variant, false, flavor),
         multi ? 0 : stage_grid(f32, ndim, o->scheme, total_tiles, variant, true, flavor)};
     hji::StageArgs base{d_desc, d_tiles, d_ntiles, 0, 0, 0.0, 0.0, 0.0f, 0.0f, 0};
+    // the tile count and, for one grid, the list itself are known here
+    base.ntiles_imm = (int)total_tiles;
+    base.direct = count == 1 ? 1 : 0;
     unsigned* d_barrier = reinterpret_cast<unsigned*>(d_active + 2);
     int* d_fault = d_active + 3;
     cudaGraphExec_t exec = nullptr;
-    // The graph's kernels read descriptors, tile list and its length from the
+    // The graph's kernels read descriptors and the tile list from the
     // leader's scratch, so it stays valid while those buffers and the launch
     // shape (scheme, RK order, chunk, grid, tile shape, launch mode) are
-    // unchanged.
-    const long long key[8] = {(long long)o->scheme, o->rk_order, chunk, grid[0], grid[1],
-                              variant + (multi ? 16 : 0) + 32 * flavor, ndim, f32 ? 1 : 0};
+    // unchanged; its launches also carry the tile count (and, for one grid,
+    // take the list as 0 .. n-1), which is therefore part of the key.
+    const long long key[9] = {(long long)o->scheme, o->rk_order, chunk, grid[0], grid[1],
+                              variant + (multi ? 16 : 0) + 32 * flavor, ndim, f32 ? 1 : 0,
+                              2 * total_tiles + base.direct};
     if (g_stage_timer) {
         // the timed march launches its stages one by one
     } else if (g0->graph && std::memcmp(key, g0->graph_key, sizeof(key)) == 0) {

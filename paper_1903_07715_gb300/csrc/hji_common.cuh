@@ -254,6 +254,10 @@ struct StageArgs {
     double aV, aE;
     float aVf, aEf;        // the same coefficients for FP32 kernels
     int reads_v;           // aV != 0
+    // Known at launch for a single solve (0: read them from device memory,
+    // as engines do, whose tile lists change between launches):
+    int ntiles_imm;        // > 0: the number of tiles in the list
+    int direct;            // 1: the list is one instance's tiles 0 .. n-1 in order
 };
 
 using StageLauncher = cudaError_t (*)(const StageArgs&, int grid, cudaStream_t);

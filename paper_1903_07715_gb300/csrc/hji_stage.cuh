@@ -942,7 +942,11 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
 
     T* dys = reinterpret_cast<T*>(sb + L::DYS);  // dys[r][c] = W(r+1, c) - W(r, c), tile columns
 
-    const int ntiles = *a.ntiles;
+    const int ntiles = a.ntiles_imm > 0 ? a.ntiles_imm : *a.ntiles;
+    // tile-list entry t (a single instance's list is t itself)
+    auto tile_entry = [&](int t) {
+        return a.direct ? static_cast<unsigned long long>(t) : a.tiles[t];
+    };
     // Stage coefficients in the kernel's precision (no conversion in FP32).
     T cV, cE;
     if constexpr (INCR) {
@@ -1016,7 +1020,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
     (void)imax;
     int run_tiles = 0;
     while (t >= 0) {
-        const unsigned long long entry = a.tiles[t];
+        const unsigned long long entry = tile_entry(t);
         const int inst = static_cast<int>(entry >> 48);
         const int local = static_cast<int>(entry & 0xFFFFFFFFFFFFull);
         if (inst != loaded) {
@@ -1038,7 +1042,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
             continue;
         }
         const int tn = walk.next();
-        const bool pref = tn >= 0 && static_cast<int>(a.tiles[tn] >> 48) == inst;
+        const bool pref = tn >= 0 && static_cast<int>(tile_entry(tn) >> 48) == inst;
         // Buffer `buf` was last read two tiles ago, which every thread
         // finished before the barrier below of the previous tile.  Thread 0
         // places the tiles (one integer division each) for everyone.
@@ -1063,7 +1067,7 @@ __device__ __forceinline__ bool stage_pass(const StageArgs& a, unsigned bar0, un
         // Prefetch the next tile of the walk while this one is computed.
         if (threadIdx.x == 0 && pref) {
             geo_s[buf ^ 1] = tile_geo<T, NDIM, TY, TX>(
-                C, HJI_CHK(CK_TILE, static_cast<int>(a.tiles[tn] & 0xFFFFFFFFFFFFull), 1, C.ntiles));
+                C, HJI_CHK(CK_TILE, static_cast<int>(tile_entry(tn) & 0xFFFFFFFFFFFFull), 1, C.ntiles));
             issue(geo_s[buf ^ 1], buf ^ 1);
         }
 
