@@ -901,10 +901,10 @@ def _served_vs_f64(hji, torch, srv, reqs, records, opts, budget_s):
 # --profile-steps 2 --workload W` of the current stage kernels (mean of the
 # two launches of each stage; summaries under profiles/).
 DRAM_BYTES_PER_LAUNCH = {
-    ("di_8192^2", "first_stage"): (541506304 + 237935872 + 542315264 + 238590208) / 2,
-    ("di_8192^2", "fused_last_stage"): (1204115456 + 506545920 + 1207416576 + 505442816) / 2,
-    ("quad4d_61^4", "first_stage"): (121088512 + 36569344 + 121139968 + 36809984) / 2,
-    ("quad4d_61^4", "fused_last_stage"): (254387456 + 93981952 + 253672704 + 94644736) / 2,
+    ("di_8192^2", "first_stage"): (542247168 + 237938688 + 543044864 + 238681344) / 2,
+    ("di_8192^2", "fused_last_stage"): (1205116160 + 506549760 + 1207448320 + 505432320) / 2,
+    ("quad4d_61^4", "first_stage"): (120999168 + 36645888 + 121103360 + 37157120) / 2,
+    ("quad4d_61^4", "fused_last_stage"): (252988160 + 93743360 + 252901888 + 93992704) / 2,
 }
 # The multi-step march kernel on 8192^2 (one launch of 20 steps, read +
 # written, from `ncu ... -k regex:march_kernel -s 2 -c 2 python bench.py
@@ -919,7 +919,7 @@ DRAM_BYTES_MARCH_BATCH_PER_STEP = (33359375616 + 15277051136 + 33355850752 + 152
 # --profile-steps 4 --workload di1001` capture (first touch of each field per
 # launch: ncu flushes the caches between launches, so these are upper bounds
 # of what a launch inside a solve moves; no DRAM writes were counted).
-DRAM_BYTES_DI1001 = [8118528, 12154880, 16197120]
+DRAM_BYTES_DI1001 = [8110080, 12146176, 16188160]
 
 
 def march_traffic(name, multi_step):
