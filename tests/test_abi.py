@@ -45,6 +45,18 @@ def test_checked_build_exports_every_declared_symbol():
     assert not [n for n in _declared() if n not in exported]
 
 
+def test_library_path_selects_the_checked_build(monkeypatch):
+    """HJI_CHECKED_BUILD=1 makes the binding load the bounds-checked build;
+    anything else, the product library."""
+    import paper_1903_07715_gb300 as hji
+    monkeypatch.setenv("HJI_CHECKED_BUILD", "1")
+    assert hji.library_path().endswith("_hji_checked.so")
+    monkeypatch.setenv("HJI_CHECKED_BUILD", "0")
+    assert hji.library_path().endswith("_hji.so")
+    monkeypatch.delenv("HJI_CHECKED_BUILD")
+    assert hji.library_path().endswith("_hji.so")
+
+
 def test_binding_names_match_header(hji_lib):
     assert sorted(hji_lib.EXPORTS) == sorted(n for n in _declared())
     for n in _declared():
