@@ -26,14 +26,21 @@ FNS = {"tan": 0, "sin": 1, "cos": 2}
 
 # What pins each oracle function (tests/test_oracle_*.py):
 PINS = {
-    "one_sided": "exact on polynomials of the scheme's degree; convergence order on smooth data",
+    "one_sided": "exact on polynomials of the scheme's degree; convergence order on smooth data; "
+                 "WENO5 and ENO2 rebuilt from their definitions (interpolant derivatives, "
+                 "solved ideal weights, Jiang-Shu integral indicators) on rough data",
+    "gradient / ghost nodes": "the averaged one-sided derivatives at every node, ghosts built "
+                              "from their definition (extrapolation, wrap)",
+    "dynamics": "the paper's model equations; sin / cos / tan terms against numpy",
     "hamiltonian": "brute-force max-min over dense samples of U x D",
     "alpha_dt": "hand-computed values for the double integrator and quadrotor; brute force",
     "control_at / optimal_control": "brute-force argmax-min over dense samples of U x D; "
-                                    "the double integrator's closed-form braking control",
+                                    "the double integrator's closed-form braking control; "
+                                    "bang-bang control at a known gradient; the tie reading",
     "step/solve": "closed-form double-integrator value (Sec. II-B cost, Eq. (3)-(4)); "
                   "1-D advection closed form; stationary case; refinement order; "
-                  "Thm. 1 / Lemma 1 / Thm. 2 / Props. 1-2 / Remarks 1-2 orderings",
+                  "Thm. 1 / Lemma 1 / Thm. 2 / Props. 1-2 / Remarks 1-2 orderings; "
+                  "BRS option: advection closed form, a given start kept as it is",
     "step/solve, discounted": "closed form of the discounted one-cell shift (Courant number 1, "
                               "periodic); contraction from two starts (Sec. II-C); "
                               "gamma 0 or 1 equals the plain march",
