@@ -74,6 +74,7 @@ class ClockSampler:
         self.thread = None
 
     def start(self):
+        self.rows = []
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
@@ -114,6 +115,51 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+THROTTLE_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+
+
+def clocks_rejected(clk, low_frac=0.9):
+    """Why a timed region's clock record disqualifies its number, or None: a
+    hardware or thermal slowdown was active, or the median SM clock sat well
+    below the maximum with no reason active (a clock lock left by another
+    user).  A power cap alone is kept (normal on this part under load)."""
+    reasons = set(clk.get("reasons") or [])
+    bad = sorted(reasons.intersection(THROTTLE_REASONS))
+    if bad:
+        return "throttled: " + ",".join(bad)
+    sm, smax = clk.get("sm_mhz"), clk.get("sm_max_mhz")
+    if sm and smax and not reasons and sm < low_frac * smax:
+        return "SM clock %.0f MHz of %.0f with no reason active" % (sm, smax)
+    return None
+
+
+def measure_with_clock_check(timed, make_sampler, dist=None, torch=None, device="cuda"):
+    """Runs the timed region `timed()` under a clock sampler; if the clocks
+    disqualify it (on any rank), runs it once more.  Returns (result of the
+    kept run, its clock record, the rejected attempts' records).  Every rank
+    takes the same decision (one max-reduction of a flag), so the ranks'
+    barriers inside `timed` stay matched."""
+    rejected = []
+    for attempt in range(2):
+        sampler = make_sampler()
+        sampler.start()
+        res = timed()
+        clk = sampler.stop()
+        why = clocks_rejected(clk)
+        again = why is not None
+        if dist is not None:
+            flag = torch.tensor([1.0 if again else 0.0], device=device, dtype=torch.float64)
+            dist.all_reduce(flag, op=dist.ReduceOp.MAX)
+            again = float(flag.item()) > 0.0
+        if not again:
+            return res, clk, rejected
+        clk = dict(clk, rejected=why or "another rank's clocks")
+        if attempt == 1:
+            return res, clk, rejected
+        rejected.append(clk)
+    return res, clk, rejected
 
 
 def reduce_over_ranks(dist, torch, ms, updates, device):
@@ -283,10 +329,8 @@ def main():
         return total_ms, updates, launches, stats
 
     timed_solves(args.warmup)
-    clocks = ClockSampler(local_rank)
-    clocks.start()
-    ms, updates, launches, stats = timed_solves(args.steps)
-    clk = clocks.stop()
+    (ms, updates, launches, stats), clk, clk_rejected = measure_with_clock_check(
+        lambda: timed_solves(args.steps), lambda: ClockSampler(local_rank), dist, torch)
     if dist is not None:
         ms, updates = reduce_over_ranks(dist, torch, ms, updates, "cuda")
     value = updates / (ms / 1000.0)
@@ -345,6 +389,8 @@ def main():
                        "tile_shape": ["31x32", "15x64", "63x16"][tuned],
                        "autotune_ms_per_step": tune_ms, "march": args.march},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk}
+    if clk_rejected:
+        line["clocks_rejected_attempts"] = clk_rejected
 
     if rank == 0 and not args.no_variants:
         line["time_to_converge"] = time_to_converge(hji, torch, gd, dyn, l, l_dev, k_dev)
@@ -987,20 +1033,24 @@ def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=N
             run()
         # clocks sampled during this case's timed marches (a sampler of its own
         # unless the caller passed one)
-        sampler = clocks if clocks is not None else ClockSampler(_env_int("LOCAL_RANK", 0))
-        sampler.start()
-        ms, upd, launches = 0.0, 0, 0
-        for _ in range(repeats):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sts = run()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms += e0.elapsed_time(e1)
-            upd += sum(int(np.prod(gd["n"])) * s["steps"] for gd, s in zip(gds, sts))
-            launches += max(s["kernel_launches"] for s in sts)
-        clk = sampler.stop()
+        def timed_marches():
+            ms, upd, launches = 0.0, 0, 0
+            for _ in range(repeats):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sts = run()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                upd += sum(int(np.prod(gd["n"])) * s["steps"] for gd, s in zip(gds, sts))
+                launches += max(s["kernel_launches"] for s in sts)
+            return ms, upd, launches
+
+        make_sampler = ((lambda: clocks) if clocks is not None
+                        else (lambda: ClockSampler(_env_int("LOCAL_RANK", 0))))
+        (ms, upd, launches), clk, clk_rejected = measure_with_clock_check(timed_marches,
+                                                                          make_sampler)
         stage = None
         if len(grids) == 1:
             # Each of the two stage kernels alone between two CUDA events
@@ -1035,6 +1085,7 @@ def hbm_workloads(hji, torch, steps=50, only=None, repeats=1, warmup=1, clocks=N
         out[name] = {"nodes": cells, "steps": steps, "ms": ms / repeats, "tile_shape": ["31x32", "15x64", "63x16"][tuned],
                      "cell_updates_per_s": upd / (ms * 1e-3), "ms_total": ms,
                      "updates_total": upd, "launches": launches, "clocks": clk,
+                     "clocks_rejected_attempts": clk_rejected,
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                                   "frac": gbs / peak, "peak_source": src,
                                   "bytes_per_node_step": bytes_per_update,
