@@ -1,5 +1,6 @@
-"""bench.py's clock check on CPU: which clock records disqualify a timed
-region, and the single retake (all ranks together under a multi-rank launch)."""
+"""bench.py's host helpers on CPU: which clock records disqualify a timed
+region, the single retake (all ranks together under a multi-rank launch), and
+the arithmetic of the whole-solve FMA-rate fraction."""
 import os
 import socket
 import sys
@@ -113,3 +114,13 @@ def test_ranks_retake_together_over_gloo():
         assert p.exitcode == 0
     assert out[0][:2] == (2, 1) and out[1][:2] == (2, 1)
     assert "another rank" in out[0][2] and "sw_thermal_slowdown" in out[1][2]
+
+
+def test_alu_roofline_arithmetic():
+    """370 flops per node-stage, 1001^2 nodes, RK3, 4006 steps in 5.4 s: the
+    product over the time, and its fraction of a 1.056 TFLOP/s rate."""
+    r = bench.alu_roofline(1002001, 4006, 3, 5400.0, 1.056)
+    want = 370 * 1002001 * 3 * 4006 / 5.4 / 1e12
+    assert r["achieved"] == want or abs(r["achieved"] - want) < 1e-12 * want
+    assert abs(r["frac"] - want / 1.056) < 1e-12 and r["unit"] == "TFLOP/s"
+    assert bench.FLOPS_PER_NODE_STAGE == 370
