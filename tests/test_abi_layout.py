@@ -1,7 +1,8 @@
 """The Python binding's view of include/hji.h, checked on CPU: a small C
 program compiled against the header prints sizeof / offsetof of every struct
 member the ctypes structures declare, and the value of every constant the
-binding mirrors; both must agree with the binding exactly."""
+binding mirrors; both must agree with the binding exactly.  Every exported
+call's ctypes prototype is compared with the header's declaration."""
 import ctypes
 import os
 import shutil
@@ -73,3 +74,65 @@ def test_constants_match_header(header_layout):
         assert header_layout["HJI_FN_" + fn.upper()] == [v]
     for m, v in hji.MARCH.items():
         assert header_layout["HJI_MARCH_" + m.upper()] == [v]
+
+
+# ---------------------------------------------------------------- prototypes
+
+def _header_prototypes():
+    import re
+    with open(os.path.join(ROOT, "include", "hji.h")) as f:
+        s = f.read()
+    s = re.sub(r"/\*.*?\*/", " ", s, flags=re.S)
+    s = "\n".join(ln for ln in s.splitlines() if not ln.lstrip().startswith("#"))
+    enums = set(re.findall(r"typedef\s+enum\s*\{[^}]*\}\s*(\w+)\s*;", s))
+    handles = set(re.findall(r"typedef\s+struct\s+\w+\s*\*\s*(\w+)\s*;", s))
+    protos = {}
+    for ret, name, args in re.findall(r"([A-Za-z_][\w\s\*]*?)\b(hji_\w+)\s*\(([^;{]*?)\)\s*;", s):
+        params = [] if args.strip() in ("", "void") else [a.strip() for a in args.split(",")]
+        protos[name] = (" ".join(ret.split()), params)
+    return protos, enums, handles
+
+
+def _c_kind(decl, enums, handles, has_name=True):
+    """(base, pointer depth) of a C parameter declaration or return type."""
+    toks = decl.replace("*", " * ").split()
+    toks = [t for t in toks if t != "const"]
+    if has_name and toks and toks[-1] != "*":
+        toks = toks[:-1]
+    depth = toks.count("*")
+    base = [t for t in toks if t != "*"][0]
+    if base in enums:
+        base = "int"
+    if base in handles:
+        base, depth = "void", depth + 1
+    return {"int": "int", "int64_t": "i64", "size_t": "size", "double": "double",
+            "void": "void", "char": "char"}.get(base, base), depth
+
+
+def _py_kind(t):
+    depth = 0
+    while hasattr(t, "_type_") and isinstance(getattr(t, "_type_"), type) and \
+            t.__name__.startswith("LP_"):
+        depth, t = depth + 1, t._type_
+    simple = {ctypes.c_int: ("int", 0), ctypes.c_int64: ("i64", 0), ctypes.c_size_t: ("size", 0),
+              ctypes.c_double: ("double", 0), ctypes.c_void_p: ("void", 1),
+              ctypes.c_char_p: ("char", 1)}
+    if t in simple:
+        b, d = simple[t]
+        return b, depth + d
+    return t.__name__, depth
+
+
+def test_prototypes_match_header(hji_lib):
+    """Every exported call's ctypes argtypes / restype against its prototype in
+    the header (enums as int, the opaque handles as pointers)."""
+    protos, enums, handles = _header_prototypes()
+    lib = hji_lib.load()
+    assert set(hji.EXPORTS) <= set(protos), set(hji.EXPORTS) - set(protos)
+    for name in hji.EXPORTS:
+        ret, params = protos[name]
+        fn = getattr(lib, name)
+        assert _py_kind(fn.restype) == _c_kind(ret, enums, handles, has_name=False), name
+        got = [_py_kind(t) for t in fn.argtypes]
+        want = [_c_kind(p, enums, handles) for p in params]
+        assert got == want, (name, got, want)
